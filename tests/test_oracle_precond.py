@@ -1,0 +1,86 @@
+"""Pins for oracle/precond.py: dense P_alpha^{-1}, closed-form P_NC^{-1}, symmetry, limits."""
+import numpy as np
+import pytest
+import scipy.fft as sfft
+
+from oracle import allatonce as aao
+from oracle import operator as op
+from oracle import precond as pc
+from oracle import spectral as spc
+from paper_2506_03947_gb300 import inputs
+
+
+def test_dft_round_trip_and_conjugate_symmetry():
+    rng = np.random.default_rng(0)
+    for ell in (4, 6, 10):
+        r = rng.standard_normal((ell, 7))
+        v = pc.forward_transform(r, 0.03)
+        for j in range(1, ell):
+            np.testing.assert_allclose(v[ell - j], np.conj(v[j]), atol=1e-13)
+        np.testing.assert_allclose(v[0].imag, 0, atol=1e-13)
+        np.testing.assert_allclose(v[ell // 2].imag, 0, atol=1e-13)
+        np.testing.assert_allclose(pc.inverse_transform(v, 0.03), r, atol=1e-12)
+        # against numpy's FFT of the scaled vector (library routine, same convention)
+        s = spc.gamma(ell, 0.03)[:, None] * r
+        np.testing.assert_allclose(v, np.fft.fft(s, axis=0) / np.sqrt(ell), atol=1e-13)
+
+
+@pytest.mark.parametrize("ell,alpha", [(4, 0.5), (6, 1e-2), (10, 1e-2), (10, 0.3)])
+def test_exact_dft_path_equals_dense_inverse(ell, alpha):
+    P = inputs.config_2d(n=4, ell=ell, alpha=alpha)
+    A = op.fv_dense(P.kx, P.ky, P.kz, P.shape)
+    r = np.random.default_rng(1).standard_normal((ell, P.N))
+    z = pc.palpha_exact_apply(A, r, alpha)
+    zd = np.linalg.solve(aao.p_alpha_dense(A, ell, alpha), r.ravel()).reshape(ell, P.N)
+    np.testing.assert_allclose(z, zd, atol=1e-11 * np.abs(zd).max())
+
+
+def _pnc_closed_form_1d(r, N, kappa, ell, alpha, p):
+    # 1D constant kappa: P_NC^{-1} = (G^{-1}U x V) diag(q(mu_k - lambda_j)) (U*G x V^T),
+    # V the orthonormal DCT-II, q(z) = (1 - Omega_p(z))/z, Omega_p the Chebyshev error polynomial.
+    mu = 1 + 4 * kappa * np.sin(np.pi * np.arange(N) / (2 * N)) ** 2
+    lam = spc.scaled_roots(ell, alpha)
+    g = spc.gamma(ell, alpha)
+    s = g[:, None] * r
+    v = np.fft.fft(s, axis=0) / np.sqrt(ell)                 # U* over t
+    vh = sfft.dct(v.real, type=2, norm="ortho", axis=1) + 1j * sfft.dct(v.imag, type=2, norm="ortho", axis=1)
+    out = np.zeros_like(vh)
+    for j in range(ell):
+        th, de = spc.cheb_interval(1.0, 1 + 4 * kappa, lam[j])
+        zk = mu - lam[j]
+        om = spc.chebyshev_T(p, (th - zk) / de) / spc.chebyshev_T(p, th / de)
+        out[j] = (1 - om) / zk * vh[j]
+    y = sfft.idct(out.real, type=2, norm="ortho", axis=1) + 1j * sfft.idct(out.imag, type=2, norm="ortho", axis=1)
+    zt = np.fft.ifft(y, axis=0) * np.sqrt(ell)
+    return zt.real / g[:, None]
+
+
+@pytest.mark.parametrize("p", [1, 2, 7, 20])
+@pytest.mark.parametrize("alpha", [0.5, 1e-2])
+def test_pnc_matches_closed_form_1d(p, alpha):
+    N, kappa, ell = 32, 5.0, 10
+    P = inputs.make_problem("t", 1, (N,), ell, alpha, p, 0.0, (0.0,), 0, 1, kappa0=kappa)
+    A = lambda v: op.fv_apply(v.reshape(P.shape), P.kx, P.ky, P.kz).ravel()
+    r = np.random.default_rng(3).standard_normal((ell, N))
+    z = pc.pnc_apply(A, r, alpha, 1.0, 1 + 4 * kappa, p)
+    zc = _pnc_closed_form_1d(r, N, kappa, ell, alpha, p)
+    np.testing.assert_allclose(z, zc, atol=1e-11 * np.abs(zc).max())
+
+
+def test_pnc_tends_to_exact_palpha_and_is_linear():
+    P = inputs.config_2d(n=6, ell=6, alpha=0.1)
+    Ad = op.fv_dense(P.kx, P.ky, P.kz, P.shape)
+    A = lambda v: Ad @ v
+    mu_max = op.gershgorin_mu_max(P.kx, P.ky, P.kz, P.shape)
+    rng = np.random.default_rng(4)
+    r1, r2 = rng.standard_normal((2, 6, P.N))
+    z_exact = pc.palpha_exact_apply(Ad, r1, 0.1)
+    prev = np.inf
+    for p in (5, 20, 80, 300):
+        e = np.abs(pc.pnc_apply(A, r1, 0.1, 1.0, mu_max, p) - z_exact).max()
+        assert e < prev
+        prev = e
+    assert prev < 1e-9 * np.abs(z_exact).max()
+    za = pc.pnc_apply(A, 2.0 * r1 - 3.0 * r2, 0.1, 1.0, mu_max, 9)
+    zb = 2.0 * pc.pnc_apply(A, r1, 0.1, 1.0, mu_max, 9) - 3.0 * pc.pnc_apply(A, r2, 0.1, 1.0, mu_max, 9)
+    np.testing.assert_allclose(za, zb, atol=1e-11 * np.abs(zb).max())
