@@ -17,6 +17,10 @@ Linear Systems, Chebyshev acceleration), written for a complex centre:
 
 No inner stopping test: a fixed p makes the preconditioner a fixed linear
 operator (Section 5, NC1).
+
+Degenerate segment (delta = 0, the spectrum of B is the single point theta,
+e.g. a one-cell grid where A = I): the recurrence's limit as delta -> 0 is
+the exact solve, x_k = f/theta for every k >= 1; that limit is returned.
 """
 from __future__ import annotations
 
@@ -34,6 +38,11 @@ def chebyshev_solve(B: Callable[[np.ndarray], np.ndarray], f: np.ndarray, theta:
     f = np.asarray(f, dtype=complex)
     x = np.zeros_like(f)
     if p <= 0:
+        return x
+    if delta == 0.0:
+        x = f / theta
+        if history is not None:
+            history.extend(x.copy() for _ in range(p))
         return x
     sigma1 = theta / delta
     rho = 1.0 / sigma1

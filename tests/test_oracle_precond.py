@@ -84,3 +84,14 @@ def test_pnc_tends_to_exact_palpha_and_is_linear():
     za = pc.pnc_apply(A, 2.0 * r1 - 3.0 * r2, 0.1, 1.0, mu_max, 9)
     zb = 2.0 * pc.pnc_apply(A, r1, 0.1, 1.0, mu_max, 9) - 3.0 * pc.pnc_apply(A, r2, 0.1, 1.0, mu_max, 9)
     np.testing.assert_allclose(za, zb, atol=1e-11 * np.abs(zb).max())
+
+
+def test_single_cell_degenerate_segment_is_exact():
+    # N = 1: A = I, the segment of Lemma 2 is one point; CI's delta -> 0 limit is the exact solve
+    P = inputs.make_problem("t", 1, (1,), 4, 0.3, 1, 0.0, (0.0,), 0, 1)
+    A = op.fv_dense(P.kx, P.ky, P.kz, P.shape)
+    assert op.gershgorin_mu_max(P.kx, P.ky, P.kz, P.shape) == 1.0
+    r = np.random.default_rng(9).standard_normal((4, 1))
+    for p in (1, 2, 5):
+        z = pc.pnc_apply(lambda v: A @ v, r, 0.3, 1.0, 1.0, p)
+        np.testing.assert_allclose(z, pc.palpha_exact_apply(A, r, 0.3), atol=1e-13)
