@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark: all-at-once solves/sec on one GB300 (or N replicas).
+
+One step = one full solve of script-A x = b (Eq. 1) to explicit relative
+residual 1e-8 by right-preconditioned FGMRES with the nested-Chebyshev
+alpha-circulant preconditioner, on the 2D 1024 x 1024 lognormal-diffusivity
+workload (N = 1,048,576, ell = 10, alpha = 1e-2), complex-FP32 inner sweeps
+with p = 40 Chebyshev steps per frequency and FP64 outer solve.  The all-FP64
+GPU path is timed beside it on the same workload.
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank solves its
+own replica of the workload (the method has no cross-instance exchange):
+weak scaling, value = total solves / max-over-ranks time.
+
+--impl reference times the CPU oracle (oracle/, numpy FP64) instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("all-at-once solves/sec at rel. residual 1e-8 (mixed vs FP64 GPU); "
+          "fused Chebyshev HBM GB/s")
+UNIT = "solves/s"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    # name: (builder kwargs, p)
+    "2d1024_p40": dict(n=1024, p=40, seed_field=21, seed_b=22),
+    "2d1024_p10": dict(n=1024, p=10, seed_field=21, seed_b=22),
+    "2d256_p20": dict(n=256, p=20, seed_field=11, seed_b=12),
+}
+
+
+def workload_name(w):
+    d = WORKLOADS[w]
+    return "2d_lognormal_%dx%d_l10_a1e-2_p%d" % (d["n"], d["n"], d["p"])
+
+
+def make_problem(w):
+    from paper_2506_03947_gb300 import inputs
+    d = WORKLOADS[w]
+    return inputs.config_2d(n=d["n"], ell=10, alpha=1e-2, inner_its=d["p"],
+                            seed_field=d["seed_field"], seed_b=d["seed_b"])
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("cheb_kernels.cuh", "aao_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_03947_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key):
+    """dram bytes per launch from profiles/ncu_traffic.txt if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if len(line) >= 3 and line[0] == kernel_key and line[1] == cur:
+                return float(line[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="aao_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2506_03947_gb300 import binding
+    from paper_2506_03947_gb300 import build as pkg_build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg_build.build()
+    binding.load_library()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    P = make_problem(args.workload)
+    p = WORKLOADS[args.workload]["p"]
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    kx = torch.from_numpy(P.kx.ravel()).cuda()
+    ky = torch.from_numpy(P.ky.ravel()).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.zeros_like(b)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    L = P.ell * P.N
+
+    def timed_solves(solver, steps, warmup, profile=False, sampler=None):
+        for _ in range(warmup):
+            solver.solve(b, x, P.tol, 64)
+        barrier()
+        if profile:
+            solver.profile_enable(True)
+        n0 = binding.aao_kernel_launch_count()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if sampler:
+            sampler.start()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.add_(1.0)                     # evict L2 between timed steps (not timed)
+            ev[k][0].record(stream)
+            solver.solve(b, x, P.tol, 64)
+            ev[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
+        launches = binding.aao_kernel_launch_count() - n0
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        prof = solver.profile() if profile else None
+        if profile:
+            solver.profile_enable(False)
+        return ms, wall, launches, prof, clocks, solver.stats()
+
+    # --- mixed precision (headline) ---
+    s32 = binding.Solver(P.dim, P.n, kx, ky, None, P.ell, P.alpha, prec=binding.AAO_MIXED, inner_its=p,
+                         restart=64, stream=sptr)
+    sampler = ClockSampler(local) if not args.no_clocks else None
+    ms, wall, launches, prof, clocks, st32 = timed_solves(s32, args.steps, args.warmup, profile=True,
+                                                          sampler=sampler)
+    ms_max = max_over_ranks(ms)
+    value = world * args.steps / (ms_max / 1e3)
+    x32 = x.clone()
+
+    # --- end to end through the C ABI with pinned host buffers (copies timed) ---
+    bh = torch.from_numpy(P.b).pin_memory()
+    xh = torch.zeros(P.b.shape, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, min(args.warmup, 2))):
+        s32.solve(bh, xh, P.tol, 64)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        s32.solve(bh, xh, P.tol, 64)           # H2D b, solve, D2H x, stream synchronised
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = world * args.steps / e2e_s
+
+    # --- all-FP64 GPU path on the same workload ---
+    fp64 = None
+    if not args.no_fp64:
+        s32.close()
+        s64 = binding.Solver(P.dim, P.n, kx, ky, None, P.ell, P.alpha, prec=binding.AAO_FP64, inner_its=p,
+                             restart=64, stream=sptr)
+        k64 = max(2, args.steps // 2)
+        ms64, _, _, prof64, _, st64 = timed_solves(s64, k64, 1, profile=True)
+        ms64 = max_over_ranks(ms64)
+        rel = float(torch.linalg.norm(x - x32) / torch.linalg.norm(x))
+        fp64 = {"value": world * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64,
+                "outer_its": st64["outer_its"], "resid_explicit": st64["resid_explicit"],
+                "mixed_vs_fp64_rel_diff": rel,
+                "step_mid_gbs": (prof64["step_mid"]["bytes"] / (prof64["step_mid"]["ms"] * 1e-3) / 1e9
+                                 if prof64["step_mid"]["ms"] > 0 else None)}
+        s64.close()
+    else:
+        s32.close()
+
+    # --- roofline of the dominant kernel (fused Chebyshev sweep, steps 3..p-2) ---
+    peak, peak_src = measured_peaks()
+    mid = prof["step_mid"]
+    per_launch_bytes = mid["bytes"] / max(1, mid["launches"])
+    avg_ms = mid["ms"] / max(1, mid["launches"])
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    total_ms_prof = sum(v["ms"] for v in prof.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic("step_mid_" + args.workload),
+                "kernel": "k_cheb_step<float,10,2,1,2,false> (fused multi-frequency Chebyshev sweep)",
+                "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+                "launches": mid["launches"], "peak_source": peak_src + " hbm_gbs",
+                "share_of_profiled_time": mid["ms"] / total_ms_prof if total_ms_prof > 0 else None,
+                "classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None)}
+                            for k, v in prof.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(P, p, st32["outer_its"])
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 inner / f64 outer",
+        "data": "synthetic (seeded lognormal diffusivity, b_1 ~ N(0,1))",
+        "config": {"workload": workload_name(args.workload), "grid": [P.n[0], P.n[1]], "N": P.N,
+                   "ell": P.ell, "alpha": P.alpha, "inner_its": p, "tol": P.tol, "restart": 64,
+                   "precision": "mixed", "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "outer_its": st32["outer_its"], "resid_explicit": st32["resid_explicit"],
+        "a_matvecs": st32["a_matvecs"], "wall_ms_per_step": wall * 1e3 / args.steps,
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * L, "d2h_bytes_per_step": 8 * L},
+        "gpu_launches": launches, "clocks": clocks, "fp64_gpu": fp64,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline_sample(P, p, outer_its):
+    """Oracle (numpy FP64) on a bounded sample: one outer FGMRES iteration on the full grid.
+
+    The sample is one Arnoldi step of the oracle (initial residual, one P_NC
+    apply with all ell frequencies, one script-A product, MGS, Givens, solution
+    update and explicit residual); a full solve is that times the number of
+    outer iterations the solve needs.
+    """
+    from oracle import solve
+    t = time.perf_counter()
+    solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, 1, fixed_its=1)
+    dt = time.perf_counter() - t
+    return {"value": 1.0 / (dt * outer_its), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one oracle FGMRES iteration on the full %dx%d grid (%.2f s), scaled by %d outer "
+                      "iterations per solve" % (P.n[0], P.n[1], dt, outer_its)}
+
+
+def oracle_outer_its(workload):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_outer_its.txt")
+    with open(path) as f:
+        for line in f:
+            parts = line.split("#", 1)[0].split()
+            if parts and parts[0] == workload_name(workload):
+                return int(parts[1])
+    raise RuntimeError("no oracle iteration count for %s in %s" % (workload, path))
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import solve
+    P = make_problem(args.workload)
+    p = WORKLOADS[args.workload]["p"]
+    its = oracle_outer_its(args.workload)
+    for _ in range(args.warmup):
+        solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, 1, fixed_its=1)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, 1, fixed_its=1)
+        times.append(time.perf_counter() - t)
+    dt = sum(times) / len(times)
+    value = 1.0 / (dt * its)
+    sample = ("each step: one oracle FGMRES iteration on the full %dx%d grid (mean %.2f s), "
+              "scaled by the oracle's %d outer iterations per solve (tests/golden/oracle_outer_its.txt)"
+              % (P.n[0], P.n[1], dt, its))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * its * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded lognormal diffusivity, b_1 ~ N(0,1))",
+           "config": {"workload": workload_name(args.workload), "grid": [P.n[0], P.n[1]], "N": P.N,
+                      "ell": P.ell, "alpha": P.alpha, "inner_its": p, "tol": P.tol},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d1024_p40")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * aao.h -- C ABI of the GB300 all-at-once alpha-circulant solver (libaao.so).
+ *
+ * Problem (Eq. 1 of Tabeart, Gurol, Pearson, Weaver, "Block alpha-circulant
+ * preconditioners for all-at-once diffusion-based covariance operators"):
+ *
+ *     script-A x = b,   script-A = block lower bidiagonal with A on the
+ *     diagonal and -I_N below it;  (script-A x)_t = A x_t - x_{t-1}, x_0 = 0.
+ *
+ * A = I + K is the SPD Neumann finite-volume diffusion matrix on a 1D/2D/3D
+ * cell grid: (K v)_c = sum over the faces f of cell c of kappa_f (v_c - v_nbr).
+ * There are no boundary faces, so the constant vector is in ker K and the
+ * smallest eigenvalue of A is mu_min = 1.
+ *
+ * Preconditioner: P_alpha (Eq. 2) applied through Eq. 5 -- alpha-scaling,
+ * length-ell DFT over the time blocks, ell shifted solves
+ * (A - lambda_j I) y_j = v_j (Eq. 7) each approximated by a fixed number p of
+ * Chebyshev semi-iteration steps over the segment of Lemma 2 (P_NC1,
+ * Section 5), inverse DFT and unscaling.  Only the ell/2+1 frequencies that
+ * are distinct for real input and even ell are computed (Section 3).
+ * Outer solver: right-preconditioned flexible GMRES with classical
+ * Gram-Schmidt plus one re-orthogonalisation; convergence is the paper's
+ * relative residual ||b - script-A x|| / ||b|| (Section 5), certified by an
+ * explicit FP64 residual.
+ *
+ * Layout of every block vector (b, x, r, z, y): "block-major" as in Eq. 1,
+ * ell blocks of N doubles, block t-1 at offset (t-1)*N; within a block cells
+ * are ordered x fastest: c = i + n0*(j + n1*k).
+ *
+ * Memory: pointers may be device pointers or host pointers (pageable or
+ * pinned); the library detects which (cudaPointerGetAttributes) and stages
+ * host data through buffers it owns, with the copies on the handle's stream.
+ * The caller owns every pointer it passes and keeps device buffers alive
+ * until the call returns (all calls synchronise the handle's stream before
+ * returning, except where noted).  The library owns all workspace.
+ *
+ * Threads and streams: one handle is used by one host thread at a time; all
+ * device work of a handle is ordered on the stream given at creation.
+ *
+ * Errors: every int-returning call returns an AAO_* status.  On failure a
+ * one-line message is available from aao_last_error(h) (or
+ * aao_last_create_error() when aao_create itself failed).  There is no CPU
+ * fallback: without a usable CUDA device every call fails with AAO_ECUDA.
+ */
+#ifndef AAO_H
+#define AAO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define AAO_OK 0        /* success                                              */
+#define AAO_EINVAL 1    /* invalid argument (sizes, ell, alpha, kappa, pointers) */
+#define AAO_ENOMEM 2    /* device or host allocation failed                     */
+#define AAO_ECUDA 3     /* a CUDA call failed (no device, launch error, ...)    */
+#define AAO_ENOTCONV 4  /* solve hit max_outer; x holds the last iterate        */
+#define AAO_ENUMERIC 5  /* a NaN or Inf appeared in a residual or norm          */
+
+/* ---- precision modes ----------------------------------------------------- */
+#define AAO_FP64 0      /* every step in FP64                                   */
+#define AAO_MIXED 1     /* DFT, Chebyshev sweeps, inverse DFT in (complex) FP32;
+                           script-A, Arnoldi, Givens, residuals in FP64         */
+
+/* ---- limits -------------------------------------------------------------- */
+#define AAO_MAX_ELL 16      /* ell must be even, 4 <= ell <= AAO_MAX_ELL        */
+#define AAO_MAX_RESTART 64  /* Krylov cycle length limit                        */
+#define AAO_MAX_HIST 512    /* residual history entries kept in aao_stats       */
+
+typedef struct aao_ctx* aao_handle;
+
+/* Options for aao_create.  Fill with aao_default_options first. */
+typedef struct {
+  int32_t prec;            /* AAO_FP64 or AAO_MIXED (default AAO_MIXED)                 */
+  int32_t inner_its;       /* p >= 1: Chebyshev steps per frequency (default 20)         */
+  int32_t restart;         /* Krylov cycle length m, 1..AAO_MAX_RESTART (default 64)     */
+  int32_t reorth;          /* 1: CGS with one re-orthogonalisation (default); 0: CGS once */
+  double mu_max_override;  /* > 0: upper spectral bound of A to use instead of the
+                              Gershgorin bound max_c (1 + 2 sum_f kappa_f) (default 0)   */
+  void* stream;            /* cudaStream_t for all work of the handle (NULL = default)  */
+} aao_options;
+
+/* Statistics of the last aao_solve (Section 5 counts A-matvecs per outer
+ * iteration: ell for script-A, ell*p for the preconditioner, Table 1). */
+typedef struct {
+  int32_t outer_its;       /* Arnoldi steps taken (all cycles)                          */
+  int32_t cycles;          /* Krylov cycles (restarts + 1)                              */
+  int32_t converged;       /* 1 if the explicit residual met tol                        */
+  int32_t n_hist;          /* entries in hist                                           */
+  int64_t a_matvecs;       /* real A-matvec equivalents, counted as in Table 1         */
+  double resid_est;        /* last Givens estimate of ||b - script-A x|| / ||b||        */
+  double resid_explicit;   /* explicit FP64 ||b - script-A x|| / ||b|| at return        */
+  double mu_min;           /* lower spectral bound of A used (1 for Neumann)            */
+  double mu_max;           /* upper spectral bound of A used                            */
+  double hist[AAO_MAX_HIST]; /* relative residual estimate after each Arnoldi step      */
+} aao_stats;
+
+/* Kernel classes timed by the built-in profiler (aao_profile_*). */
+#define AAO_PROF_DFT 0        /* forward transform (Eq. 5's U* Gamma)                      */
+#define AAO_PROF_STEP_FIRST 1 /* Chebyshev step k = 1 (x_1 = bhat/theta)                   */
+#define AAO_PROF_STEP_SECOND 2 /* Chebyshev step k = 2                                     */
+#define AAO_PROF_STEP_MID 3   /* Chebyshev steps 3 <= k <= p-2 (the fused sweep)           */
+#define AAO_PROF_STEP_LAST 4  /* last Chebyshev step fused with the inverse transform      */
+#define AAO_PROF_MATVEC 5     /* script-A matvec and explicit residual                      */
+#define AAO_PROF_ORTH 6       /* Gram-Schmidt multi-dots, updates and their reductions     */
+#define AAO_NPROF 7
+
+/* Accumulated device time of each kernel class, from CUDA events recorded on
+ * the handle's stream around every launch while profiling is on, with the
+ * algorithmic bytes each launch must move (reads + writes of its operands,
+ * every value once). */
+typedef struct {
+  int64_t launches[AAO_NPROF];
+  double ms[AAO_NPROF];
+  double bytes[AAO_NPROF];
+} aao_profile;
+
+/* Fill *opt with the defaults listed above.  Never fails. */
+void aao_default_options(aao_options* opt);
+
+/*
+ * Create a solver for one instance (Eq. 1 with Eq. 2's preconditioner).
+ *   h      out: new handle (NULL on failure).
+ *   dim    1, 2 or 3.
+ *   n      cells per axis n[0] (x), n[1] (y), n[2] (z); unused axes must be 1;
+ *          N = n0*n1*n2 >= 1.
+ *   kx     interior x-face diffusivities, (n2, n1, n0-1) x fastest, doubles;
+ *   ky     y-faces (n2, n1-1, n0); kz z-faces (n2-1, n1, n0).  A pointer for
+ *          an axis with no faces may be NULL.  Host or device memory; copied.
+ *          Every value must be finite and > 0.
+ *   ell    number of time blocks: even, 4 <= ell <= AAO_MAX_ELL (Section 1
+ *          takes ell > 2 even; conjugate symmetry needs ell even, Section 3).
+ *   alpha  0 < alpha < mu_min^ell = 1 (Corollary 1 and Lemma 1 need
+ *          alpha != mu_j^ell; alpha = 1 makes P_alpha singular here).
+ *   opt    options or NULL for the defaults.
+ * Sets up: Gershgorin mu_max (or the override), shifts lambda_j, scalings,
+ * Chebyshev coefficient tables (host FP64, uploaded as FP32 and/or FP64),
+ * and the workspace (about (2m+3) ell N doubles plus 3 ell N Chebyshev
+ * values).  Returns AAO_EINVAL, AAO_ENOMEM or AAO_ECUDA on failure.
+ */
+int aao_create(aao_handle* h, int dim, const int64_t n[3], const double* kx,
+               const double* ky, const double* kz, int ell, double alpha,
+               const aao_options* opt);
+
+/* y = script-A x (Eq. 1), FP64.  x, y: ell*N doubles, block-major, distinct. */
+int aao_matvec(aao_handle h, const double* x, double* y);
+
+/* z = P_NC^{-1} r: Eq. 5 with p Chebyshev steps per frequency (NC1), in the
+ * handle's precision.  r, z: ell*N doubles, block-major, distinct. */
+int aao_precond_apply(aao_handle h, const double* r, double* z);
+
+/*
+ * Solve script-A x = b by right-preconditioned FGMRES(m) with P_NC.
+ *   b          ell*N doubles (the paper's b has only b_1 non-zero; any b works).
+ *   x          in: initial guess if use_x0 != 0, else ignored (x_0 = 0,
+ *              Section 5); out: the solution iterate.
+ *   tol        target for the explicit relative residual ||b - script-A x||/||b||.
+ *   max_outer  limit on Arnoldi steps over all cycles (>= 1).
+ *   inner_its  p for this solve (> 0), or 0 to keep the handle's value.
+ * Returns AAO_OK when the explicit residual is below tol, AAO_ENOTCONV when
+ * max_outer was reached first (x then holds the last iterate), AAO_ENUMERIC
+ * on NaN/Inf.  Statistics: aao_get_stats.
+ */
+int aao_solve(aao_handle h, const double* b, double* x, double tol, int max_outer,
+              int inner_its, int use_x0);
+
+/* Run exactly k Arnoldi steps in one cycle from x_0 = 0 and form x (no early
+ * stop); used to compare iterates step by step with a reference.  Same
+ * arguments as aao_solve.  Returns AAO_OK (or an error). */
+int aao_solve_fixed(aao_handle h, const double* b, double* x, int k, int inner_its);
+
+/* Copy the statistics of the last solve into *s. */
+int aao_get_stats(aao_handle h, aao_stats* s);
+
+/* Spectral bounds used for A: mu_min and mu_max (Lemma 2's segment ends). */
+int aao_get_bounds(aao_handle h, double* mu_min, double* mu_max);
+
+/* Message of the last failed call on h ("" if none).  Valid until the next
+ * call on h.  Never NULL. */
+const char* aao_last_error(aao_handle h);
+
+/* Message of the last failed aao_create in this process. */
+const char* aao_last_create_error(void);
+
+/* Turn event timing of the kernel classes on (1) or off (0) for h; either
+ * way the accumulated profile is cleared.  Timing adds two event records per
+ * timed launch on the handle's stream. */
+int aao_profile_enable(aao_handle h, int on);
+
+/* Synchronise h's stream, resolve the recorded events and copy the
+ * accumulated profile into *out. */
+int aao_profile_get(aao_handle h, aao_profile* out);
+
+/* Number of kernels this library has launched in this process (all handles);
+ * used to count device work inside a timed region. */
+int64_t aao_kernel_launch_count(void);
+
+/* Release the handle and all workspace.  NULL is allowed. */
+void aao_destroy(aao_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AAO_H */

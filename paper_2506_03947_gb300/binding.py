@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libaao.so (include/aao.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they must
+be contiguous float64.  There is no fallback: if libaao.so is missing or
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libaao.so")
+
+AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOTCONV, AAO_ENUMERIC = 0, 1, 2, 3, 4, 5
+AAO_FP64, AAO_MIXED = 0, 1
+AAO_MAX_ELL, AAO_MAX_RESTART, AAO_MAX_HIST = 16, 64, 512
+
+STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA",
+                4: "AAO_ENOTCONV", 5: "AAO_ENUMERIC"}
+
+# every symbol include/aao.h declares (checked by the CPU test suite)
+EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_apply", "aao_solve",
+            "aao_solve_fixed", "aao_get_stats", "aao_get_bounds", "aao_last_error",
+            "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
+            "aao_profile_enable", "aao_profile_get")
+
+AAO_NPROF = 7
+PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth")
+
+
+class AaoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class aao_options(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("inner_its", C.c_int32), ("restart", C.c_int32),
+                ("reorth", C.c_int32), ("mu_max_override", C.c_double), ("stream", C.c_void_p)]
+
+
+class aao_stats(C.Structure):
+    _fields_ = [("outer_its", C.c_int32), ("cycles", C.c_int32), ("converged", C.c_int32),
+                ("n_hist", C.c_int32), ("a_matvecs", C.c_int64), ("resid_est", C.c_double),
+                ("resid_explicit", C.c_double), ("mu_min", C.c_double), ("mu_max", C.c_double),
+                ("hist", C.c_double * AAO_MAX_HIST)]
+
+
+class aao_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * AAO_NPROF), ("ms", C.c_double * AAO_NPROF),
+                ("bytes", C.c_double * AAO_NPROF)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> C.CDLL:
+    """Load libaao.so once; raise if it is absent (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libaao.so not found at %s: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % p)
+    lib = C.CDLL(p)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    lib.aao_default_options.argtypes = [C.POINTER(aao_options)]
+    lib.aao_default_options.restype = None
+    lib.aao_create.argtypes = [C.POINTER(vp), i32, C.POINTER(C.c_int64), vp, vp, vp, i32, dbl,
+                               C.POINTER(aao_options)]
+    lib.aao_create.restype = i32
+    lib.aao_matvec.argtypes = [vp, vp, vp]
+    lib.aao_matvec.restype = i32
+    lib.aao_precond_apply.argtypes = [vp, vp, vp]
+    lib.aao_precond_apply.restype = i32
+    lib.aao_solve.argtypes = [vp, vp, vp, dbl, i32, i32, i32]
+    lib.aao_solve.restype = i32
+    lib.aao_solve_fixed.argtypes = [vp, vp, vp, i32, i32]
+    lib.aao_solve_fixed.restype = i32
+    lib.aao_get_stats.argtypes = [vp, C.POINTER(aao_stats)]
+    lib.aao_get_stats.restype = i32
+    lib.aao_get_bounds.argtypes = [vp, C.POINTER(dbl), C.POINTER(dbl)]
+    lib.aao_get_bounds.restype = i32
+    lib.aao_last_error.argtypes = [vp]
+    lib.aao_last_error.restype = C.c_char_p
+    lib.aao_last_create_error.argtypes = []
+    lib.aao_last_create_error.restype = C.c_char_p
+    lib.aao_kernel_launch_count.argtypes = []
+    lib.aao_kernel_launch_count.restype = i64
+    lib.aao_destroy.argtypes = [vp]
+    lib.aao_destroy.restype = None
+    lib.aao_profile_enable.argtypes = [vp, i32]
+    lib.aao_profile_enable.restype = i32
+    lib.aao_profile_get.argtypes = [vp, C.POINTER(aao_profile)]
+    lib.aao_profile_get.restype = i32
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous float64 torch tensor or numpy array (None -> 0)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):                       # torch.Tensor
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors passed to libaao must be contiguous float64")
+        return int(a.data_ptr())
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays passed to libaao must be C-contiguous float64 numpy arrays")
+    return int(a.ctypes.data)
+
+
+def _check(h, rc: int, ok=(AAO_OK,)) -> int:
+    if rc not in ok:
+        lib = load_library()
+        msg = (lib.aao_last_error(h) if h else lib.aao_last_create_error()) or b""
+        raise AaoError(rc, msg.decode(errors="replace"))
+    return rc
+
+
+def aao_default_options() -> aao_options:
+    opt = aao_options()
+    load_library().aao_default_options(C.byref(opt))
+    return opt
+
+
+def aao_create(dim: int, n: Sequence[int], kx, ky, kz, ell: int, alpha: float,
+               opt: Optional[aao_options] = None):
+    lib = load_library()
+    h = C.c_void_p()
+    n3 = (C.c_int64 * 3)(*[int(v) for v in (list(n) + [1, 1, 1])[:3]])
+    rc = lib.aao_create(C.byref(h), int(dim), n3, _ptr(kx) or None, _ptr(ky) or None,
+                        _ptr(kz) or None, int(ell), float(alpha),
+                        C.byref(opt) if opt is not None else None)
+    _check(None, rc)
+    return h
+
+
+def aao_matvec(h, x, y) -> int:
+    return _check(h, load_library().aao_matvec(h, _ptr(x), _ptr(y)))
+
+
+def aao_precond_apply(h, r, z) -> int:
+    return _check(h, load_library().aao_precond_apply(h, _ptr(r), _ptr(z)))
+
+
+def aao_solve(h, b, x, tol: float, max_outer: int, inner_its: int = 0, use_x0: bool = False,
+              allow_notconv: bool = False) -> int:
+    ok = (AAO_OK, AAO_ENOTCONV) if allow_notconv else (AAO_OK,)
+    return _check(h, load_library().aao_solve(h, _ptr(b), _ptr(x), float(tol), int(max_outer),
+                                              int(inner_its), 1 if use_x0 else 0), ok)
+
+
+def aao_solve_fixed(h, b, x, k: int, inner_its: int = 0) -> int:
+    return _check(h, load_library().aao_solve_fixed(h, _ptr(b), _ptr(x), int(k), int(inner_its)))
+
+
+def aao_get_stats(h) -> dict:
+    s = aao_stats()
+    _check(h, load_library().aao_get_stats(h, C.byref(s)))
+    return {"outer_its": s.outer_its, "cycles": s.cycles, "converged": bool(s.converged),
+            "a_matvecs": s.a_matvecs, "resid_est": s.resid_est,
+            "resid_explicit": s.resid_explicit, "mu_min": s.mu_min, "mu_max": s.mu_max,
+            "hist": [s.hist[i] for i in range(s.n_hist)]}
+
+
+def aao_get_bounds(h):
+    a, b = C.c_double(), C.c_double()
+    _check(h, load_library().aao_get_bounds(h, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def aao_last_error(h) -> str:
+    return (load_library().aao_last_error(h) or b"").decode(errors="replace")
+
+
+def aao_kernel_launch_count() -> int:
+    return int(load_library().aao_kernel_launch_count())
+
+
+def aao_profile_enable(h, on: bool) -> int:
+    return _check(h, load_library().aao_profile_enable(h, 1 if on else 0))
+
+
+def aao_profile_get(h) -> dict:
+    p = aao_profile()
+    _check(h, load_library().aao_profile_get(h, C.byref(p)))
+    return {name: {"launches": int(p.launches[i]), "ms": float(p.ms[i]), "bytes": float(p.bytes[i])}
+            for i, name in enumerate(PROF_NAMES)}
+
+
+def aao_destroy(h) -> None:
+    if h:
+        load_library().aao_destroy(h)
+
+
+class Solver:
+    """Owns one handle; methods forward to the C ABI (marshalling only)."""
+
+    def __init__(self, dim, n, kx, ky, kz, ell, alpha, prec=AAO_MIXED, inner_its=20, restart=64,
+                 reorth=True, mu_max_override=0.0, stream=None):
+        opt = aao_default_options()
+        opt.prec = int(prec)
+        opt.inner_its = int(inner_its)
+        opt.restart = int(restart)
+        opt.reorth = 1 if reorth else 0
+        opt.mu_max_override = float(mu_max_override)
+        opt.stream = stream
+        self.ell = int(ell)
+        self.n = tuple(int(v) for v in (list(n) + [1, 1, 1])[:3])
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.h = aao_create(dim, n, kx, ky, kz, ell, alpha, opt)
+
+    def matvec(self, x, y):
+        return aao_matvec(self.h, x, y)
+
+    def precond_apply(self, r, z):
+        return aao_precond_apply(self.h, r, z)
+
+    def solve(self, b, x, tol, max_outer, inner_its=0, use_x0=False, allow_notconv=False):
+        return aao_solve(self.h, b, x, tol, max_outer, inner_its, use_x0, allow_notconv)
+
+    def solve_fixed(self, b, x, k, inner_its=0):
+        return aao_solve_fixed(self.h, b, x, k, inner_its)
+
+    def stats(self):
+        return aao_get_stats(self.h)
+
+    def bounds(self):
+        return aao_get_bounds(self.h)
+
+    def profile_enable(self, on=True):
+        return aao_profile_enable(self.h, on)
+
+    def profile(self):
+        return aao_profile_get(self.h)
+
+    def close(self):
+        if self.h:
+            aao_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,728 @@
+// Host side of libaao: the C ABI declared in include/aao.h.
+//
+// aao_create builds the scalar set-up of the method on the host in FP64
+// (shifts lambda_j and scalings of Section 2.2, Chebyshev coefficients for the
+// segment of Lemma 2) and everything O(N) on the device.  The solve loop is
+// driven from the host: per Arnoldi step it launches the preconditioner
+// kernels, the script-A matvec and the Gram-Schmidt kernels, and reads back
+// one 16-byte residual estimate to decide whether to stop.
+#include "aao.h"
+#include "aao_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace aao {
+long long launch_count();
+cudaError_t launch_build_coeffs(const GridDesc& g, const double* kx, const double* ky, const double* kz,
+                                double* cx, double* cy, double* cz, float* fx, float* fy, float* fz,
+                                double* partials, int* bad, double* smax_out, cudaStream_t s);
+int build_coeff_blocks(int64_t N);
+}  // namespace aao
+
+using aao::DftArgs;
+using aao::GridDesc;
+using aao::IdftArgs;
+using aao::ScLayout;
+using aao::StepArgs;
+
+struct aao_ctx {
+  int dim = 0;
+  int64_t n[3] = {1, 1, 1};
+  int64_t N = 0, L = 0;
+  int ell = 0;
+  double alpha = 0.0;
+  int prec = AAO_MIXED;
+  int p = 20;
+  int m = 64;
+  int reorth = 1;
+  double mu_min = 1.0, mu_max = 0.0;
+  cudaStream_t stream = nullptr;
+  GridDesc g{};
+
+  double *cx64 = nullptr, *cy64 = nullptr, *cz64 = nullptr;
+  float *cx32 = nullptr, *cy32 = nullptr, *cz32 = nullptr;
+  void *bhat = nullptr, *xa = nullptr, *xb = nullptr;  // Chebyshev fields (float or double)
+  double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
+  double* sc = nullptr;                                // small scalars, ScLayout
+  double* partials = nullptr;                          // reduction partials
+  int64_t part_cap = 0;
+  double *stage_a = nullptr, *stage_b = nullptr;       // staging for host pointers (L each)
+  double* pinned = nullptr;                            // pinned host scalars
+
+  std::vector<StepArgs<float>> steps32;    // index k = 0 .. p-1 (0 holds 1/theta for p = 1)
+  std::vector<StepArgs<double>> steps64;
+  DftArgs<float> dft32{};
+  DftArgs<double> dft64{};
+  IdftArgs<float> idft32{};
+  IdftArgs<double> idft64{};
+
+  aao_stats stats{};
+  std::string err;
+
+  // event timing of kernel classes (aao_profile_*)
+  struct Pending {
+    int cls;
+    int e0;
+    int launches;
+    double bytes;
+  };
+  bool prof = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<Pending> pending;
+  aao_profile profacc{};
+};
+
+static std::string g_create_error;
+
+namespace {
+
+int fail(aao_ctx* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define AAO_CK(h, call)                                                                        \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- profiling: events around timed launches -------------------------------
+
+int prof_begin(aao_ctx* h, int cls, double bytes, int launches = 1) {
+  if (!h->prof) return -1;
+  const int idx = (int)h->pending.size();
+  const int e0 = 2 * idx;
+  while ((int)h->events.size() < e0 + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->events.push_back(e);
+  }
+  if (cudaEventRecord(h->events[e0], h->stream) != cudaSuccess) return -1;
+  h->pending.push_back({cls, e0, launches, bytes});
+  return idx;
+}
+
+void prof_end(aao_ctx* h, int idx) {
+  if (idx < 0) return;
+  cudaEventRecord(h->events[h->pending[idx].e0 + 1], h->stream);
+}
+
+// The stream must be synchronised: every recorded pair has completed.
+void prof_resolve(aao_ctx* h) {
+  for (const auto& p : h->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->events[p.e0], h->events[p.e0 + 1]) == cudaSuccess) {
+      h->profacc.ms[p.cls] += ms;
+      h->profacc.launches[p.cls] += p.launches;
+      h->profacc.bytes[p.cls] += p.bytes;
+    }
+  }
+  h->pending.clear();
+}
+
+// Chebyshev and transform tables for the current p (host FP64, Section 2.2 and
+// Lemma 2): lambda_m = alpha^{1/ell} exp(-2 pi i m/ell) paired with the forward
+// transform exp(-2 pi i t m/ell); theta_m = (mu_max+mu_min)/2 - lambda_m,
+// delta = (mu_max-mu_min)/2; rho_0 = delta/theta, rho_k = 1/(2 theta/delta - rho_{k-1}).
+void build_tables(aao_ctx* h) {
+  using cd = std::complex<double>;
+  const int ell = h->ell, F = ell / 2 + 1, p = h->p;
+  const double pi = 3.14159265358979323846;
+  const double delta = 0.5 * (h->mu_max - h->mu_min);
+  const double root = std::pow(h->alpha, 1.0 / ell);
+  std::vector<cd> lam(F), theta(F);
+  for (int m = 0; m < F; ++m) {
+    lam[m] = root * std::exp(cd(0.0, -2.0 * pi * m / ell));
+    if (m == 0 || 2 * m == ell) lam[m] = cd(lam[m].real(), 0.0);
+    theta[m] = 0.5 * (h->mu_max + h->mu_min) - lam[m];
+  }
+  h->steps32.assign(std::max(p, 1), StepArgs<float>{});
+  h->steps64.assign(std::max(p, 1), StepArgs<double>{});
+  std::vector<cd> rho_prev(F);
+  for (int m = 0; m < F; ++m) rho_prev[m] = delta / theta[m];
+  for (int k = 0; k < std::max(p, 1); ++k) {
+    StepArgs<double>& s = h->steps64[k];
+    for (int m = 0; m < F; ++m) {
+      cd a(0.0, 0.0), gk(0.0, 0.0);
+      if (k >= 1 && delta == 0.0) {
+        // single-point segment (one cell, A = I): the delta -> 0 limit is the
+        // exact solve, a = 0 and g = 1/theta
+        gk = 1.0 / theta[m];
+      } else if (k >= 1) {
+        const cd rho = 1.0 / (2.0 * theta[m] / delta - rho_prev[m]);
+        a = rho * rho_prev[m];
+        gk = 2.0 * rho / delta;
+        rho_prev[m] = rho;
+      }
+      const cd it = 1.0 / theta[m];
+      s.lam_re[m] = lam[m].real();
+      s.lam_im[m] = lam[m].imag();
+      s.a_re[m] = a.real();
+      s.a_im[m] = a.imag();
+      s.g_re[m] = gk.real();
+      s.g_im[m] = gk.imag();
+      s.it_re[m] = it.real();
+      s.it_im[m] = it.imag();
+    }
+    StepArgs<float>& f = h->steps32[k];
+    for (int m = 0; m < aao::kMaxF; ++m) {
+      f.lam_re[m] = (float)s.lam_re[m];
+      f.lam_im[m] = (float)s.lam_im[m];
+      f.a_re[m] = (float)s.a_re[m];
+      f.a_im[m] = (float)s.a_im[m];
+      f.g_re[m] = (float)s.g_re[m];
+      f.g_im[m] = (float)s.g_im[m];
+      f.it_re[m] = (float)s.it_re[m];
+      f.it_im[m] = (float)s.it_im[m];
+    }
+  }
+  const double isq = 1.0 / std::sqrt((double)ell);
+  h->dft64 = DftArgs<double>{};
+  h->idft64 = IdftArgs<double>{};
+  for (int t = 0; t < ell; ++t) {
+    h->dft64.gamma[t] = std::pow(h->alpha, (double)t / ell);
+    h->idft64.igamma[t] = std::pow(h->alpha, -(double)t / ell);
+    for (int m = 0; m < F; ++m) {
+      const double ang = 2.0 * pi * (double)((t * m) % ell) / ell;
+      h->dft64.cf[t][m] = std::cos(ang) * isq;
+      h->dft64.sf[t][m] = std::sin(ang) * isq;
+      if (m == 0) {
+        h->idft64.ci[t][m] = isq;
+        h->idft64.si[t][m] = 0.0;
+      } else if (2 * m == ell) {
+        h->idft64.ci[t][m] = (t % 2 == 0) ? isq : -isq;
+        h->idft64.si[t][m] = 0.0;
+      } else {
+        h->idft64.ci[t][m] = 2.0 * std::cos(ang) * isq;
+        h->idft64.si[t][m] = 2.0 * std::sin(ang) * isq;
+      }
+    }
+  }
+  h->dft32 = DftArgs<float>{};
+  h->idft32 = IdftArgs<float>{};
+  for (int t = 0; t < aao::kMaxEll; ++t) {
+    h->dft32.gamma[t] = h->dft64.gamma[t];
+    h->idft32.igamma[t] = h->idft64.igamma[t];
+    for (int m = 0; m < aao::kMaxF; ++m) {
+      h->dft32.cf[t][m] = (float)h->dft64.cf[t][m];
+      h->dft32.sf[t][m] = (float)h->dft64.sf[t][m];
+      h->idft32.ci[t][m] = (float)h->idft64.ci[t][m];
+      h->idft32.si[t][m] = (float)h->idft64.si[t][m];
+    }
+  }
+}
+
+template <typename T>
+int precond_impl(aao_ctx* h, const double* r, const double* rscale, double* z, const std::vector<StepArgs<T>>& st,
+                 const DftArgs<T>& da, const IdftArgs<T>& ia, const T* cx, const T* cy, const T* cz) {
+  const int p = h->p;
+  cudaStream_t s = h->stream;
+  T* bhat = (T*)h->bhat;
+  T* xa = (T*)h->xa;
+  T* xb = (T*)h->xb;
+  const double N = (double)h->N, ell = (double)h->ell, Ts = (double)sizeof(T), dim = (double)h->dim;
+  if (p == 1) {
+    const int pi = prof_begin(h, AAO_PROF_STEP_LAST, N * 16.0 * ell);
+    AAO_CK(h, aao::launch_direct<T>(h->g, h->dim, h->ell, r, rscale, z, da, st[0], ia, s));
+    prof_end(h, pi);
+    return AAO_OK;
+  }
+  int pi = prof_begin(h, AAO_PROF_DFT, N * (8.0 * ell + ell * Ts));
+  AAO_CK(h, aao::launch_dft<T>(h->g, h->dim, h->ell, r, rscale, bhat, da, s));
+  prof_end(h, pi);
+  // algorithmic bytes of one step: x_k (or bhat) read, bhat read when x_k is a
+  // buffer, x_{k-1} read when buffered, coefficients, and x_{k+1} or z written
+  auto step_bytes = [&](int ksrc, int psrc, bool last) {
+    double b = ell * Ts + (ksrc == 1 ? ell * Ts : 0.0) + (psrc == 2 ? ell * Ts : 0.0) + dim * Ts;
+    b += last ? 8.0 * ell : ell * Ts;
+    return N * b;
+  };
+  auto step_class = [](int ksrc, int psrc, bool last) {
+    if (last) return AAO_PROF_STEP_LAST;
+    if (ksrc == 0) return AAO_PROF_STEP_FIRST;
+    if (psrc == 1) return AAO_PROF_STEP_SECOND;
+    return AAO_PROF_STEP_MID;
+  };
+  // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in xa (or z if p == 2)
+  pi = prof_begin(h, step_class(0, 0, p == 2), step_bytes(0, 0, p == 2));
+  AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 0, 0, p == 2, cx, cy, cz, bhat, nullptr, xa, z, st[1], ia, s));
+  prof_end(h, pi);
+  if (p >= 3) {
+    // k = 2: x_2 from xa, x_1 = bhat/theta -> x_3 in xb
+    pi = prof_begin(h, step_class(1, 1, p == 3), step_bytes(1, 1, p == 3));
+    AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 1, 1, p == 3, cx, cy, cz, bhat, xa, xb, z, st[2], ia, s));
+    prof_end(h, pi);
+  }
+  for (int k = 3; k <= p - 1; ++k) {
+    // x_k in `cur`, x_{k-1} in `prev`; x_{k+1} overwrites x_{k-1}
+    T* cur = (k % 2 == 1) ? xb : xa;
+    T* prev = (k % 2 == 1) ? xa : xb;
+    const bool last = (k == p - 1);
+    pi = prof_begin(h, step_class(1, 2, last), step_bytes(1, 2, last));
+    AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 1, 2, last, cx, cy, cz, bhat, cur, prev, z, st[k], ia, s));
+    prof_end(h, pi);
+  }
+  return AAO_OK;
+}
+
+int precond(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  if (h->prec == AAO_MIXED)
+    return precond_impl<float>(h, r, rscale, z, h->steps32, h->dft32, h->idft32, h->cx32, h->cy32, h->cz32);
+  return precond_impl<double>(h, r, rscale, z, h->steps64, h->dft64, h->idft64, h->cx64, h->cy64, h->cz64);
+}
+
+int matvec(aao_ctx* h, const double* x, const double* b, double* y, int* nblocks) {
+  const double bytes = (double)h->N * (16.0 * h->ell + 8.0 * h->dim + (b ? 8.0 * h->ell : 0.0));
+  const int pi = prof_begin(h, AAO_PROF_MATVEC, bytes);
+  AAO_CK(h, aao::launch_aao_matvec(h->g, h->dim, h->ell, h->cx64, h->cy64, h->cz64, x, b, y, h->partials, nblocks,
+                                   h->stream));
+  prof_end(h, pi);
+  return AAO_OK;
+}
+
+int read_scalars(aao_ctx* h, int offset, int count, double* out) {
+  AAO_CK(h, cudaMemcpyAsync(h->pinned, h->sc + offset, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
+  AAO_CK(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < count; ++i) out[i] = h->pinned[i];
+  prof_resolve(h);
+  return AAO_OK;
+}
+
+int ensure_stage(aao_ctx* h) {
+  if (!h->stage_a) AAO_CK(h, cudaMalloc(&h->stage_a, sizeof(double) * h->L));
+  if (!h->stage_b) AAO_CK(h, cudaMalloc(&h->stage_b, sizeof(double) * h->L));
+  return AAO_OK;
+}
+
+// explicit ||b - script-A x||^2 into sc[nrm2] with r written to `r`; returns its value.
+int residual(aao_ctx* h, const double* b, const double* x, double* r, double* rn2) {
+  int nb = 0;
+  int rc = matvec(h, x, b, r, &nb);
+  if (rc) return rc;
+  const ScLayout Lsc{h->m};
+  AAO_CK(h, aao::launch_reduce(h->partials, 1, nb, h->sc + Lsc.nrm2(), 0, h->stream));
+  return read_scalars(h, Lsc.nrm2(), 1, rn2);
+}
+
+int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer, int fixed) {
+  const ScLayout Lsc{h->m};
+  const int64_t L = h->L;
+  cudaStream_t s = h->stream;
+  aao_stats& st = h->stats;
+  std::memset(&st, 0, sizeof(st));
+  st.mu_min = h->mu_min;
+  st.mu_max = h->mu_max;
+  const int64_t per_outer = (int64_t)h->ell * h->p + h->ell;
+
+  // ||b||
+  AAO_CK(h, aao::launch_norm2_partials(b, L, h->partials, s));
+  AAO_CK(h, aao::launch_reduce(h->partials, 1, aao::reduction_blocks(L), h->sc + Lsc.nrm2(), 0, s));
+  double bn2 = 0.0;
+  int rc = read_scalars(h, Lsc.nrm2(), 1, &bn2);
+  if (rc) return rc;
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) return fail(h, AAO_ENUMERIC, "||b|| is not finite");
+  if (bnorm == 0.0) {
+    AAO_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * L, s));
+    AAO_CK(h, cudaStreamSynchronize(s));
+    st.converged = 1;
+    return AAO_OK;
+  }
+  int total = 0;
+  const int m = fixed ? fixed : h->m;
+  while (true) {
+    double rn2 = 0.0;
+    rc = residual(h, b, x, h->V, &rn2);
+    if (rc) return rc;
+    st.a_matvecs += h->ell;
+    const double rel = std::sqrt(rn2) / bnorm;
+    st.resid_explicit = rel;
+    if (!std::isfinite(rel)) return fail(h, AAO_ENUMERIC, "residual is not finite");
+    if (fixed && st.cycles > 0) {
+      st.converged = rel < tol;
+      return AAO_OK;
+    }
+    if (!fixed && rel < tol) {
+      st.converged = 1;
+      return AAO_OK;
+    }
+    if (total >= max_outer) return fail(h, AAO_ENOTCONV, "no convergence in %d outer iterations (rel. residual %.3e)",
+                                        total, rel);
+    AAO_CK(h, aao::launch_cycle_init(h->sc, h->m, s));
+    st.cycles++;
+    const double beta = std::sqrt(rn2);
+    int k = 0;
+    for (int j = 0; j < m && total < max_outer; ++j) {
+      double* Vj = h->V + (int64_t)j * L;
+      double* Zj = h->Z + (int64_t)j * L;
+      double* w = h->V + (int64_t)(j + 1) * L;
+      rc = precond(h, Vj, h->sc + Lsc.vscale(j), Zj);
+      if (rc) return rc;
+      rc = matvec(h, Zj, nullptr, w, nullptr);
+      if (rc) return rc;
+      const int nv = j + 1;
+      const int nb = aao::reduction_blocks(L);
+      // Gram-Schmidt: algorithmic bytes = each V_i read once per pass plus w
+      const int ndot = (nv + 7) / 8;
+      const double dot_bytes = 8.0 * (double)L * (nv + ndot);
+      const double upd_bytes = 8.0 * (double)L * (nv + 2);
+      const int passes = h->reorth ? 2 : 1;
+      const int pi = prof_begin(h, AAO_PROF_ORTH, passes * (dot_bytes + upd_bytes), passes * (ndot + 2) + 1);
+      AAO_CK(h, aao::launch_multidot(h->V, L, nv, h->sc + Lsc.vscale(0), w, L, h->partials, s));
+      AAO_CK(h, aao::launch_reduce(h->partials, nv, nb, h->sc + Lsc.h1(0), 0, s));
+      double* normpart = h->partials + (int64_t)(h->m + 1) * nb;
+      if (h->reorth) {
+        AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h1(0), h->sc + Lsc.vscale(0), w, L, nullptr, s));
+        AAO_CK(h, aao::launch_multidot(h->V, L, nv, h->sc + Lsc.vscale(0), w, L, h->partials, s));
+        AAO_CK(h, aao::launch_reduce(h->partials, nv, nb, h->sc + Lsc.h2(0), 0, s));
+        AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h2(0), h->sc + Lsc.vscale(0), w, L, normpart, s));
+      } else {
+        AAO_CK(h, cudaMemsetAsync(h->sc + Lsc.h2(0), 0, sizeof(double) * nv, s));
+        AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h1(0), h->sc + Lsc.vscale(0), w, L, normpart, s));
+      }
+      AAO_CK(h, aao::launch_reduce(normpart, 1, nb, h->sc + Lsc.nrm2(), 0, s));
+      prof_end(h, pi);
+      AAO_CK(h, aao::launch_givens(h->sc, j, h->m, bnorm, s));
+      double eh[2];
+      rc = read_scalars(h, Lsc.est(), 2, eh);
+      if (rc) return rc;
+      k = j + 1;
+      total++;
+      st.outer_its = total;
+      st.a_matvecs += per_outer;
+      st.resid_est = eh[0];
+      if (st.n_hist < AAO_MAX_HIST) st.hist[st.n_hist++] = eh[0];
+      if (!std::isfinite(eh[0]) || !std::isfinite(eh[1]))
+        return fail(h, AAO_ENUMERIC, "non-finite value in Arnoldi step %d", total);
+      const bool breakdown = eh[1] <= 1e-14 * beta;
+      if (breakdown) break;
+      if (!fixed && eh[0] < tol) break;
+    }
+    AAO_CK(h, aao::launch_backsolve(h->sc, k, h->m, s));
+    AAO_CK(h, aao::launch_xupdate(h->Z, L, k, h->sc + Lsc.y(0), x, L, s));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void aao_default_options(aao_options* opt) {
+  if (!opt) return;
+  opt->prec = AAO_MIXED;
+  opt->inner_its = 20;
+  opt->restart = 64;
+  opt->reorth = 1;
+  opt->mu_max_override = 0.0;
+  opt->stream = nullptr;
+}
+
+const char* aao_last_create_error(void) { return g_create_error.c_str(); }
+
+const char* aao_last_error(aao_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int64_t aao_kernel_launch_count(void) { return (int64_t)aao::launch_count(); }
+
+void aao_destroy(aao_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  void* dev[] = {h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32, h->bhat, h->xa,      h->xb,
+                 h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  delete h;
+}
+
+int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, const double* ky, const double* kz,
+               int ell, double alpha, const aao_options* opt_in) {
+  if (!out) return fail(nullptr, AAO_EINVAL, "aao_create: handle pointer is NULL");
+  *out = nullptr;
+  aao_options opt;
+  aao_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (dim < 1 || dim > 3) return fail(nullptr, AAO_EINVAL, "dim must be 1, 2 or 3 (got %d)", dim);
+  if (!n) return fail(nullptr, AAO_EINVAL, "n is NULL");
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 1) return fail(nullptr, AAO_EINVAL, "n[%d] = %lld must be >= 1", d, (long long)n[d]);
+    if (d >= dim && n[d] != 1) return fail(nullptr, AAO_EINVAL, "n[%d] must be 1 for dim = %d", d, dim);
+  }
+  if (n[0] > 2000000000LL || n[1] > 8LL * 65535 || n[2] > 65535)
+    return fail(nullptr, AAO_EINVAL, "grid too large (n0 <= 2e9, n1 <= 524280, n2 <= 65535)");
+  if (n[0] > 1 && !kx) return fail(nullptr, AAO_EINVAL, "kx is NULL but n0 > 1");
+  if (n[1] > 1 && !ky) return fail(nullptr, AAO_EINVAL, "ky is NULL but n1 > 1");
+  if (n[2] > 1 && !kz) return fail(nullptr, AAO_EINVAL, "kz is NULL but n2 > 1");
+  if (ell < 4 || ell > AAO_MAX_ELL || (ell % 2) != 0)
+    return fail(nullptr, AAO_EINVAL, "ell must be even and in [4, %d] (got %d)", AAO_MAX_ELL, ell);
+  if (!(alpha > 0.0 && alpha < 1.0))
+    return fail(nullptr, AAO_EINVAL, "alpha must satisfy 0 < alpha < mu_min^ell = 1 (got %g)", alpha);
+  if (opt.prec != AAO_FP64 && opt.prec != AAO_MIXED) return fail(nullptr, AAO_EINVAL, "bad precision mode %d", opt.prec);
+  if (opt.inner_its < 1 || opt.inner_its > 100000) return fail(nullptr, AAO_EINVAL, "inner_its must be in [1, 100000]");
+  if (opt.restart < 1 || opt.restart > AAO_MAX_RESTART)
+    return fail(nullptr, AAO_EINVAL, "restart must be in [1, %d]", AAO_MAX_RESTART);
+  if (!(opt.mu_max_override >= 0.0) || !std::isfinite(opt.mu_max_override))
+    return fail(nullptr, AAO_EINVAL, "mu_max_override must be finite and >= 0");
+  if (opt.mu_max_override > 0.0 && opt.mu_max_override <= 1.0)
+    return fail(nullptr, AAO_EINVAL, "mu_max_override must exceed mu_min = 1");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(nullptr, AAO_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(ce));
+  }
+
+  aao_ctx* h = new aao_ctx();
+  h->dim = dim;
+  for (int d = 0; d < 3; ++d) h->n[d] = n[d];
+  h->N = n[0] * n[1] * n[2];
+  h->ell = ell;
+  h->L = (int64_t)ell * h->N;
+  h->alpha = alpha;
+  h->prec = opt.prec;
+  h->p = opt.inner_its;
+  h->m = opt.restart;
+  h->reorth = opt.reorth ? 1 : 0;
+  h->stream = (cudaStream_t)opt.stream;
+  h->g.n0 = (int)n[0];
+  h->g.n1 = (int)n[1];
+  h->g.n2 = (int)n[2];
+  h->g.N = h->N;
+
+  auto bail = [&](int code) {
+    g_create_error = h->err;
+    aao_destroy(h);
+    return code;
+  };
+#define AAO_CK_CREATE(call)                                                                          \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      fail(h, e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+      return bail(e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA);                         \
+    }                                                                                                \
+  } while (0)
+
+  const int64_t N = h->N;
+  const int64_t nfx = n[2] * n[1] * (n[0] - 1), nfy = n[2] * (n[1] - 1) * n[0], nfz = (n[2] - 1) * n[1] * n[0];
+  AAO_CK_CREATE(cudaMalloc(&h->cx64, sizeof(double) * N));
+  AAO_CK_CREATE(cudaMalloc(&h->cy64, sizeof(double) * N));
+  AAO_CK_CREATE(cudaMalloc(&h->cz64, sizeof(double) * N));
+  AAO_CK_CREATE(cudaMalloc(&h->cx32, sizeof(float) * N));
+  AAO_CK_CREATE(cudaMalloc(&h->cy32, sizeof(float) * N));
+  AAO_CK_CREATE(cudaMalloc(&h->cz32, sizeof(float) * N));
+  const int nbred = aao::reduction_blocks(h->L);
+  const int nbmv = (int)(((n[0] + 31) / 32) * ((n[1] + 7) / 8) * n[2]) + (int)((n[0] + 255) / 256);
+  const int nbcf = aao::build_coeff_blocks(N);
+  h->part_cap = std::max<int64_t>({(int64_t)(h->m + 2) * nbred, (int64_t)nbmv, (int64_t)nbcf}) + 64;
+  AAO_CK_CREATE(cudaMalloc(&h->partials, sizeof(double) * h->part_cap));
+  const ScLayout Lsc{h->m};
+  AAO_CK_CREATE(cudaMalloc(&h->sc, sizeof(double) * Lsc.size()));
+  AAO_CK_CREATE(cudaMemset(h->sc, 0, sizeof(double) * Lsc.size()));
+  AAO_CK_CREATE(cudaMallocHost(&h->pinned, sizeof(double) * 16));
+
+  // face arrays: device pointers are used in place, host arrays are staged
+  const double* fk[3] = {kx, ky, kz};
+  const int64_t fn[3] = {nfx, nfy, nfz};
+  double* tmp[3] = {nullptr, nullptr, nullptr};
+  const double* dk[3] = {nullptr, nullptr, nullptr};
+  for (int d = 0; d < 3; ++d) {
+    if (fn[d] == 0) continue;
+    if (is_device_ptr(fk[d])) {
+      dk[d] = fk[d];
+    } else {
+      cudaError_t e = cudaMalloc(&tmp[d], sizeof(double) * fn[d]);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tmp[d], fk[d], sizeof(double) * fn[d], cudaMemcpyHostToDevice, h->stream);
+      if (e != cudaSuccess) {
+        for (double* t : tmp)
+          if (t) cudaFree(t);
+        fail(h, AAO_ECUDA, "staging face array %d: %s", d, cudaGetErrorString(e));
+        return bail(e == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA);
+      }
+      dk[d] = tmp[d];
+    }
+  }
+  int* bad = nullptr;
+  cudaError_t e = cudaMalloc(&bad, sizeof(int) * 2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int) * 2, h->stream);
+  if (e == cudaSuccess)
+    e = aao::launch_build_coeffs(h->g, dk[0], dk[1], dk[2], h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32,
+                                 h->partials, bad, h->sc + Lsc.nrm2(), h->stream);
+  int hbad[2] = {0, 0};
+  double smax = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hbad, bad, sizeof(int) * 2, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&smax, h->sc + Lsc.nrm2(), sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  for (double* t : tmp)
+    if (t) cudaFree(t);
+  if (bad) cudaFree(bad);
+  if (e != cudaSuccess) {
+    fail(h, AAO_ECUDA, "coefficient set-up: %s", cudaGetErrorString(e));
+    return bail(AAO_ECUDA);
+  }
+  if (hbad[0]) {
+    fail(h, AAO_EINVAL, "face diffusivities must be finite and > 0");
+    return bail(AAO_EINVAL);
+  }
+  h->mu_min = 1.0;  // K annihilates constants and is PSD: lambda_min(I + K) = 1
+  h->mu_max = opt.mu_max_override > 0.0 ? opt.mu_max_override : 1.0 + 2.0 * smax;  // Gershgorin
+  if (!(h->mu_max >= h->mu_min)) h->mu_max = h->mu_min;
+
+  const size_t fsz = (h->prec == AAO_MIXED) ? sizeof(float) : sizeof(double);
+  AAO_CK_CREATE(cudaMalloc(&h->bhat, fsz * h->L));
+  AAO_CK_CREATE(cudaMalloc(&h->xa, fsz * h->L));
+  AAO_CK_CREATE(cudaMalloc(&h->xb, fsz * h->L));
+  AAO_CK_CREATE(cudaMalloc(&h->V, sizeof(double) * h->L * (h->m + 1)));
+  AAO_CK_CREATE(cudaMalloc(&h->Z, sizeof(double) * h->L * h->m));
+  build_tables(h);
+  *out = h;
+#undef AAO_CK_CREATE
+  return AAO_OK;
+}
+
+int aao_get_bounds(aao_handle h, double* mu_min, double* mu_max) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (mu_min) *mu_min = h->mu_min;
+  if (mu_max) *mu_max = h->mu_max;
+  return AAO_OK;
+}
+
+int aao_matvec(aao_handle h, const double* x, double* y) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (!x || !y || x == y) return fail(h, AAO_EINVAL, "aao_matvec: x and y must be distinct non-NULL pointers");
+  h->err.clear();
+  const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
+  int rc = (hx || hy) ? ensure_stage(h) : AAO_OK;
+  if (rc) return rc;
+  const double* dx = x;
+  double* dy = y;
+  if (hx) {
+    AAO_CK(h, cudaMemcpyAsync(h->stage_a, x, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
+    dx = h->stage_a;
+  }
+  if (hy) dy = h->stage_b;
+  rc = matvec(h, dx, nullptr, dy, nullptr);
+  if (rc) return rc;
+  if (hy) AAO_CK(h, cudaMemcpyAsync(y, dy, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
+  AAO_CK(h, cudaStreamSynchronize(h->stream));
+  return AAO_OK;
+}
+
+int aao_precond_apply(aao_handle h, const double* r, double* z) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (!r || !z || r == z) return fail(h, AAO_EINVAL, "aao_precond_apply: r and z must be distinct non-NULL pointers");
+  h->err.clear();
+  const bool hr = !is_device_ptr(r), hz = !is_device_ptr(z);
+  int rc = (hr || hz) ? ensure_stage(h) : AAO_OK;
+  if (rc) return rc;
+  const double* dr = r;
+  double* dz = z;
+  if (hr) {
+    AAO_CK(h, cudaMemcpyAsync(h->stage_a, r, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
+    dr = h->stage_a;
+  }
+  if (hz) dz = h->stage_b;
+  rc = precond(h, dr, nullptr, dz);
+  if (rc) return rc;
+  if (hz) AAO_CK(h, cudaMemcpyAsync(z, dz, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
+  AAO_CK(h, cudaStreamSynchronize(h->stream));
+  return AAO_OK;
+}
+
+static int solve_entry(aao_handle h, const double* b, double* x, double tol, int max_outer, int inner_its,
+                       int use_x0, int fixed) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  h->err.clear();
+  if (!b || !x || b == x) return fail(h, AAO_EINVAL, "b and x must be distinct non-NULL pointers");
+  if (!fixed && !(tol > 0.0 && tol < 1.0)) return fail(h, AAO_EINVAL, "tol must be in (0, 1)");
+  if (max_outer < 1) return fail(h, AAO_EINVAL, "max_outer must be >= 1");
+  if (fixed && fixed > h->m) return fail(h, AAO_EINVAL, "fixed step count %d exceeds restart %d", fixed, h->m);
+  if (inner_its < 0 || inner_its > 100000) return fail(h, AAO_EINVAL, "inner_its must be in [0, 100000]");
+  if (inner_its > 0 && inner_its != h->p) {
+    h->p = inner_its;
+    build_tables(h);
+  }
+  const bool hb = !is_device_ptr(b), hx = !is_device_ptr(x);
+  int rc = (hb || hx) ? ensure_stage(h) : AAO_OK;
+  if (rc) return rc;
+  const double* db = b;
+  double* dx = x;
+  if (hb) {
+    AAO_CK(h, cudaMemcpyAsync(h->stage_a, b, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
+    db = h->stage_a;
+  }
+  if (hx) {
+    dx = h->stage_b;
+    if (use_x0) AAO_CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
+  }
+  if (!use_x0) AAO_CK(h, cudaMemsetAsync(dx, 0, sizeof(double) * h->L, h->stream));
+  rc = solve_impl(h, db, dx, fixed ? 1.0 : tol, fixed ? fixed : max_outer, fixed);
+  if (hx && (rc == AAO_OK || rc == AAO_ENOTCONV)) {
+    cudaError_t e = cudaMemcpyAsync(x, dx, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, AAO_ECUDA, "copy of x to host: %s", cudaGetErrorString(e));
+  }
+  if (rc == AAO_OK || rc == AAO_ENOTCONV) AAO_CK(h, cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int aao_solve(aao_handle h, const double* b, double* x, double tol, int max_outer, int inner_its, int use_x0) {
+  return solve_entry(h, b, x, tol, max_outer, inner_its, use_x0, 0);
+}
+
+int aao_solve_fixed(aao_handle h, const double* b, double* x, int k, int inner_its) {
+  if (k < 1) return fail(h, AAO_EINVAL, "k must be >= 1");
+  return solve_entry(h, b, x, 0.5, k, inner_its, 0, k);
+}
+
+int aao_profile_enable(aao_handle h, int on) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  AAO_CK(h, cudaStreamSynchronize(h->stream));
+  h->pending.clear();
+  h->profacc = aao_profile{};
+  h->prof = on != 0;
+  return AAO_OK;
+}
+
+int aao_profile_get(aao_handle h, aao_profile* out) {
+  if (!h || !out) return fail(h, AAO_EINVAL, "NULL argument");
+  AAO_CK(h, cudaStreamSynchronize(h->stream));
+  prof_resolve(h);
+  *out = h->profacc;
+  return AAO_OK;
+}
+
+int aao_get_stats(aao_handle h, aao_stats* s) {
+  if (!h || !s) return fail(h, AAO_EINVAL, "NULL argument");
+  *s = h->stats;
+  return AAO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// Internal declarations shared by the CUDA translation units of libaao.
+//
+// Device data layouts:
+//  * FP64 block vectors (b, x, Krylov V and Z): ell planes of N doubles
+//    ("block-major", Eq. 1), cell c = i + n0*(j + n1*k).
+//  * Chebyshev fields (bhat, x_k, x_{k-1}): ell planes of N values of type T
+//    (float in the mixed path, double in the FP64 path).  The ell/2+1
+//    frequencies that are distinct for real input pack into exactly ell
+//    planes: plane 0 = Re f_0, plane 1 = Re f_{ell/2}, planes 2m and 2m+1 =
+//    Re and Im of f_m for m = 1 .. ell/2-1 (f_0 and f_{ell/2} are real).
+//  * Face diffusivities per cell: cx[c] = kappa of the face between c and its
+//    +x neighbour (0 on the last column), likewise cy, cz.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aao {
+
+constexpr int kMaxEll = 16;
+constexpr int kMaxF = kMaxEll / 2 + 1;
+constexpr int kMaxRestart = 64;
+
+struct GridDesc {
+  int n0, n1, n2;
+  int64_t N;
+};
+
+// Coefficients of one Chebyshev step k (producing x_{k+1}) for every
+// frequency m = 0 .. ell/2 (indexing: m, not the packed plane):
+//   x_{k+1} = x_k + a (x_k - x_{k-1}) + g (bhat - A x_k + lambda x_k)
+// with a = rho_k rho_{k-1}, g = 2 rho_k / delta, and itheta = 1/theta (x_1 = bhat/theta).
+template <typename T>
+struct StepArgs {
+  T lam_re[kMaxF], lam_im[kMaxF];
+  T a_re[kMaxF], a_im[kMaxF];
+  T g_re[kMaxF], g_im[kMaxF];
+  T it_re[kMaxF], it_im[kMaxF];
+};
+
+// Forward transform: s_t = gamma_t * scale * r_t (FP64), then
+//   Re f_m = sum_t s_t cf[t][m],  Im f_m = -sum_t s_t sf[t][m]
+// with cf = cos(2 pi t m/ell)/sqrt(ell), sf = sin(2 pi t m/ell)/sqrt(ell).
+template <typename T>
+struct DftArgs {
+  double gamma[kMaxEll];
+  T cf[kMaxEll][kMaxF];
+  T sf[kMaxEll][kMaxF];
+};
+
+// Inverse transform of the ell/2+1 distinct frequencies y_m (real signal):
+//   z_t = igamma_t * sum_m (Re y_m ci[t][m] - Im y_m si[t][m])
+// with ci[t][0] = 1/sqrt(ell), ci[t][ell/2] = (-1)^t/sqrt(ell),
+// ci[t][m] = 2 cos(2 pi t m/ell)/sqrt(ell), si[t][m] = 2 sin(.)/sqrt(ell).
+template <typename T>
+struct IdftArgs {
+  double igamma[kMaxEll];
+  T ci[kMaxEll][kMaxF];
+  T si[kMaxEll][kMaxF];
+};
+
+// Modes of the Chebyshev step kernel.
+//  KSRC: where x_k comes from: 0 = x_1 = bhat/theta (step k = 1), 1 = buffer.
+//  PSRC: where x_{k-1} comes from: 0 = zero (k = 1), 1 = bhat/theta (k = 2), 2 = buffer.
+//  LAST: write x_{k+1} to the field buffer (false) or inverse-transform it to z (true).
+
+// Launchers (one per precision; dispatch on ell and dim inside).  All return
+// cudaSuccess or the launch error.  Every launch adds 1 to the launch counter.
+template <typename T>
+cudaError_t launch_dft(const GridDesc& g, int dim, int ell, const double* r, const double* rscale,
+                       T* bhat, const DftArgs<T>& da, cudaStream_t s);
+template <typename T>
+cudaError_t launch_direct(const GridDesc& g, int dim, int ell, const double* r, const double* rscale,
+                          double* z, const DftArgs<T>& da, const StepArgs<T>& sa,
+                          const IdftArgs<T>& ia, cudaStream_t s);
+template <typename T>
+cudaError_t launch_step(const GridDesc& g, int dim, int ell, int ksrc, int psrc, bool last,
+                        const T* cx, const T* cy, const T* cz, const T* bhat, const T* xk, T* xio,
+                        double* z, const StepArgs<T>& sa, const IdftArgs<T>& ia, cudaStream_t s);
+
+// FP64 Krylov kernels (krylov.cu).
+// y = script-A x (mode 0) or y = b - script-A x with per-block partial sums of y^2 (mode 1).
+cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,
+                              const double* cz, const double* x, const double* b, double* y,
+                              double* partials, int* nblocks_out, cudaStream_t s);
+// Number of blocks the flat-vector reductions use for length L (depends on L only).
+int reduction_blocks(int64_t L);
+// partials[i*NB + blk] = vscale[i] * sum over the block's slice of V_i . w, i < nv.
+cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* vscale, const double* w,
+                            int64_t L, double* partials, cudaStream_t s);
+// w -= sum_i (h[i] * vscale[i]) V_i for i < nv; optional per-block partial sums of w^2.
+cudaError_t launch_orth_update(const double* V, int64_t ldv, int nv, const double* h, const double* vscale,
+                               double* w, int64_t L, double* partials_norm, cudaStream_t s);
+// partial sums of v^2 per block.
+cudaError_t launch_norm2_partials(const double* v, int64_t L, double* partials, cudaStream_t s);
+// out[i] (+)= sum_b partials[i*NB + b] for i < nv, fixed order (deterministic).
+cudaError_t launch_reduce(const double* partials, int nv, int nb, double* out, int accumulate,
+                          cudaStream_t s);
+// One Arnoldi column: combine h1 + h2, the new norm, rotations, residual estimate.
+cudaError_t launch_givens(double* sc, int j, int m, double bnorm, cudaStream_t s);
+// y = R^{-1} g for the first k columns; x += sum y_i Z_i.
+cudaError_t launch_backsolve(double* sc, int k, int m, cudaStream_t s);
+cudaError_t launch_xupdate(const double* Z, int64_t ldz, int k, const double* y, double* x, int64_t L,
+                           cudaStream_t s);
+// Starting vector of a cycle: sc[vscale 0] = 1/sqrt(nrm2), g[0] = sqrt(nrm2), clears H/g.
+cudaError_t launch_cycle_init(double* sc, int m, cudaStream_t s);
+
+// Layout of the small FP64 scalar block `sc` (device), m = restart length.
+struct ScLayout {
+  int m;
+  __host__ __device__ int H(int i, int j) const { return i * m + j; }          // (m+1) x m
+  __host__ __device__ int cs(int i) const { return (m + 1) * m + i; }
+  __host__ __device__ int sn(int i) const { return (m + 1) * m + m + i; }
+  __host__ __device__ int gv(int i) const { return (m + 1) * m + 2 * m + i; }  // m+1
+  __host__ __device__ int y(int i) const { return (m + 1) * m + 3 * m + 1 + i; }
+  __host__ __device__ int vscale(int i) const { return (m + 1) * m + 4 * m + 1 + i; }  // m+1
+  __host__ __device__ int h1(int i) const { return (m + 1) * m + 5 * m + 2 + i; }      // m+1
+  __host__ __device__ int h2(int i) const { return (m + 1) * m + 6 * m + 3 + i; }      // m+1
+  __host__ __device__ int nrm2() const { return (m + 1) * m + 7 * m + 4; }
+  __host__ __device__ int est() const { return (m + 1) * m + 7 * m + 5; }
+  __host__ __device__ int hnext() const { return (m + 1) * m + 7 * m + 6; }
+  __host__ __device__ int size() const { return (m + 1) * m + 7 * m + 8; }
+};
+
+void count_launch();
+
+}  // namespace aao

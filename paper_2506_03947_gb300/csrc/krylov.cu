@@ -1,0 +1,349 @@
+// FP64 kernels of the outer solve: the all-at-once matvec (Eq. 1), the
+// Gram-Schmidt reductions and updates of FGMRES, Givens rotations, the
+// triangular solve and the solution update.
+//
+// Reductions are deterministic: every flat-vector reduction uses a block count
+// that depends on the vector length only, writes one partial sum per block,
+// and a second kernel adds the partials in a fixed order.
+#include "aao_internal.cuh"
+
+#include <atomic>
+
+namespace aao {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+constexpr int kRedThreads = 256;
+constexpr int kRedWarps = kRedThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread gets the result.  `sh` holds kRedWarps doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int lane = tid & 31, warp = tid >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kRedWarps; ++w) t += sh[w];  // fixed order
+  return t;
+}
+
+// ---- script-A matvec --------------------------------------------------------
+
+// y_t = A x_t - x_{t-1} (MODE 0) or y_t = b_t - (A x_t - x_{t-1}) (MODE 1), for all
+// t at one cell per thread; A = I + K with per-cell face coefficients.  MODE 1
+// also writes one partial sum of y^2 per block.
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(256)
+    k_aao_matvec(GridDesc g, int ell, const double* __restrict__ cx, const double* __restrict__ cy,
+                 const double* __restrict__ cz, const double* __restrict__ x, const double* __restrict__ b,
+                 double* __restrict__ y, double* __restrict__ partials) {
+  __shared__ double sh[kRedWarps];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double acc2 = 0.0;
+  if (i < g.n0 && j < g.n1) {
+    const int64_t N = g.N;
+    const int64_t c = i + (int64_t)g.n0 * (j + (int64_t)g.n1 * k);
+    double kap[2 * DIM];
+    int64_t nb[2 * DIM];
+    kap[0] = __ldg(cx + c);
+    kap[1] = (i > 0) ? __ldg(cx + c - 1) : 0.0;
+    nb[0] = (i < g.n0 - 1) ? c + 1 : c;
+    nb[1] = (i > 0) ? c - 1 : c;
+    if constexpr (DIM >= 2) {
+      kap[2] = __ldg(cy + c);
+      kap[3] = (j > 0) ? __ldg(cy + c - g.n0) : 0.0;
+      nb[2] = (j < g.n1 - 1) ? c + g.n0 : c;
+      nb[3] = (j > 0) ? c - g.n0 : c;
+    }
+    if constexpr (DIM == 3) {
+      const int64_t pl = (int64_t)g.n0 * g.n1;
+      kap[4] = __ldg(cz + c);
+      kap[5] = (k > 0) ? __ldg(cz + c - pl) : 0.0;
+      nb[4] = (k < g.n2 - 1) ? c + pl : c;
+      nb[5] = (k > 0) ? c - pl : c;
+    }
+    double prev = 0.0;
+    for (int t = 0; t < ell; ++t) {
+      const double* xt = x + (int64_t)t * N;
+      const double xc = __ldg(xt + c);
+      double a = xc;
+#pragma unroll
+      for (int q = 0; q < 2 * DIM; ++q) a += kap[q] * (xc - __ldg(xt + nb[q]));
+      double v = a - prev;
+      prev = xc;
+      if constexpr (MODE == 1) {
+        v = __ldg(b + (int64_t)t * N + c) - v;
+        acc2 += v * v;
+      }
+      y[(int64_t)t * N + c] = v;
+    }
+  }
+  if constexpr (MODE == 1) {
+    const double s = block_sum(acc2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+      partials[blk] = s;
+    }
+  }
+}
+
+cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,
+                              const double* cz, const double* x, const double* b, double* y, double* partials,
+                              int* nblocks_out, cudaStream_t s) {
+  dim3 block, grid;
+  if (dim == 1) {
+    block = dim3(256, 1, 1);
+    grid = dim3((unsigned)((g.n0 + 255) / 256), 1, 1);
+  } else {
+    block = dim3(32, 8, 1);
+    grid = dim3((unsigned)((g.n0 + 31) / 32), (unsigned)((g.n1 + 7) / 8), (unsigned)g.n2);
+  }
+  if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+  const int mode = (b != nullptr) ? 1 : 0;
+#define AAO_MV(D, M) k_aao_matvec<D, M><<<grid, block, 0, s>>>(g, ell, cx, cy, cz, x, b, y, partials)
+  switch (dim * 10 + mode) {
+    case 10: AAO_MV(1, 0); break;
+    case 11: AAO_MV(1, 1); break;
+    case 20: AAO_MV(2, 0); break;
+    case 21: AAO_MV(2, 1); break;
+    case 30: AAO_MV(3, 0); break;
+    case 31: AAO_MV(3, 1); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef AAO_MV
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---- flat-vector reductions ---------------------------------------------------
+
+int reduction_blocks(int64_t L) {
+  // about 8 elements per thread at least, at most 1216 blocks (8 per SM on 152 SMs)
+  int64_t nb = (L + (int64_t)kRedThreads * 8 - 1) / ((int64_t)kRedThreads * 8);
+  if (nb < 1) nb = 1;
+  if (nb > 1216) nb = 1216;
+  return (int)nb;
+}
+
+constexpr int kDotGroup = 8;  // dot products accumulated per pass over w
+
+// partials[i*NB + blk] = vscale[i] * sum_{e in block slice} V_i[e] w[e], for i in [i0, i0+G).
+template <int G>
+__global__ void __launch_bounds__(kRedThreads)
+    k_multidot(const double* __restrict__ V, int64_t ldv, int i0, int nv, const double* __restrict__ vscale,
+               const double* __restrict__ w, int64_t L, double* __restrict__ partials) {
+  __shared__ double sh[G][kRedWarps];
+  double acc[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) acc[q] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    const double we = __ldg(w + e);
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if (i0 + q < nv) acc[q] += __ldg(V + (int64_t)(i0 + q) * ldv + e) * we;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    const double v = warp_sum(acc[q]);
+    if (lane == 0) sh[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < G && i0 + (int)threadIdx.x < nv) {
+    const int q = threadIdx.x;
+    double t = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < kRedWarps; ++w2) t += sh[q][w2];
+    const double scl = vscale ? vscale[i0 + q] : 1.0;
+    partials[(int64_t)(i0 + q) * gridDim.x + blockIdx.x] = t * scl;
+  }
+}
+
+cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* vscale, const double* w,
+                            int64_t L, double* partials, cudaStream_t s) {
+  const int nb = reduction_blocks(L);
+  for (int i0 = 0; i0 < nv; i0 += kDotGroup) {
+    k_multidot<kDotGroup><<<nb, kRedThreads, 0, s>>>(V, ldv, i0, nv, vscale, w, L, partials);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+// w[e] -= sum_i h[i] vscale[i] V_i[e]; optional per-block partial sums of the new w^2.
+__global__ void __launch_bounds__(kRedThreads)
+    k_orth_update(const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ h,
+                  const double* __restrict__ vscale, double* __restrict__ w, int64_t L,
+                  double* __restrict__ partials) {
+  __shared__ double coef[kMaxRestart + 1];
+  __shared__ double sh[kRedWarps];
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) coef[q] = h[q] * (vscale ? vscale[q] : 1.0);
+  __syncthreads();
+  double acc2 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    double v = w[e];
+    for (int q = 0; q < nv; ++q) v -= coef[q] * __ldg(V + (int64_t)q * ldv + e);
+    w[e] = v;
+    acc2 += v * v;
+  }
+  if (partials) {
+    const double t = block_sum(acc2, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_orth_update(const double* V, int64_t ldv, int nv, const double* h, const double* vscale,
+                               double* w, int64_t L, double* partials_norm, cudaStream_t s) {
+  const int nb = reduction_blocks(L);
+  k_orth_update<<<nb, kRedThreads, 0, s>>>(V, ldv, nv, h, vscale, w, L, partials_norm);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_norm2_partials(const double* __restrict__ v, int64_t L, double* __restrict__ partials) {
+  __shared__ double sh[kRedWarps];
+  double acc2 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    const double a = __ldg(v + e);
+    acc2 += a * a;
+  }
+  const double t = block_sum(acc2, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+cudaError_t launch_norm2_partials(const double* v, int64_t L, double* partials, cudaStream_t s) {
+  k_norm2_partials<<<reduction_blocks(L), kRedThreads, 0, s>>>(v, L, partials);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// out[i] (+)= sum_b partials[i*nb + b]: one block per i, fixed summation order.
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce(const double* __restrict__ partials, int nb, double* __restrict__ out, int accumulate) {
+  __shared__ double sh[kRedWarps];
+  const int i = blockIdx.x;
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += partials[(int64_t)i * nb + b];
+  const double t = block_sum(a, sh);
+  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + t : t;
+}
+
+cudaError_t launch_reduce(const double* partials, int nv, int nb, double* out, int accumulate, cudaStream_t s) {
+  if (nv <= 0) return cudaSuccess;
+  k_reduce<<<nv, kRedThreads, 0, s>>>(partials, nb, out, accumulate);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---- small dense FGMRES steps (one thread; sizes <= kMaxRestart) ---------------
+
+// Column j of the Hessenberg matrix: H[i][j] = h1[i] + h2[i] (i <= j), H[j+1][j] = sqrt(nrm2);
+// apply the stored rotations, build the new one, update g, and record the
+// relative residual estimate |g[j+1]| / bnorm.  vscale[j+1] = 1/H[j+1][j].
+__global__ void k_givens(double* sc, int j, int m, double bnorm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const ScLayout L{m};
+  for (int i = 0; i <= j; ++i) sc[L.H(i, j)] = sc[L.h1(i)] + sc[L.h2(i)];
+  const double hn = sqrt(sc[L.nrm2()]);
+  sc[L.hnext()] = hn;
+  sc[L.vscale(j + 1)] = (hn > 0.0) ? 1.0 / hn : 0.0;
+  const double hj1 = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = sc[L.H(i, j)], b = sc[L.H(i + 1, j)];
+    sc[L.H(i, j)] = sc[L.cs(i)] * a + sc[L.sn(i)] * b;
+    sc[L.H(i + 1, j)] = -sc[L.sn(i)] * a + sc[L.cs(i)] * b;
+  }
+  const double hjj = sc[L.H(j, j)];
+  const double r = hypot(hjj, hj1);
+  double c = 1.0, s = 0.0;
+  if (r != 0.0) {
+    c = hjj / r;
+    s = hj1 / r;
+  }
+  sc[L.cs(j)] = c;
+  sc[L.sn(j)] = s;
+  sc[L.H(j, j)] = r;
+  sc[L.H(j + 1, j)] = 0.0;
+  const double gj = sc[L.gv(j)];
+  sc[L.gv(j + 1)] = -s * gj;
+  sc[L.gv(j)] = c * gj;
+  sc[L.est()] = fabs(sc[L.gv(j + 1)]) / bnorm;
+}
+
+cudaError_t launch_givens(double* sc, int j, int m, double bnorm, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(sc, j, m, bnorm);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_backsolve(double* sc, int k, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const ScLayout L{m};
+  for (int i = k - 1; i >= 0; --i) {
+    double v = sc[L.gv(i)];
+    for (int q = i + 1; q < k; ++q) v -= sc[L.H(i, q)] * sc[L.y(q)];
+    sc[L.y(i)] = v / sc[L.H(i, i)];
+  }
+}
+
+cudaError_t launch_backsolve(double* sc, int k, int m, cudaStream_t s) {
+  k_backsolve<<<1, 32, 0, s>>>(sc, k, m);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_xupdate(const double* __restrict__ Z, int64_t ldz, int k, const double* __restrict__ y,
+              double* __restrict__ x, int64_t L) {
+  __shared__ double coef[kMaxRestart];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) coef[q] = y[q];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    double v = x[e];
+    for (int q = 0; q < k; ++q) v += coef[q] * __ldg(Z + (int64_t)q * ldz + e);
+    x[e] = v;
+  }
+}
+
+cudaError_t launch_xupdate(const double* Z, int64_t ldz, int k, const double* y, double* x, int64_t L,
+                           cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_xupdate<<<reduction_blocks(L), kRedThreads, 0, s>>>(Z, ldz, k, y, x, L);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Start of a cycle: beta = sqrt(nrm2); g = (beta, 0, ..); vscale[0] = 1/beta.
+__global__ void k_cycle_init(double* sc, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const ScLayout L{m};
+  const double beta = sqrt(sc[L.nrm2()]);
+  for (int i = 0; i <= m; ++i) sc[L.gv(i)] = 0.0;
+  sc[L.gv(0)] = beta;
+  sc[L.vscale(0)] = (beta > 0.0) ? 1.0 / beta : 0.0;
+}
+
+cudaError_t launch_cycle_init(double* sc, int m, cudaStream_t s) {
+  k_cycle_init<<<1, 32, 0, s>>>(sc, m);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace aao

@@ -1,0 +1,84 @@
+"""Helpers for the GPU parity tests: build/load the CUDA library, make solvers,
+wrap the oracle for a Problem, and compute derived tolerances."""
+import json
+import os
+
+import numpy as np
+
+U64 = np.finfo(np.float64).eps / 2     # unit roundoff, FP64
+U32 = np.finfo(np.float32).eps / 2     # unit roundoff, FP32
+
+
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        import pytest
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def ensure_lib():
+    from paper_2506_03947_gb300 import build
+    build.build()
+    from paper_2506_03947_gb300 import binding
+    binding.load_library()
+    return binding
+
+
+def faces_or_none(a):
+    return a.ravel() if a.size else None
+
+
+def make_solver(P, prec, p, restart=64, mu_max_override=0.0, device_faces=True):
+    torch = torch_cuda()
+    binding = ensure_lib()
+    fk = []
+    for a in (P.kx, P.ky, P.kz):
+        if a.size == 0:
+            fk.append(None)
+        elif device_faces:
+            fk.append(torch.from_numpy(np.ascontiguousarray(a.ravel())).cuda())
+        else:
+            fk.append(np.ascontiguousarray(a.ravel()))
+    s = binding.Solver(P.dim, P.n, fk[0], fk[1], fk[2], P.ell, P.alpha, prec=prec, inner_its=p,
+                       restart=restart, mu_max_override=mu_max_override,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    s._faces = fk   # keep device copies alive
+    return s
+
+
+def to_dev(a):
+    torch = torch_cuda()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def oracle_ops(P):
+    from oracle import allatonce, operator, precond
+    from oracle.solve import make_block_op
+    A = make_block_op(P.kx, P.ky, P.kz, P.shape)
+    mu_max = operator.gershgorin_mu_max(P.kx, P.ky, P.kz, P.shape)
+    return A, mu_max
+
+
+def precond_tol(prec, p, ell, alpha):
+    """Bound on max|z_gpu - z_oracle| / max|z| for one preconditioner apply.
+
+    Rounding model: a Chebyshev step forms A x_k from differences of
+    neighbours (relative error about mu_max u) but multiplies that residual by
+    g_k = 2 rho_k / delta, about 2/mu_max, so each step adds an error of a few
+    units of roundoff relative to |x|; Chebyshev semi-iteration propagates
+    such errors with at most linear growth in the step count.  The inverse
+    transform mixes all frequencies and the unscaling Gamma^{-1} multiplies
+    block t by alpha^{-t/ell}, at most alpha^{-(ell-1)/ell}.  With c = 16 for
+    the operations per step and the transforms:
+        tol = 16 (p + 2) u alpha^{-(ell-1)/ell}.
+    """
+    u = U32 if prec == 1 else U64
+    return 16.0 * (max(p, 1) + 2) * u * alpha ** (-(ell - 1) / ell)
+
+
+def log_record(rec):
+    path = os.environ.get("AAO_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")

@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI: the library builds, loads and exports what include/aao.h declares."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "aao.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(aao_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_03947_gb300 import build
+    build.build()
+    from paper_2506_03947_gb300 import binding
+    return binding.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("aao_create", "aao_matvec", "aao_precond_apply", "aao_solve", "aao_get_stats",
+                     "aao_last_error", "aao_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2506_03947_gb300 import binding
+    names = _declared_functions()
+    assert sorted(binding.EXPORTED) == names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
+
+
+def test_default_options(lib):
+    from paper_2506_03947_gb300 import binding
+    o = binding.aao_default_options()
+    assert (o.prec, o.inner_its, o.restart, o.reorth) == (binding.AAO_MIXED, 20, 64, 1)
+    assert o.mu_max_override == 0.0
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    from paper_2506_03947_gb300 import binding
+    kx = np.ones(7)
+    for kwargs, frag in (({"ell": 5}, "ell"), ({"ell": 18}, "ell"), ({"alpha": 1.0}, "alpha"),
+                         ({"alpha": 0.0}, "alpha"), ({"dim": 4}, "dim")):
+        args = dict(dim=1, n=(8, 1, 1), kx=kx, ky=None, kz=None, ell=10, alpha=1e-2)
+        args.update(kwargs)
+        with pytest.raises(binding.AaoError) as ei:
+            binding.aao_create(**args)
+        assert ei.value.status == binding.AAO_EINVAL
+        assert frag in str(ei.value)
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_create(2, (4, 4, 1), np.ones(12), None, None, 10, 1e-2)
+    assert "ky" in str(ei.value)
+
+
+def test_no_gpu_means_loud_failure(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2506_03947_gb300 import binding
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_create(1, (8, 1, 1), np.ones(7), None, None, 10, 1e-2)
+    assert ei.value.status == binding.AAO_ECUDA

@@ -1,0 +1,173 @@
+"""GPU solves (aao_solve) against the oracle.
+
+* FP64 path, fixed number of Arnoldi steps: the GPU iterate matches the
+  oracle's FGMRES iterate after the same steps to relative 1e-10.
+* FP64 path, converged: solution error vs the oracle <= 1e-10 (config 1 with
+  tol 1e-10; dense LU reference at ell*N = 2560).
+* Mixed path: explicit residual (recomputed by the oracle) <= tol, solution
+  error vs the oracle's exact solution <= 1e-7, outer iterations <= FP64 + 2.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import log_record, make_solver, to_dev, torch_cuda
+from oracle import allatonce, exact, operator, solve
+from paper_2506_03947_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _explicit_residual(P, x):
+    A = solve.make_block_op(P.kx, P.ky, P.kz, P.shape)
+    r = P.b - allatonce.aao_apply(A, x)
+    return np.linalg.norm(r) / np.linalg.norm(P.b)
+
+
+def _exact(P):
+    if P.N <= 4096:
+        return exact.sequential_solve_dense(operator.fv_dense(P.kx, P.ky, P.kz, P.shape), P.b)
+    A = operator.fv_sparse(P.kx, P.ky, P.kz, P.shape)
+    return exact.sequential_solve_cg(lambda v: A @ v, P.b)
+
+
+def _gpu_solve(P, prec, p, tol, max_outer=64, restart=64, fixed=None):
+    torch = torch_cuda()
+    s = make_solver(P, prec, p, restart=restart)
+    bd = to_dev(P.b)
+    xd = torch.zeros_like(bd)
+    if fixed:
+        s.solve_fixed(bd, xd, fixed)
+    else:
+        s.solve(bd, xd, tol, max_outer)
+    return xd.cpu().numpy(), s.stats()
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+@pytest.mark.parametrize("name,mk,p", [
+    ("2d_32x32_l10", lambda: inputs.config_2d(n=32), 10),
+    ("3d_9x7x5_l6", lambda: inputs.make_problem("c", 3, (9, 7, 5), 6, 1e-2, 1, 0.7, (8.0, 8.0, 4.0), 1, 2), 7),
+    ("1d_n256_l10", lambda: inputs.config_1d(), 20),
+])
+def test_fp64_fixed_steps_match_oracle(name, mk, p, k):
+    P = mk()
+    ref = solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, k, fixed_its=k)
+    x, st = _gpu_solve(P, 0, p, 1.0, fixed=k)
+    err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    log_record({"test": "fixed", "case": name, "k": k, "err": err})
+    assert st["outer_its"] == k
+    assert err <= 1e-10, err
+    # Givens estimates agree with the oracle's step by step
+    np.testing.assert_allclose(st["hist"], ref.history, rtol=1e-7)
+
+
+def test_config1_fp64_converged():
+    # 1D N = 256, ell = 10, alpha = 1e-2, p = 20, GMRES to 1e-10 (dense check at ell*N = 2560)
+    P = inputs.config_1d()
+    x, st = _gpu_solve(P, 0, 20, 1e-10)
+    ref = solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, 20, 1e-10, 64)
+    xe = _exact(P)
+    assert st["converged"] and st["resid_explicit"] < 1e-10
+    assert st["outer_its"] == ref.outer_its
+    assert _explicit_residual(P, x) < 1e-10
+    e_oracle = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    e_exact = np.linalg.norm(x - xe) / np.linalg.norm(xe)
+    log_record({"test": "config1", "e_oracle": e_oracle, "e_exact": e_exact, "its": st["outer_its"]})
+    assert e_oracle <= 1e-10
+    assert e_exact <= 1e-9
+
+
+@pytest.mark.parametrize("alpha", [1e-1, 1e-2, 1e-3])
+@pytest.mark.parametrize("p", [10, 20, 40])
+def test_mixed_vs_fp64_2d_small(alpha, p):
+    P = inputs.config_2d(n=64, alpha=alpha)
+    xe = _exact(P)
+    x64, s64 = _gpu_solve(P, 0, p, 1e-8)
+    x32, s32 = _gpu_solve(P, 1, p, 1e-8)
+    for x, st in ((x64, s64), (x32, s32)):
+        assert st["converged"]
+        assert _explicit_residual(P, x) <= 1e-8
+    e64 = np.linalg.norm(x64 - xe) / np.linalg.norm(xe)
+    e32 = np.linalg.norm(x32 - xe) / np.linalg.norm(xe)
+    log_record({"test": "mixed_small", "alpha": alpha, "p": p, "its64": s64["outer_its"],
+                "its32": s32["outer_its"], "e64": e64, "e32": e32})
+    assert s32["outer_its"] <= s64["outer_its"] + 2
+    assert e32 <= 1e-7 and e64 <= 1e-7
+
+
+@pytest.mark.parametrize("alpha", [1e-1, 1e-2, 1e-3])
+def test_config2_full_size_fp64_and_mixed(alpha):
+    # 2D 256 x 256 (N = 65536), ell = 10, p = 20, tol 1e-8
+    P = inputs.config_2d(alpha=alpha)
+    xe = _exact(P)
+    ref = solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, 20, 1e-8, 64)
+    x64, s64 = _gpu_solve(P, 0, 20, 1e-8)
+    x32, s32 = _gpu_solve(P, 1, 20, 1e-8)
+    e64_or = np.linalg.norm(x64 - ref.x) / np.linalg.norm(ref.x)
+    e32_ex = np.linalg.norm(x32 - xe) / np.linalg.norm(xe)
+    e32_or = np.linalg.norm(x32 - ref.x) / np.linalg.norm(ref.x)
+    log_record({"test": "config2", "alpha": alpha, "its_oracle": ref.outer_its, "its64": s64["outer_its"],
+                "its32": s32["outer_its"], "e64_oracle": e64_or, "e32_exact": e32_ex, "e32_oracle": e32_or})
+    assert s64["outer_its"] == ref.outer_its
+    assert e64_or <= 1e-10
+    assert _explicit_residual(P, x32) <= 1e-8
+    assert s32["outer_its"] <= s64["outer_its"] + 2
+    assert e32_ex <= 1e-7 and e32_or <= 1e-7
+
+
+def test_restarted_solve_and_host_buffers():
+    torch = torch_cuda()
+    P = inputs.config_2d(n=48)
+    s = make_solver(P, 1, 10, restart=6)
+    x = np.zeros_like(P.b)
+    s.solve(P.b, x, 1e-8, 300)                   # host (numpy) b and x
+    st = s.stats()
+    assert st["converged"] and st["cycles"] > 1
+    assert _explicit_residual(P, x) <= 1e-8
+    # same solve on device buffers gives the same bits
+    bd = to_dev(P.b)
+    xd = torch.zeros_like(bd)
+    s.solve(bd, xd, 1e-8, 300)
+    np.testing.assert_array_equal(xd.cpu().numpy(), x)
+
+
+def test_initial_guess_and_notconv():
+    torch = torch_cuda()
+    from paper_2506_03947_gb300 import binding
+    P = inputs.config_2d(n=32)
+    s = make_solver(P, 1, 10)
+    bd = to_dev(P.b)
+    xd = torch.zeros_like(bd)
+    rc = s.solve(bd, xd, 1e-12, 2, allow_notconv=True)
+    assert rc == binding.AAO_ENOTCONV
+    st = s.stats()
+    assert st["outer_its"] == 2 and not st["converged"]
+    r2 = st["resid_explicit"]
+    assert abs(r2 - _explicit_residual(P, xd.cpu().numpy())) <= 1e-6 * r2
+    # continue from that iterate
+    s.solve(bd, xd, 1e-8, 64, use_x0=True)
+    assert s.stats()["converged"]
+    assert _explicit_residual(P, xd.cpu().numpy()) <= 1e-8
+
+
+def test_matvec_count_follows_table1():
+    P = inputs.config_2d(n=32)
+    _, st = _gpu_solve(P, 1, 12, 1e-8)
+    its, cyc = st["outer_its"], st["cycles"]
+    # per Arnoldi step: ell (script-A) + ell*p (P_NC); plus ell per explicit residual
+    assert st["a_matvecs"] == its * (P.ell + P.ell * 12) + (cyc + 1) * P.ell
+
+
+def test_zero_rhs_and_solve_determinism():
+    torch = torch_cuda()
+    P = inputs.config_2d(n=40)
+    s = make_solver(P, 1, 10)
+    bd = to_dev(P.b)
+    x1 = torch.zeros_like(bd)
+    x2 = torch.zeros_like(bd)
+    s.solve(bd, x1, 1e-8, 64)
+    s.solve(bd, x2, 1e-8, 64)
+    assert torch.equal(x1, x2)
+    z = torch.zeros_like(bd)
+    xz = torch.ones_like(bd)
+    s.solve(z, xz, 1e-8, 64)
+    assert torch.count_nonzero(xz).item() == 0
