@@ -196,13 +196,17 @@ def run_ours(args):
         if sampler:
             sampler.start()
         t0 = time.perf_counter()
+        walls = []
         for k in range(steps):
             flush.add_(1.0)                     # evict L2 between timed steps (not timed)
             ev[k][0].record(stream)
+            tw = time.perf_counter()
             solver.solve(b, x, P.tol, 64)
+            walls.append(time.perf_counter() - tw)
             ev[k][1].record(stream)
         barrier()
         wall = time.perf_counter() - t0
+        timed_solves.walls = walls
         clocks = sampler.stop() if sampler else None
         launches = binding.aao_kernel_launch_count() - n0
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
@@ -217,6 +221,7 @@ def run_ours(args):
     sampler = ClockSampler(local) if not args.no_clocks else None
     ms, wall, launches, prof, clocks, st32 = timed_solves(s32, args.steps, args.warmup, profile=True,
                                                           sampler=sampler)
+    walls32 = list(timed_solves.walls)
     ms_max = max_over_ranks(ms)
     value = world * args.steps / (ms_max / 1e3)
     x32 = x.clone()
@@ -289,12 +294,41 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * L, "d2h_bytes_per_step": 8 * L},
         "gpu_launches": launches, "clocks": clocks, "fp64_gpu": fp64,
+        "step_wall_ms": [round(w * 1e3, 3) for w in walls32],
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_ncu_case(args):
+    """Small launch sequence for ncu captures: preconditioner applies only.
+
+    The workload's grid and coefficients, a solver with a one-vector Krylov
+    space (so the device holds about 1 GB), and --steps applications of
+    P_NC^{-1} (one transform, p Chebyshev steps each).
+    """
+    import torch
+
+    from paper_2506_03947_gb300 import binding
+    from paper_2506_03947_gb300 import build as pkg_build
+    pkg_build.build()
+    P = make_problem(args.workload)
+    p = WORKLOADS[args.workload]["p"]
+    prec = binding.AAO_FP64 if args.ncu_fp64 else binding.AAO_MIXED
+    sptr = torch.cuda.current_stream().cuda_stream
+    s = binding.Solver(P.dim, P.n, P.kx.ravel(), P.ky.ravel(), None, P.ell, P.alpha, prec=prec, inner_its=p,
+                       restart=1, stream=sptr)
+    r = torch.from_numpy(P.b).cuda()
+    z = torch.empty_like(r)
+    for _ in range(args.steps):
+        s.precond_apply(r, z)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": workload_name(args.workload), "prec": "fp64" if args.ncu_fp64 else "mixed",
+                      "applies": args.steps, "launches": binding.aao_kernel_launch_count(),
+                      "z_norm": float(torch.linalg.norm(z))}))
 
 
 def cpu_baseline_sample(P, p, outer_its):
@@ -365,7 +399,13 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run only preconditioner applies (small device footprint) for ncu captures")
+    ap.add_argument("--ncu-fp64", action="store_true", help="with --ncu-case: FP64 path")
     args = ap.parse_args()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

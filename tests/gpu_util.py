@@ -5,8 +5,8 @@ import os
 
 import numpy as np
 
-U64 = np.finfo(np.float64).eps / 2     # unit roundoff, FP64
-U32 = np.finfo(np.float32).eps / 2     # unit roundoff, FP32
+U64 = float(np.finfo(np.float64).eps) / 2     # unit roundoff, FP64
+U32 = float(np.finfo(np.float32).eps) / 2     # unit roundoff, FP32
 
 
 def torch_cuda():
@@ -81,4 +81,4 @@ def log_record(rec):
     path = os.environ.get("AAO_PARITY_LOG")
     if path:
         with open(path, "a") as f:
-            f.write(json.dumps(rec) + "\n")
+            f.write(json.dumps(rec, default=float) + "\n")

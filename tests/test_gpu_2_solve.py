@@ -56,8 +56,9 @@ def test_fp64_fixed_steps_match_oracle(name, mk, p, k):
     log_record({"test": "fixed", "case": name, "k": k, "err": err})
     assert st["outer_its"] == k
     assert err <= 1e-10, err
-    # Givens estimates agree with the oracle's step by step
-    np.testing.assert_allclose(st["hist"], ref.history, rtol=1e-7)
+    # Givens estimates agree with the oracle's step by step (down to the rounding floor
+    # of ||b|| u: below ~1e-13 relative both are rounding noise)
+    np.testing.assert_allclose(st["hist"], ref.history, rtol=1e-7, atol=1e-13)
 
 
 def test_config1_fp64_converged():
