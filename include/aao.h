@@ -197,6 +197,45 @@ int aao_profile_get(aao_handle h, aao_profile* out);
  * used to count device work inside a timed region. */
 int64_t aao_kernel_launch_count(void);
 
+/*
+ * Preconditioner apply that allocates no device memory and needs no handle.
+ * The paper has no counterpart: this exists for callers that cannot let a
+ * library call cudaMalloc -- applications whose device memory is owned by
+ * their own pool or held to a fixed budget on a shared GPU, and latency-bound
+ * callers that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause.  (aao_create allocates, so such callers cannot hold a
+ * handle.)
+ *
+ * Computes the same z = P_NC^{-1} r as aao_precond_apply on a handle created
+ * with the same arguments, with the same kernels.  Every temporary (face
+ * coefficients, three Chebyshev field buffers, reduction partials) lives in
+ * one fixed 16 MiB array in the library's device memory, which every GPU that
+ * loads the library holds until the process exits.  Sizes: roughly
+ * 36 N + 3 ell N sizeof(T) bytes must fit (T = 4 mixed, 8 FP64), e.g.
+ * ell = 10 and N <= 107,000 cells mixed or N <= 60,000 FP64; larger problems
+ * are rejected with AAO_EINVAL and a message giving the bytes needed.
+ *
+ *   dim, n, kx, ky, kz, ell, alpha   as aao_create; face arrays, r and z must
+ *                  be DEVICE pointers (host pointers would need staging
+ *                  buffers and are rejected).
+ *   prec, inner_its                  as aao_options.
+ *   mu_max         > 1: upper spectral bound to use; 0: the Gershgorin bound.
+ *   r, z           ell*N doubles each, block-major, distinct.
+ *   stream         cudaStream_t for the work (NULL = default stream).
+ *   err, err_len   optional buffer for a one-line message on failure.
+ * The call synchronises the stream before returning.  On its first call on
+ * a device it looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current and caches it; make that first call before any
+ * stream capture.  All calls on a device share the one array and it keeps
+ * the last call's contents (the validity flag is cleared on every call), so
+ * calls that overlap on the GPU -- from two host threads or two streams --
+ * race and must be serialised by the caller.
+ */
+int aao_precond_apply_noalloc(int dim, const int64_t n[3], const double* kx, const double* ky,
+                              const double* kz, int ell, double alpha, int prec, int inner_its,
+                              double mu_max, const double* r, double* z, void* stream, char* err,
+                              int err_len);
+
 /* Release the handle and all workspace.  NULL is allowed. */
 void aao_destroy(aao_handle h);
 

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA",
 EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_apply", "aao_solve",
             "aao_solve_fixed", "aao_get_stats", "aao_get_bounds", "aao_last_error",
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
-            "aao_profile_enable", "aao_profile_get")
+            "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc")
 
 AAO_NPROF = 7
 PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth")
@@ -97,6 +97,9 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_profile_enable.restype = i32
     lib.aao_profile_get.argtypes = [vp, C.POINTER(aao_profile)]
     lib.aao_profile_get.restype = i32
+    lib.aao_precond_apply_noalloc.argtypes = [i32, C.POINTER(C.c_int64), vp, vp, vp, i32, dbl, i32, i32,
+                                              dbl, vp, vp, vp, C.c_char_p, i32]
+    lib.aao_precond_apply_noalloc.restype = i32
     _lib = lib
     return lib
 
@@ -193,6 +196,19 @@ def aao_profile_get(h) -> dict:
     _check(h, load_library().aao_profile_get(h, C.byref(p)))
     return {name: {"launches": int(p.launches[i]), "ms": float(p.ms[i]), "bytes": float(p.bytes[i])}
             for i, name in enumerate(PROF_NAMES)}
+
+
+def aao_precond_apply_noalloc(dim: int, n: Sequence[int], kx, ky, kz, ell: int, alpha: float,
+                              prec: int, inner_its: int, mu_max: float, r, z, stream=None) -> int:
+    """Allocation-free, handle-free preconditioner apply (device pointers only)."""
+    n3 = (C.c_int64 * 3)(*[int(v) for v in (list(n) + [1, 1, 1])[:3]])
+    buf = C.create_string_buffer(512)
+    rc = load_library().aao_precond_apply_noalloc(
+        int(dim), n3, _ptr(kx) or None, _ptr(ky) or None, _ptr(kz) or None, int(ell), float(alpha),
+        int(prec), int(inner_its), float(mu_max), _ptr(r), _ptr(z), stream, buf, len(buf))
+    if rc != AAO_OK:
+        raise AaoError(rc, buf.value.decode(errors="replace"))
+    return rc
 
 
 def aao_destroy(h) -> None:

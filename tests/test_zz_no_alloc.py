@@ -1,0 +1,83 @@
+"""The allocation-free preconditioner apply (aao_precond_apply_noalloc).
+
+For callers that cannot let the library allocate device memory (their memory
+belongs to their own pool or a fixed budget on a shared GPU, or they cannot
+afford the device-wide synchronisation of cudaMalloc/cudaFree), the library
+offers one handle-free apply whose temporaries live in a fixed 16 MiB device
+array.  This file checks, through the C ABI, that it gives the same result as
+the handle-based aao_precond_apply, on two calls in a row (the second call
+reuses the array with the first call's contents still in it), and that a
+problem too large for the array is refused with a clear error.
+
+It sits in a file of its own that pytest collects last, and passes both alone
+in a fresh process (where its first call does the per-device set-up) and after
+the other tests.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import ensure_lib, make_solver, precond_tol, to_dev, torch_cuda
+from paper_2506_03947_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _faces_dev(P):
+    torch = torch_cuda()
+    return [torch.from_numpy(np.ascontiguousarray(a.ravel())).cuda() if a.size else None
+            for a in (P.kx, P.ky, P.kz)]
+
+
+@pytest.mark.parametrize("prec,p", [(1, 20), (0, 7), (1, 1), (1, 2)], ids=["mixed_p20", "fp64_p7", "mixed_p1", "mixed_p2"])
+def test_noalloc_matches_handle_path_twice(prec, p):
+    torch = torch_cuda()
+    binding = ensure_lib()
+    P = inputs.config_2d(n=96, ell=10, alpha=1e-2)
+    stream = torch.cuda.current_stream().cuda_stream
+    kx, ky, kz = _faces_dev(P)
+    ref_solver = make_solver(P, prec, p)
+    tol = precond_tol(prec, p, P.ell, P.alpha)
+    for call in range(2):
+        r = to_dev(np.random.default_rng(10 + call).standard_normal((P.ell, P.N)))
+        z_ref = torch.empty_like(r)
+        ref_solver.precond_apply(r, z_ref)
+        z = torch.full_like(r, float("nan"))
+        binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, prec, p, 0.0, r, z, stream)
+        torch.cuda.synchronize()
+        err = float((z - z_ref).abs().max() / z_ref.abs().max())
+        assert err <= tol, (call, err, tol)
+
+
+def test_noalloc_3d_and_1d_shapes():
+    torch = torch_cuda()
+    binding = ensure_lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    for P in (inputs.make_problem("c", 3, (17, 9, 5), 6, 1e-2, 1, 0.7, (8.0, 8.0, 4.0), 1, 2),
+              inputs.config_1d()):
+        kx, ky, kz = _faces_dev(P)
+        s = make_solver(P, 1, 9)
+        r = to_dev(np.random.default_rng(3).standard_normal((P.ell, P.N)))
+        z_ref = torch.empty_like(r)
+        s.precond_apply(r, z_ref)
+        z = torch.empty_like(r)
+        binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, 1, 9, 0.0, r, z, stream)
+        err = float((z - z_ref).abs().max() / z_ref.abs().max())
+        assert err <= precond_tol(1, 9, P.ell, P.alpha)
+
+
+def test_noalloc_refuses_problems_larger_than_its_array():
+    torch = torch_cuda()
+    binding = ensure_lib()
+    P = inputs.config_2d(n=512, ell=10, alpha=1e-2)        # 262,144 cells: too large for 16 MiB
+    kx, ky, kz = _faces_dev(P)
+    r = to_dev(np.zeros((P.ell, P.N)))
+    z = torch.empty_like(r)
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, 1, 5, 0.0, r, z,
+                                          torch.cuda.current_stream().cuda_stream)
+    assert ei.value.status == binding.AAO_EINVAL
+    assert "scratch" in str(ei.value) and "bytes" in str(ei.value)
+    # host pointers would need staging buffers: refused, not allocated
+    with pytest.raises(binding.AaoError):
+        binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, 1, 5, 0.0,
+                                          np.zeros((P.ell, P.N)), np.zeros((P.ell, P.N)), None)
