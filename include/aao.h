@@ -105,7 +105,8 @@ typedef struct {
 #define AAO_PROF_STEP_LAST 4  /* last Chebyshev step fused with the inverse transform      */
 #define AAO_PROF_MATVEC 5     /* script-A matvec and explicit residual                      */
 #define AAO_PROF_ORTH 6       /* Gram-Schmidt multi-dots, updates and their reductions     */
-#define AAO_NPROF 7
+#define AAO_PROF_STEP_PAIR 7  /* two fused Chebyshev steps (2D mixed path)                 */
+#define AAO_NPROF 8
 
 /* Accumulated device time of each kernel class, from CUDA events recorded on
  * the handle's stream around every launch while profiling is on, with the

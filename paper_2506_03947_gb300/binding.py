@@ -27,8 +27,8 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc")
 
-AAO_NPROF = 7
-PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth")
+AAO_NPROF = 8
+PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair")
 
 
 class AaoError(RuntimeError):

@@ -49,6 +49,8 @@ struct aao_ctx {
   double *cx64 = nullptr, *cy64 = nullptr, *cz64 = nullptr;
   float *cx32 = nullptr, *cy32 = nullptr, *cz32 = nullptr;
   void *bhat = nullptr, *xa = nullptr, *xb = nullptr;  // Chebyshev fields (float or double)
+  void *xc = nullptr, *xd = nullptr;                   // extra fields for fused step pairs (2D mixed)
+  bool pairs = false;                                  // fused two-step kernels in use
   double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
   double* sc = nullptr;                                // small scalars, ScLayout
   double* partials = nullptr;                          // reduction partials
@@ -291,7 +293,71 @@ int precond_impl(aao_ctx* h, const double* r, const double* rscale, double* z, c
   return AAO_OK;
 }
 
+// Mixed 2D schedule with fused step pairs: k = 1 alone, then pairs (k, k+1)
+// while both are before the last step, at most one single step, then the
+// last step fused with the inverse transform.  Four field buffers rotate so
+// that a pair never writes a buffer it (or a neighbouring tile) reads.
+int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  const int p = h->p;
+  cudaStream_t s = h->stream;
+  const auto& st = h->steps32;
+  const auto& ia = h->idft32;
+  float* bhat = (float*)h->bhat;
+  float* X[4] = {(float*)h->xa, (float*)h->xb, (float*)h->xc, (float*)h->xd};
+  const float *cx = h->cx32, *cy = h->cy32, *cz = h->cz32;
+  const double N = (double)h->N, ell = (double)h->ell;
+  int pi = prof_begin(h, AAO_PROF_DFT, N * (8.0 * ell + 4.0 * ell));
+  AAO_CK(h, aao::launch_dft<float>(h->g, h->dim, h->ell, r, rscale, bhat, h->dft32, s));
+  prof_end(h, pi);
+  const bool last1 = (p == 2);
+  pi = prof_begin(h, last1 ? AAO_PROF_STEP_LAST : AAO_PROF_STEP_FIRST,
+                  N * (last1 ? (4.0 * ell + 8.0 + 8.0 * ell) : (8.0 * ell + 8.0)));
+  AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 0, 0, last1, cx, cy, cz, bhat, nullptr, X[0], z, st[1], ia,
+                                    s));
+  prof_end(h, pi);
+  if (last1) return AAO_OK;
+  int cur = 0, prev = -1;  // prev = -1: x_{k-1} = x_1 = bhat/theta (not stored)
+  int k = 2;
+  while (k + 1 <= p - 2) {
+    int o[2], n = 0;
+    for (int b = 0; b < 4 && n < 2; ++b)
+      if (b != cur && b != prev) o[n++] = b;
+    pi = prof_begin(h, AAO_PROF_STEP_PAIR, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
+    AAO_CK(h, aao::launch_pair(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
+                               X[o[0]], X[o[1]], st[k], st[k + 1], s));
+    prof_end(h, pi);
+    prev = o[0];
+    cur = o[1];
+    k += 2;
+  }
+  if (k <= p - 2) {
+    int dst = prev;
+    if (dst < 0)
+      for (int b = 0; b < 4; ++b)
+        if (b != cur) {
+          dst = b;
+          break;
+        }
+    const int psrc = prev < 0 ? 1 : 2;
+    pi = prof_begin(h, psrc == 1 ? AAO_PROF_STEP_SECOND : AAO_PROF_STEP_MID,
+                    N * ((psrc == 1 ? 3.0 : 4.0) * 4.0 * ell + 8.0));
+    AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 1, psrc, false, cx, cy, cz, bhat, X[cur], X[dst], z, st[k],
+                                      ia, s));
+    prof_end(h, pi);
+    prev = cur;
+    cur = dst;
+    k += 1;
+  }
+  const int psrc = prev < 0 ? 1 : 2;
+  pi = prof_begin(h, AAO_PROF_STEP_LAST, N * ((psrc == 1 ? 2.0 : 3.0) * 4.0 * ell + 8.0 + 8.0 * ell));
+  AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 1, psrc, true, cx, cy, cz, bhat, X[cur],
+                                    prev < 0 ? X[cur] : X[prev], z, st[k], ia, s));
+  prof_end(h, pi);
+  return AAO_OK;
+}
+
 int precond(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  if (h->pairs && h->p >= 3) return precond_pairs(h, r, rscale, z);
   if (h->prec == AAO_MIXED)
     return precond_impl<float>(h, r, rscale, z, h->steps32, h->dft32, h->idft32, h->cx32, h->cy32, h->cz32);
   return precond_impl<double>(h, r, rscale, z, h->steps64, h->dft64, h->idft64, h->cx64, h->cy64, h->cz64);
@@ -453,8 +519,8 @@ void aao_destroy(aao_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
-  void* dev[] = {h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32, h->bhat, h->xa,      h->xb,
-                 h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b};
+  void* dev[] = {h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32, h->bhat, h->xa, h->xb, h->xc,
+                 h->xd,   h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -599,6 +665,11 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   AAO_CK_CREATE(cudaMalloc(&h->bhat, fsz * h->L));
   AAO_CK_CREATE(cudaMalloc(&h->xa, fsz * h->L));
   AAO_CK_CREATE(cudaMalloc(&h->xb, fsz * h->L));
+  h->pairs = (h->prec == AAO_MIXED && dim == 2 && n[0] % 4 == 0);
+  if (h->pairs) {
+    AAO_CK_CREATE(cudaMalloc(&h->xc, fsz * h->L));
+    AAO_CK_CREATE(cudaMalloc(&h->xd, fsz * h->L));
+  }
   AAO_CK_CREATE(cudaMalloc(&h->V, sizeof(double) * h->L * (h->m + 1)));
   AAO_CK_CREATE(cudaMalloc(&h->Z, sizeof(double) * h->L * h->m));
   build_tables(h);

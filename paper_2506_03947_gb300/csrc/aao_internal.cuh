@@ -78,6 +78,13 @@ cudaError_t launch_step(const GridDesc& g, int dim, int ell, int ksrc, int psrc,
                         const T* cx, const T* cy, const T* cz, const T* bhat, const T* xk, T* xio,
                         double* z, const StepArgs<T>& sa, const IdftArgs<T>& ia, cudaStream_t s);
 
+// Two fused FP32 steps (k, k+1) on a 2D grid with n0 % 4 == 0 (cheb_d2.cu):
+// reads xk, xkm1 (or bhat/theta when psrc == 1) and bhat; writes x_{k+1} to
+// out1 and x_{k+2} to out2, which must differ from every input.
+cudaError_t launch_pair(const GridDesc& g, int ell, int psrc, const float* cx, const float* cy, const float* bhat,
+                        const float* xk, const float* xkm1, float* out1, float* out2, const StepArgs<float>& s1,
+                        const StepArgs<float>& s2, cudaStream_t s);
+
 // FP64 Krylov kernels (krylov.cu).
 // y = script-A x (mode 0) or y = b - script-A x with per-block partial sums of y^2 (mode 1).
 cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,

@@ -13,6 +13,9 @@
 #pragma once
 
 #include "aao_internal.cuh"
+#include "cheb_v4.cuh"
+
+#include <type_traits>
 
 namespace aao {
 
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(256)
 
   if constexpr (LAST) {
 #pragma unroll
-    for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = (double)zt[t] * ia.igamma[t];
+    for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = (double)(zt[t] * (T)ia.igamma[t]);
   }
 }
 
@@ -174,9 +177,10 @@ template <typename T, int ELL>
 __device__ __forceinline__ void dft_point(int64_t N, int64_t c, const double* __restrict__ r, double sc,
                                           const DftArgs<T>& da, T (&fre)[ELL / 2 + 1],
                                           T (&fim)[ELL / 2 + 1]) {
+  // alpha-scaling: in T (the mixed path rounds r to FP32 first and scales in FP32)
   T s[ELL];
 #pragma unroll
-  for (int t = 0; t < ELL; ++t) s[t] = (T)(__ldg(r + (int64_t)t * N + c) * (da.gamma[t] * sc));
+  for (int t = 0; t < ELL; ++t) s[t] = (T)__ldg(r + (int64_t)t * N + c) * (T)(da.gamma[t] * sc);
 #pragma unroll
   for (int m = 0; m <= ELL / 2; ++m) {
     T re = T(0), im = T(0);
@@ -229,15 +233,51 @@ __global__ void __launch_bounds__(256)
     for (int t = 0; t < ELL; ++t) zt[t] += yr * ia.ci[t][m] - yi * ia.si[t][m];
   }
 #pragma unroll
-  for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = (double)zt[t] * ia.igamma[t];
+  for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = (double)(zt[t] * (T)ia.igamma[t]);
 }
 
 // ---- dispatch -------------------------------------------------------------
+
+// FP32 steps on grids whose rows are a multiple of 4 cells use the vectorised
+// kernel (16-byte accesses; the inverse-transform output needs a 16-byte
+// aligned z as well).
+template <int ELL, int DIM>
+cudaError_t launch_step_v4(const GridDesc& g, int ksrc, int psrc, bool last, const float* cx, const float* cy,
+                           const float* cz, const float* bhat, const float* xk, float* xio, double* z,
+                           const StepArgs<float>& sa, const IdftArgs<float>& ia, cudaStream_t s) {
+  dim3 block, grid;
+  if (DIM == 1) {
+    block = dim3(256, 1, 1);
+    grid = dim3((unsigned)((g.n0 + 1023) / 1024), 1, 1);
+  } else {
+    block = dim3(32, 8, 1);
+    grid = dim3((unsigned)((g.n0 + 127) / 128), (unsigned)((g.n1 + 7) / 8), (unsigned)g.n2);
+  }
+  const int mode = ksrc * 100 + psrc * 10 + (last ? 1 : 0);
+#define AAO_V4(K, P, LST) \
+  k_cheb_step_v4<ELL, DIM, K, P, LST><<<grid, block, 0, s>>>(g, cx, cy, cz, bhat, xk, xio, z, sa, ia)
+  switch (mode) {
+    case 0: AAO_V4(0, 0, false); break;
+    case 1: AAO_V4(0, 0, true); break;
+    case 110: AAO_V4(1, 1, false); break;
+    case 111: AAO_V4(1, 1, true); break;
+    case 120: AAO_V4(1, 2, false); break;
+    case 121: AAO_V4(1, 2, true); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef AAO_V4
+  count_launch();
+  return cudaGetLastError();
+}
 
 template <typename T, int ELL, int DIM>
 cudaError_t launch_step_ell_dim(const GridDesc& g, int ksrc, int psrc, bool last, const T* cx, const T* cy,
                                 const T* cz, const T* bhat, const T* xk, T* xio, double* z,
                                 const StepArgs<T>& sa, const IdftArgs<T>& ia, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (g.n0 % 4 == 0 && (!last || (reinterpret_cast<uintptr_t>(z) % 16) == 0))
+      return launch_step_v4<ELL, DIM>(g, ksrc, psrc, last, cx, cy, cz, bhat, xk, xio, z, sa, ia, s);
+  }
   dim3 block, grid;
   if (DIM == 1) {
     block = dim3(256, 1, 1);

@@ -75,14 +75,20 @@ __global__ void __launch_bounds__(256)
       nb[4] = (k < g.n2 - 1) ? c + pl : c;
       nb[5] = (k > 0) ? c - pl : c;
     }
+    // diagonal form (1 + sum kappa) x_c - sum kappa x_nbr: the diagonal is formed
+    // once per cell and reused for all ell blocks (FP64 arithmetic is the
+    // scarce resource here, not bandwidth)
+    double diag = 1.0;
+#pragma unroll
+    for (int q = 0; q < 2 * DIM; ++q) diag += kap[q];
     double prev = 0.0;
     for (int t = 0; t < ell; ++t) {
       const double* xt = x + (int64_t)t * N;
       const double xc = __ldg(xt + c);
-      double a = xc;
+      double a = diag * xc - prev;
 #pragma unroll
-      for (int q = 0; q < 2 * DIM; ++q) a += kap[q] * (xc - __ldg(xt + nb[q]));
-      double v = a - prev;
+      for (int q = 0; q < 2 * DIM; ++q) a -= kap[q] * __ldg(xt + nb[q]);
+      double v = a;
       prev = xc;
       if constexpr (MODE == 1) {
         v = __ldg(b + (int64_t)t * N + c) - v;
@@ -140,6 +146,14 @@ int reduction_blocks(int64_t L) {
 
 constexpr int kDotGroup = 8;  // dot products accumulated per pass over w
 
+// The flat-vector kernels below walk the vectors two doubles at a time
+// (16-byte loads) and unroll by two, so each thread keeps several independent
+// loads in flight; L (= ell N) is even whenever N is even, and an odd tail is
+// handled separately.
+__device__ __forceinline__ double2 ld2(const double* __restrict__ p) {
+  return __ldg(reinterpret_cast<const double2*>(p));
+}
+
 // partials[i*NB + blk] = vscale[i] * sum_{e in block slice} V_i[e] w[e], for i in [i0, i0+G).
 template <int G>
 __global__ void __launch_bounds__(kRedThreads)
@@ -149,12 +163,39 @@ __global__ void __launch_bounds__(kRedThreads)
   double acc[G];
 #pragma unroll
   for (int q = 0; q < G; ++q) acc[q] = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
-    const double we = __ldg(w + e);
+  const int ng = min(G, nv - i0);
+  const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const int64_t L2 = L / 2;
+    int64_t e2 = tid;
+    for (; e2 + nthr < L2; e2 += 2 * nthr) {
+      const double2 wa = ld2(w + 2 * e2), wb = ld2(w + 2 * (e2 + nthr));
 #pragma unroll
-    for (int q = 0; q < G; ++q)
-      if (i0 + q < nv) acc[q] += __ldg(V + (int64_t)(i0 + q) * ldv + e) * we;
+      for (int q = 0; q < G; ++q)
+        if (q < ng) {
+          const double* vq = V + (int64_t)(i0 + q) * ldv;
+          const double2 va = ld2(vq + 2 * e2), vb = ld2(vq + 2 * (e2 + nthr));
+          acc[q] += va.x * wa.x + va.y * wa.y + vb.x * wb.x + vb.y * wb.y;
+        }
+    }
+    for (; e2 < L2; e2 += nthr) {
+      const double2 wa = ld2(w + 2 * e2);
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (q < ng) {
+          const double2 va = ld2(V + (int64_t)(i0 + q) * ldv + 2 * e2);
+          acc[q] += va.x * wa.x + va.y * wa.y;
+        }
+    }
+  } else {
+    for (int64_t e = tid; e < L; e += nthr) {
+      const double we = __ldg(w + e);
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (q < ng) acc[q] += __ldg(V + (int64_t)(i0 + q) * ldv + e) * we;
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -163,7 +204,7 @@ __global__ void __launch_bounds__(kRedThreads)
     if (lane == 0) sh[q][warp] = v;
   }
   __syncthreads();
-  if (threadIdx.x < G && i0 + (int)threadIdx.x < nv) {
+  if (threadIdx.x < G && (int)threadIdx.x < ng) {
     const int q = threadIdx.x;
     double t = 0.0;
 #pragma unroll
@@ -193,12 +234,39 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int q = threadIdx.x; q < nv; q += blockDim.x) coef[q] = h[q] * (vscale ? vscale[q] : 1.0);
   __syncthreads();
   double acc2 = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
-    double v = w[e];
-    for (int q = 0; q < nv; ++q) v -= coef[q] * __ldg(V + (int64_t)q * ldv + e);
-    w[e] = v;
-    acc2 += v * v;
+  const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  if (vec) {
+    const int64_t L2 = L / 2;
+    for (int64_t e2 = tid; e2 < L2; e2 += nthr) {
+      double2 v = *reinterpret_cast<const double2*>(w + 2 * e2);
+      int q = 0;
+      for (; q + 4 <= nv; q += 4) {
+        const double2 a0 = ld2(V + (int64_t)q * ldv + 2 * e2);
+        const double2 a1 = ld2(V + (int64_t)(q + 1) * ldv + 2 * e2);
+        const double2 a2 = ld2(V + (int64_t)(q + 2) * ldv + 2 * e2);
+        const double2 a3 = ld2(V + (int64_t)(q + 3) * ldv + 2 * e2);
+        v.x -= coef[q] * a0.x; v.y -= coef[q] * a0.y;
+        v.x -= coef[q + 1] * a1.x; v.y -= coef[q + 1] * a1.y;
+        v.x -= coef[q + 2] * a2.x; v.y -= coef[q + 2] * a2.y;
+        v.x -= coef[q + 3] * a3.x; v.y -= coef[q + 3] * a3.y;
+      }
+      for (; q < nv; ++q) {
+        const double2 a = ld2(V + (int64_t)q * ldv + 2 * e2);
+        v.x -= coef[q] * a.x;
+        v.y -= coef[q] * a.y;
+      }
+      *reinterpret_cast<double2*>(w + 2 * e2) = v;
+      acc2 += v.x * v.x + v.y * v.y;
+    }
+  } else {
+    for (int64_t e = tid; e < L; e += nthr) {
+      double v = w[e];
+      for (int q = 0; q < nv; ++q) v -= coef[q] * __ldg(V + (int64_t)q * ldv + e);
+      w[e] = v;
+      acc2 += v * v;
+    }
   }
   if (partials) {
     const double t = block_sum(acc2, sh);
