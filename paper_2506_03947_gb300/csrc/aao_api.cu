@@ -231,6 +231,8 @@ void build_tables(aao_ctx* h) {
   for (int t = 0; t < aao::kMaxEll; ++t) {
     h->dft32.gamma[t] = h->dft64.gamma[t];
     h->idft32.igamma[t] = h->idft64.igamma[t];
+    h->idft32.igamma_T[t] = (float)h->idft64.igamma[t];
+    h->idft64.igamma_T[t] = h->idft64.igamma[t];
     for (int m = 0; m < aao::kMaxF; ++m) {
       h->dft32.cf[t][m] = (float)h->dft64.cf[t][m];
       h->dft32.sf[t][m] = (float)h->dft64.sf[t][m];

@@ -55,6 +55,7 @@ struct DftArgs {
 template <typename T>
 struct IdftArgs {
   double igamma[kMaxEll];
+  T igamma_T[kMaxEll];   // igamma rounded to T on the host
   T ci[kMaxEll][kMaxF];
   T si[kMaxEll][kMaxF];
 };
@@ -130,5 +131,39 @@ struct ScLayout {
 };
 
 void count_launch();
+
+// IEEE binary64 -> binary32 with round-to-nearest-even, on the integer pipe.
+// GB300 issues FP64<->FP32 conversions on its (narrow) FP64 pipe; the mixed
+// path converts every residual value once per preconditioner apply.  Results
+// below the FP32 normal range become signed zero and results above it
+// infinity (NaN also becomes infinity); the scaled residuals here are far
+// from both limits.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const int hi = __double2hiint(d);
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  const int fe = ((hi >> 20) & 0x7ff) - 896;
+  const unsigned m = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem > 0x10000000u) || (rem == 0x10000000u && (m & 1u));
+  unsigned bits = ((unsigned)fe << 23) + m + up;
+  bits = (fe <= 0) ? 0u : bits;
+  bits = (fe >= 255) ? 0x7f800000u : bits;
+  return __uint_as_float(sign | bits);
+}
+
+// IEEE binary32 -> binary64 (exact) on the integer pipe; FP32 subnormals
+// become signed zero, infinities and NaNs keep their class.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  const unsigned eo = (e == 0u) ? 0u : ((e == 255u) ? 0x7ffu : e + 896u);
+  const unsigned mm = (e == 0u) ? 0u : m;
+  const unsigned hi = sign | (eo << 20) | (mm >> 3);
+  const unsigned lo = mm << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
 
 }  // namespace aao

@@ -19,6 +19,18 @@
 
 namespace aao {
 
+// conversions between the Chebyshev field type and FP64 (integer pipe for FP32)
+template <typename T>
+__device__ __forceinline__ T to_T(double v) {
+  if constexpr (std::is_same<T, float>::value) return d2f_rn(v);
+  else return v;
+}
+template <typename T>
+__device__ __forceinline__ double from_T(T v) {
+  if constexpr (std::is_same<T, float>::value) return f2d_exact(v);
+  else return v;
+}
+
 template <typename T, int DIM>
 struct Stencil {
   T kap[2 * DIM];
@@ -168,19 +180,20 @@ __global__ void __launch_bounds__(256)
 
   if constexpr (LAST) {
 #pragma unroll
-    for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = (double)(zt[t] * (T)ia.igamma[t]);
+    for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = from_T<T>(zt[t] * ia.igamma_T[t]);
   }
 }
 
 // Forward transform (Eq. 5's U* Gamma): r (FP64, block-major) -> packed bhat.
+// gs[t] = gamma_t * scale in T, formed once per block by the caller.
 template <typename T, int ELL>
-__device__ __forceinline__ void dft_point(int64_t N, int64_t c, const double* __restrict__ r, double sc,
+__device__ __forceinline__ void dft_point(int64_t N, int64_t c, const double* __restrict__ r, const T* gs,
                                           const DftArgs<T>& da, T (&fre)[ELL / 2 + 1],
                                           T (&fim)[ELL / 2 + 1]) {
-  // alpha-scaling: in T (the mixed path rounds r to FP32 first and scales in FP32)
+  // alpha-scaling in T: the mixed path rounds r to FP32 first and scales in FP32
   T s[ELL];
 #pragma unroll
-  for (int t = 0; t < ELL; ++t) s[t] = (T)__ldg(r + (int64_t)t * N + c) * (T)(da.gamma[t] * sc);
+  for (int t = 0; t < ELL; ++t) s[t] = to_T<T>(__ldg(r + (int64_t)t * N + c)) * gs[t];
 #pragma unroll
   for (int m = 0; m <= ELL / 2; ++m) {
     T re = T(0), im = T(0);
@@ -198,11 +211,13 @@ template <typename T, int ELL>
 __global__ void __launch_bounds__(256)
     k_dft(int64_t N, const double* __restrict__ r, const double* __restrict__ rscale, T* __restrict__ bhat,
           DftArgs<T> da) {
+  __shared__ T gs[ELL];
+  if (threadIdx.x < ELL) gs[threadIdx.x] = (T)(da.gamma[threadIdx.x] * (rscale ? *rscale : 1.0));
+  __syncthreads();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  const double sc = rscale ? *rscale : 1.0;
   T fre[ELL / 2 + 1], fim[ELL / 2 + 1];
-  dft_point<T, ELL>(N, c, r, sc, da, fre, fim);
+  dft_point<T, ELL>(N, c, r, gs, da, fre, fim);
   bhat[c] = fre[0];
   bhat[N + c] = fre[ELL / 2];
 #pragma unroll
@@ -217,11 +232,17 @@ template <typename T, int ELL>
 __global__ void __launch_bounds__(256)
     k_direct(int64_t N, const double* __restrict__ r, const double* __restrict__ rscale, double* __restrict__ z,
              DftArgs<T> da, StepArgs<T> sa, IdftArgs<T> ia) {
+  __shared__ T gs[ELL];
+  __shared__ T ig[ELL];
+  if (threadIdx.x < ELL) {
+    gs[threadIdx.x] = (T)(da.gamma[threadIdx.x] * (rscale ? *rscale : 1.0));
+    ig[threadIdx.x] = (T)ia.igamma[threadIdx.x];
+  }
+  __syncthreads();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  const double sc = rscale ? *rscale : 1.0;
   T fre[ELL / 2 + 1], fim[ELL / 2 + 1];
-  dft_point<T, ELL>(N, c, r, sc, da, fre, fim);
+  dft_point<T, ELL>(N, c, r, gs, da, fre, fim);
   T zt[ELL];
 #pragma unroll
   for (int t = 0; t < ELL; ++t) zt[t] = T(0);
@@ -233,7 +254,7 @@ __global__ void __launch_bounds__(256)
     for (int t = 0; t < ELL; ++t) zt[t] += yr * ia.ci[t][m] - yi * ia.si[t][m];
   }
 #pragma unroll
-  for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = (double)(zt[t] * (T)ia.igamma[t]);
+  for (int t = 0; t < ELL; ++t) z[(int64_t)t * N + c] = from_T<T>(zt[t] * ig[t]);
 }
 
 // ---- dispatch -------------------------------------------------------------

@@ -231,9 +231,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int t = 0; t < ELL; ++t) {
         double2* zp = reinterpret_cast<double2*>(z + (int64_t)t * N + c);
-        const float gmul = (float)ia.igamma[t];
-        zp[0] = make_double2((double)(zt[0][t] * gmul), (double)(zt[1][t] * gmul));
-        zp[1] = make_double2((double)(zt[2][t] * gmul), (double)(zt[3][t] * gmul));
+        const float gmul = ia.igamma_T[t];
+        zp[0] = make_double2(f2d_exact(zt[0][t] * gmul), f2d_exact(zt[1][t] * gmul));
+        zp[1] = make_double2(f2d_exact(zt[2][t] * gmul), f2d_exact(zt[3][t] * gmul));
       }
     }
   }

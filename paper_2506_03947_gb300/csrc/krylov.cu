@@ -155,46 +155,46 @@ __device__ __forceinline__ double2 ld2(const double* __restrict__ p) {
 }
 
 // partials[i*NB + blk] = vscale[i] * sum_{e in block slice} V_i[e] w[e], for i in [i0, i0+G).
+// G is the exact number of vectors of this launch: a runtime bound inside the
+// unrolled loop would let the compiler turn the guards into selects and issue
+// FP64 multiply-adds for all slots, and FP64 arithmetic is this kernel's limit.
 template <int G>
 __global__ void __launch_bounds__(kRedThreads)
-    k_multidot(const double* __restrict__ V, int64_t ldv, int i0, int nv, const double* __restrict__ vscale,
+    k_multidot(const double* __restrict__ V, int64_t ldv, int i0, const double* __restrict__ vscale,
                const double* __restrict__ w, int64_t L, double* __restrict__ partials) {
   __shared__ double sh[G][kRedWarps];
   double acc[G];
 #pragma unroll
   for (int q = 0; q < G; ++q) acc[q] = 0.0;
-  const int ng = min(G, nv - i0);
   const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const double* V0 = V + (int64_t)i0 * ldv;
   if (vec) {
     const int64_t L2 = L / 2;
     int64_t e2 = tid;
     for (; e2 + nthr < L2; e2 += 2 * nthr) {
       const double2 wa = ld2(w + 2 * e2), wb = ld2(w + 2 * (e2 + nthr));
 #pragma unroll
-      for (int q = 0; q < G; ++q)
-        if (q < ng) {
-          const double* vq = V + (int64_t)(i0 + q) * ldv;
-          const double2 va = ld2(vq + 2 * e2), vb = ld2(vq + 2 * (e2 + nthr));
-          acc[q] += va.x * wa.x + va.y * wa.y + vb.x * wb.x + vb.y * wb.y;
-        }
+      for (int q = 0; q < G; ++q) {
+        const double* vq = V0 + (int64_t)q * ldv;
+        const double2 va = ld2(vq + 2 * e2), vb = ld2(vq + 2 * (e2 + nthr));
+        acc[q] += va.x * wa.x + va.y * wa.y + vb.x * wb.x + vb.y * wb.y;
+      }
     }
     for (; e2 < L2; e2 += nthr) {
       const double2 wa = ld2(w + 2 * e2);
 #pragma unroll
-      for (int q = 0; q < G; ++q)
-        if (q < ng) {
-          const double2 va = ld2(V + (int64_t)(i0 + q) * ldv + 2 * e2);
-          acc[q] += va.x * wa.x + va.y * wa.y;
-        }
+      for (int q = 0; q < G; ++q) {
+        const double2 va = ld2(V0 + (int64_t)q * ldv + 2 * e2);
+        acc[q] += va.x * wa.x + va.y * wa.y;
+      }
     }
   } else {
     for (int64_t e = tid; e < L; e += nthr) {
       const double we = __ldg(w + e);
 #pragma unroll
-      for (int q = 0; q < G; ++q)
-        if (q < ng) acc[q] += __ldg(V + (int64_t)(i0 + q) * ldv + e) * we;
+      for (int q = 0; q < G; ++q) acc[q] += __ldg(V0 + (int64_t)q * ldv + e) * we;
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kRedThreads)
     if (lane == 0) sh[q][warp] = v;
   }
   __syncthreads();
-  if (threadIdx.x < G && (int)threadIdx.x < ng) {
+  if (threadIdx.x < G) {
     const int q = threadIdx.x;
     double t = 0.0;
 #pragma unroll
@@ -218,7 +218,24 @@ cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* 
                             int64_t L, double* partials, cudaStream_t s) {
   const int nb = reduction_blocks(L);
   for (int i0 = 0; i0 < nv; i0 += kDotGroup) {
-    k_multidot<kDotGroup><<<nb, kRedThreads, 0, s>>>(V, ldv, i0, nv, vscale, w, L, partials);
+    const int g = (nv - i0 < kDotGroup) ? nv - i0 : kDotGroup;
+    switch (g) {
+#define AAO_MD(G) \
+  case G:         \
+    k_multidot<G><<<nb, kRedThreads, 0, s>>>(V, ldv, i0, vscale, w, L, partials); \
+    break;
+      AAO_MD(1)
+      AAO_MD(2)
+      AAO_MD(3)
+      AAO_MD(4)
+      AAO_MD(5)
+      AAO_MD(6)
+      AAO_MD(7)
+      AAO_MD(8)
+#undef AAO_MD
+      default:
+        return cudaErrorInvalidValue;
+    }
     count_launch();
   }
   return cudaGetLastError();

@@ -144,6 +144,7 @@ void transform_tables(int ell, double alpha, aao::DftArgs<T>& da, aao::IdftArgs<
   for (int t = 0; t < ell; ++t) {
     da.gamma[t] = std::pow(alpha, (double)t / ell);
     ia.igamma[t] = std::pow(alpha, -(double)t / ell);
+    ia.igamma_T[t] = (T)ia.igamma[t];
     for (int m = 0; m <= ell / 2; ++m) {
       const double ang = 2.0 * pi * (double)((t * m) % ell) / ell;
       da.cf[t][m] = (T)(std::cos(ang) * isq);
