@@ -73,7 +73,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("cheb_kernels.cuh", "cheb_v4.cuh", "cheb_pair.cuh", "aao_internal.cuh"):
+    for f in ("cheb_kernels.cuh", "cheb_v4.cuh", "cheb_pair.cuh", "cheb_quad.cuh", "aao_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2506_03947_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -261,14 +261,15 @@ def run_ours(args):
 
     # --- roofline of the dominant kernel (the fused Chebyshev sweep class with the most time)
     peak, peak_src = measured_peaks()
-    sweep_classes = [k for k in ("step_pair", "step_mid") if prof[k]["launches"] > 0]
+    sweep_classes = [k for k in ("step_quad", "step_pair", "step_mid") if prof[k]["launches"] > 0]
     dom = max(sweep_classes, key=lambda k: prof[k]["ms"])
     mid = prof[dom]
     per_launch_bytes = mid["bytes"] / max(1, mid["launches"])
     avg_ms = mid["ms"] / max(1, mid["launches"])
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     total_ms_prof = sum(v["ms"] for v in prof.values())
-    kernels = {"step_pair": "k_cheb_pair_v4<10,2> (two fused multi-frequency Chebyshev steps, FP32)",
+    kernels = {"step_quad": "k_cheb_quad<10,16,2> (four fused multi-frequency Chebyshev steps, FP32, shared-memory tile)",
+               "step_pair": "k_cheb_pair_v4<10,2> (two fused multi-frequency Chebyshev steps, FP32)",
                "step_mid": "k_cheb_step_v4<10,2,1,2,false> (fused multi-frequency Chebyshev step, FP32)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(dom + "_" + args.workload),

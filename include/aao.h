@@ -106,7 +106,8 @@ typedef struct {
 #define AAO_PROF_MATVEC 5     /* script-A matvec and explicit residual                      */
 #define AAO_PROF_ORTH 6       /* Gram-Schmidt multi-dots, updates and their reductions     */
 #define AAO_PROF_STEP_PAIR 7  /* two fused Chebyshev steps (2D mixed path)                 */
-#define AAO_NPROF 8
+#define AAO_PROF_STEP_QUAD 8  /* four fused Chebyshev steps (2D mixed path)                */
+#define AAO_NPROF 9
 
 /* Accumulated device time of each kernel class, from CUDA events recorded on
  * the handle's stream around every launch while profiling is on, with the

@@ -27,8 +27,9 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc")
 
-AAO_NPROF = 8
-PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair")
+AAO_NPROF = 9
+PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair",
+              "step_quad")
 
 
 class AaoError(RuntimeError):

@@ -320,6 +320,20 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
   if (last1) return AAO_OK;
   int cur = 0, prev = -1;  // prev = -1: x_{k-1} = x_1 = bhat/theta (not stored)
   int k = 2;
+  while (k + 3 <= p - 2) {
+    int o[2], n = 0;
+    for (int b = 0; b < 4 && n < 2; ++b)
+      if (b != cur && b != prev) o[n++] = b;
+    aao::QuadSteps qs;
+    for (int q = 0; q < 4; ++q) qs.s[q] = st[k + q];
+    pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
+    AAO_CK(h, aao::launch_quad(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
+                               X[o[0]], X[o[1]], qs, s));
+    prof_end(h, pi);
+    prev = o[0];
+    cur = o[1];
+    k += 4;
+  }
   while (k + 1 <= p - 2) {
     int o[2], n = 0;
     for (int b = 0; b < 4 && n < 2; ++b)

@@ -86,6 +86,17 @@ cudaError_t launch_pair(const GridDesc& g, int ell, int psrc, const float* cx, c
                         const float* xk, const float* xkm1, float* out1, float* out2, const StepArgs<float>& s1,
                         const StepArgs<float>& s2, cudaStream_t s);
 
+// Four fused FP32 steps (k .. k+3) on a 2D grid with n0 % 4 == 0 (cheb_d2.cu):
+// reads xk, xkm1 (or bhat/theta when psrc == 1) and bhat; writes x_{k+3} to
+// out3 and x_{k+4} to out4, which must differ from every input.  s[q] holds
+// the coefficients of step k + q.
+struct QuadSteps {
+  StepArgs<float> s[4];
+};
+cudaError_t launch_quad(const GridDesc& g, int ell, int psrc, const float* cx, const float* cy, const float* bhat,
+                        const float* xk, const float* xkm1, float* out3, float* out4, const QuadSteps& qs,
+                        cudaStream_t s);
+
 // FP64 Krylov kernels (krylov.cu).
 // y = script-A x (mode 0) or y = b - script-A x with per-block partial sums of y^2 (mode 1).
 cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,

@@ -1,6 +1,7 @@
 // Chebyshev step kernels for 2D grids (instantiations; bodies in cheb_kernels.cuh).
 #include "cheb_kernels.cuh"
 #include "cheb_pair.cuh"
+#include "cheb_quad.cuh"
 
 namespace aao {
 template cudaError_t launch_step_dim<float, 2>(const GridDesc&, int, int, int, bool, const float*, const float*,
@@ -26,6 +27,26 @@ cudaError_t launch_pair(const GridDesc& g, int ell, int psrc, const float* cx, c
     AAO_PAIR_CASE(14)
     AAO_PAIR_CASE(16)
 #undef AAO_PAIR_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_quad(const GridDesc& g, int ell, int psrc, const float* cx, const float* cy, const float* bhat,
+                        const float* xk, const float* xkm1, float* out3, float* out4, const QuadSteps& qs,
+                        cudaStream_t s) {
+  switch (ell) {
+#define AAO_QUAD_CASE(L) \
+  case L:                \
+    return launch_quad_ell<L>(g, psrc, cx, cy, bhat, xk, xkm1, out3, out4, qs, s);
+    AAO_QUAD_CASE(4)
+    AAO_QUAD_CASE(6)
+    AAO_QUAD_CASE(8)
+    AAO_QUAD_CASE(10)
+    AAO_QUAD_CASE(12)
+    AAO_QUAD_CASE(14)
+    AAO_QUAD_CASE(16)
+#undef AAO_QUAD_CASE
     default:
       return cudaErrorInvalidValue;
   }
