@@ -14,7 +14,11 @@
 //
 // Frequencies are processed one plane pair at a time (the two real
 // frequencies together, then each complex one), so the staged tile is two
-// planes deep; the face coefficients are staged once per block.
+// planes deep; the face coefficients and the diagonal d = 1 + sum kappa of
+// A are staged once per block.  Each level forms the residual as
+//   b - (A - lambda) x = bhat + sum_f kappa_f x_nbr(f) - (d - lambda) x,
+// one multiply-add per term; its rounding (about d u |x|) enters the update
+// multiplied by g ~ 2/mu_max, i.e. a few units of roundoff of |x| per step.
 #pragma once
 
 #include "aao_internal.cuh"
@@ -27,23 +31,24 @@ constexpr int kQuadCols = 128;                 // staged cells per row (32 lanes
 constexpr int kQuadPad = 4;                    // zero padding each side of a staged row
 constexpr int kQuadStride = kQuadCols + 2 * kQuadPad;
 constexpr int kQuadInnerX = kQuadCols - 2 * kQuadS;  // 120
-constexpr int kQuadThreads = 256;
 
 template <int TY>
 __host__ __device__ constexpr int quad_rows() {
   return TY + 2 * kQuadS;
 }
-// shared memory: two level buffers and bhat (2 planes each), cx and cy
+// shared memory: two level buffers (2 planes each), cx, cy and the diagonal
 template <int TY>
 constexpr size_t quad_smem_bytes() {
-  return sizeof(float) * (size_t)quad_rows<TY>() * kQuadStride * (3 * 2 + 2);
+  return sizeof(float) * (size_t)quad_rows<TY>() * kQuadStride * (2 * 2 + 3);
 }
 
 using QuadArgs = QuadSteps;
 
 // PSRC: x_{k-1} = bhat/theta (1, first fused step is k = 2) or read from xkm1 (2).
-template <int ELL, int TY, int PSRC>
-__global__ void __launch_bounds__(kQuadThreads, 2)
+// NT threads: NT/32 warps, each owning the staged rows warp, warp + NT/32, ...
+// (RPW of them) for the whole launch, so bhat of those rows stays in registers.
+template <int ELL, int TY, int PSRC, int NT>
+__global__ void __launch_bounds__(NT)
     k_cheb_quad(GridDesc g, const float* __restrict__ cx, const float* __restrict__ cy,
                 const float* __restrict__ bhat, const float* __restrict__ xk, const float* __restrict__ xkm1,
                 float* __restrict__ out3, float* __restrict__ out4, QuadArgs qa) {
@@ -52,12 +57,14 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
   extern __shared__ float sm[];
   float* bufA = sm;                  // [2][ROWS][stride]
   float* bufB = sm + 2 * PLANE;
-  float* bufH = sm + 4 * PLANE;      // bhat
-  float* kxs = sm + 6 * PLANE;       // cx
-  float* kys = sm + 7 * PLANE;       // cy
+  float* kxs = sm + 4 * PLANE;       // cx
+  float* kys = sm + 5 * PLANE;       // cy
+  float* kds = sm + 6 * PLANE;       // diagonal 1 + sum of the four face coefficients
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  constexpr int NW = kQuadThreads / 32;
+  constexpr int NW = NT / 32;
+  constexpr int RPW = (ROWS + NW - 1) / NW;   // staged rows per warp
+  F4 hreg[RPW][2];                             // bhat of this thread's rows, current pass
   const int gx0 = blockIdx.x * kQuadInnerX - kQuadS;   // global x of staged column 0
   const int gy0 = blockIdx.y * TY - kQuadS;            // global y of staged row 0
   const int gx = gx0 + 4 * lane;
@@ -65,22 +72,30 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
   const int64_t N = g.N;
 
   // zero the padding columns once (read as neighbours of edge cells that no valid cell uses)
-  for (int i = threadIdx.x; i < 8 * ROWS; i += kQuadThreads) {
+  for (int i = threadIdx.x; i < 8 * ROWS; i += NT) {
     const int row = i >> 3, k = i & 7;
     const int col = (k < 4) ? k : kQuadPad + kQuadCols + (k - 4);
-    float* base[8] = {bufA, bufA + PLANE, bufB, bufB + PLANE, bufH, bufH + PLANE, kxs, kys};
+    float* base[7] = {bufA, bufA + PLANE, bufB, bufB + PLANE, kxs, kys, kds};
 #pragma unroll
-    for (int b = 0; b < 8; ++b) base[b][(size_t)row * kQuadStride + col] = 0.f;
+    for (int b = 0; b < 7; ++b) base[b][(size_t)row * kQuadStride + col] = 0.f;
   }
-  // stage the face coefficients of the whole staged region (zero outside the grid)
+  // stage the face coefficients and the diagonal of the whole staged region (zero outside the grid)
   for (int ly = warp; ly < ROWS; ly += NW) {
     const int gy = gy0 + ly;
     const bool ok = colok && gy >= 0 && gy < g.n1;
     const int64_t c = (int64_t)g.n0 * gy + gx;
     const F4 a = ok ? ld4(cx + c) : zero4();
     const F4 b = ok ? ld4(cy + c) : zero4();
+    const F4 bs = (ok && gy > 0) ? ld4(cy + c - g.n0) : zero4();
+    float aw = __shfl_up_sync(0xffffffffu, a.v[3], 1);
+    if (lane == 0) aw = (ok && gx > 0) ? __ldg(cx + c - 1) : 0.f;
+    const float kw[4] = {aw, a.v[0], a.v[1], a.v[2]};
+    F4 d;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d.v[e] = ok ? 1.f + ((a.v[e] + kw[e]) + (b.v[e] + bs.v[e])) : 0.f;
     st4(kxs + (size_t)ly * kQuadStride + kQuadPad + 4 * lane, a);
     st4(kys + (size_t)ly * kQuadStride + kQuadPad + 4 * lane, b);
+    st4(kds + (size_t)ly * kQuadStride + kQuadPad + 4 * lane, d);
   }
 
   const int npass = ELL / 2;
@@ -92,8 +107,11 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
     const int m0 = (pass == 0) ? 0 : pass;      // frequency of plane p0
     const int m1 = (pass == 0) ? ELL / 2 : pass;  // frequency of plane p1
     __syncthreads();  // previous pass finished reading the buffers
-    // ---- stage x_k (bufA), x_{k-1} (bufB) and bhat (bufH) on the staged region
-    for (int ly = warp; ly < ROWS; ly += NW) {
+    // ---- stage x_k (bufA) and x_{k-1} (bufB) on the staged region; bhat into registers
+#pragma unroll
+    for (int rr = 0; rr < RPW; ++rr) {
+      const int ly = warp + rr * NW;
+      if (ly >= ROWS) break;
       const int gy = gy0 + ly;
       const bool ok = colok && gy >= 0 && gy < g.n1;
       const int64_t c = (int64_t)g.n0 * gy + gx;
@@ -122,10 +140,10 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
       }
       st4(bufA + o, x0);
       st4(bufA + PLANE + o, x1);
-      st4(bufH + o, h0);
-      st4(bufH + PLANE + o, h1);
       st4(bufB + o, m0v);
       st4(bufB + PLANE + o, m1v);
+      hreg[rr][0] = h0;
+      hreg[rr][1] = h1;
     }
     // ---- four levels; level q+1 lives where level q-1 was
     float* cur = bufA;   // level q
@@ -135,7 +153,10 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
       __syncthreads();
       const StepArgs<float>& st = qa.s[lv];
       const int lo = lv + 1;  // valid region of the new level: rows/cols [lo, extent - lo)
-      for (int ly = warp; ly < ROWS; ly += NW) {
+#pragma unroll
+      for (int rr = 0; rr < RPW; ++rr) {
+        const int ly = warp + rr * NW;
+        if (ly >= ROWS) break;
         if (ly < lo || ly >= ROWS - lo) continue;
         const size_t o = (size_t)ly * kQuadStride + kQuadPad + 4 * lane;
         // coefficients of the four cells (E: own cx, W: cx of the left cell, N: own cy, S: cy of the row below)
@@ -143,11 +164,14 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
         const float kxw = kxs[o - 1];
         const float4 kyn = *reinterpret_cast<const float4*>(kys + o);
         const float4 kys_ = *reinterpret_cast<const float4*>(kys + o - kQuadStride);
+        const float4 kdd = *reinterpret_cast<const float4*>(kds + o);
         const float kE[4] = {kxe.x, kxe.y, kxe.z, kxe.w};
         const float kW[4] = {kxw, kxe.x, kxe.y, kxe.z};
         const float kN[4] = {kyn.x, kyn.y, kyn.z, kyn.w};
         const float kS[4] = {kys_.x, kys_.y, kys_.z, kys_.w};
-        float Ax[2][4], xc[2][4], xm[2][4], bh[2][4];
+        const float kD[4] = {kdd.x, kdd.y, kdd.z, kdd.w};
+        // nb[pl][e] = bhat + sum of kappa * neighbour values; xc = centre; xm = level q-1
+        float nb[2][4], xc[2][4], xm[2][4];
 #pragma unroll
         for (int pl = 0; pl < 2; ++pl) {
           const float* rp = cur + (size_t)pl * PLANE + o;
@@ -159,23 +183,19 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
           const float n4[4] = {nn.x, nn.y, nn.z, nn.w};
           const float s4[4] = {ss.x, ss.y, ss.z, ss.w};
           const float4 mm = *reinterpret_cast<const float4*>(oth + (size_t)pl * PLANE + o);
-          const float4 hh = *reinterpret_cast<const float4*>(bufH + (size_t)pl * PLANE + o);
           const float m4[4] = {mm.x, mm.y, mm.z, mm.w};
-          const float h4[4] = {hh.x, hh.y, hh.z, hh.w};
+          const F4& h4v = hreg[rr][pl];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const float x = c4[e];
             const float xe = (e < 3) ? c4[e + 1] : right;
             const float xw = (e > 0) ? c4[e - 1] : left;
-            float acc = x;
-            acc += kE[e] * (x - xe);
-            acc += kW[e] * (x - xw);
-            acc += kN[e] * (x - n4[e]);
-            acc += kS[e] * (x - s4[e]);
-            Ax[pl][e] = acc;
-            xc[pl][e] = x;
+            float acc = fmaf(kE[e], xe, h4v.v[e]);
+            acc = fmaf(kW[e], xw, acc);
+            acc = fmaf(kN[e], n4[e], acc);
+            acc = fmaf(kS[e], s4[e], acc);
+            nb[pl][e] = acc;
+            xc[pl][e] = c4[e];
             xm[pl][e] = m4[e];
-            bh[pl][e] = h4[e];
           }
         }
         float n0v[4], n1v[4];
@@ -185,16 +205,18 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
             const float lr = st.lam_re[m0], li = st.lam_im[m0];
             const float ar = st.a_re[m0], ai = st.a_im[m0], gr = st.g_re[m0], gi = st.g_im[m0];
             const float xr = xc[0][e], xi = xc[1][e];
-            const float rr = bh[0][e] - Ax[0][e] + (lr * xr - li * xi);
-            const float ri = bh[1][e] - Ax[1][e] + (lr * xi + li * xr);
+            const float dl = kD[e] - lr;
+            // b - (A - lambda) x, real and imaginary parts
+            const float rr_ = fmaf(-li, xi, fmaf(-dl, xr, nb[0][e]));
+            const float ri = fmaf(li, xr, fmaf(-dl, xi, nb[1][e]));
             const float dr = xr - xm[0][e], di = xi - xm[1][e];
-            n0v[e] = xr + (ar * dr - ai * di) + (gr * rr - gi * ri);
-            n1v[e] = xi + (ar * di + ai * dr) + (gr * ri + gi * rr);
+            n0v[e] = fmaf(-gi, ri, fmaf(gr, rr_, fmaf(-ai, di, fmaf(ar, dr, xr))));
+            n1v[e] = fmaf(gi, rr_, fmaf(gr, ri, fmaf(ai, dr, fmaf(ar, di, xi))));
           } else {
-            const float r0 = bh[0][e] - Ax[0][e] + st.lam_re[m0] * xc[0][e];
-            const float r1 = bh[1][e] - Ax[1][e] + st.lam_re[m1] * xc[1][e];
-            n0v[e] = xc[0][e] + st.a_re[m0] * (xc[0][e] - xm[0][e]) + st.g_re[m0] * r0;
-            n1v[e] = xc[1][e] + st.a_re[m1] * (xc[1][e] - xm[1][e]) + st.g_re[m1] * r1;
+            const float r0 = fmaf(-(kD[e] - st.lam_re[m0]), xc[0][e], nb[0][e]);
+            const float r1 = fmaf(-(kD[e] - st.lam_re[m1]), xc[1][e], nb[1][e]);
+            n0v[e] = fmaf(st.g_re[m0], r0, fmaf(st.a_re[m0], xc[0][e] - xm[0][e], xc[0][e]));
+            n1v[e] = fmaf(st.g_re[m1], r1, fmaf(st.a_re[m1], xc[1][e] - xm[1][e], xc[1][e]));
           }
         }
         *reinterpret_cast<float4*>(oth + o) = make_float4(n0v[0], n0v[1], n0v[2], n0v[3]);
@@ -221,23 +243,29 @@ __global__ void __launch_bounds__(kQuadThreads, 2)
   }
 }
 
+template <int ELL, int TY, int NT>
+cudaError_t launch_quad_cfg(const GridDesc& g, int psrc, const float* cx, const float* cy, const float* bhat,
+                            const float* xk, const float* xkm1, float* out3, float* out4, const QuadArgs& qa,
+                            cudaStream_t s) {
+  const dim3 block(NT, 1, 1);
+  const dim3 grid((unsigned)((g.n0 + kQuadInnerX - 1) / kQuadInnerX), (unsigned)((g.n1 + TY - 1) / TY), 1);
+  const size_t smem = quad_smem_bytes<TY>();
+  if (psrc == 1) {
+    cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cheb_quad<ELL, TY, 1, NT><<<grid, block, smem, s>>>(g, cx, cy, bhat, xk, xkm1, out3, out4, qa);
+  } else {
+    cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cheb_quad<ELL, TY, 2, NT><<<grid, block, smem, s>>>(g, cx, cy, bhat, xk, xkm1, out3, out4, qa);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <int ELL>
 cudaError_t launch_quad_ell(const GridDesc& g, int psrc, const float* cx, const float* cy, const float* bhat,
                             const float* xk, const float* xkm1, float* out3, float* out4, const QuadArgs& qa,
                             cudaStream_t s) {
-  constexpr int TY = 16;
-  const dim3 block(kQuadThreads, 1, 1);
-  const dim3 grid((unsigned)((g.n0 + kQuadInnerX - 1) / kQuadInnerX), (unsigned)((g.n1 + TY - 1) / TY), 1);
-  const size_t smem = quad_smem_bytes<TY>();
-  if (psrc == 1) {
-    cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cheb_quad<ELL, TY, 1><<<grid, block, smem, s>>>(g, cx, cy, bhat, xk, xkm1, out3, out4, qa);
-  } else {
-    cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cheb_quad<ELL, TY, 2><<<grid, block, smem, s>>>(g, cx, cy, bhat, xk, xkm1, out3, out4, qa);
-  }
-  count_launch();
-  return cudaGetLastError();
+  return launch_quad_cfg<ELL, 16, 384>(g, psrc, cx, cy, bhat, xk, xkm1, out3, out4, qa, s);
 }
 
 }  // namespace aao
