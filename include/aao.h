@@ -173,6 +173,27 @@ int aao_solve(aao_handle h, const double* b, double* x, double tol, int max_oute
  * arguments as aao_solve.  Returns AAO_OK (or an error). */
 int aao_solve_fixed(aao_handle h, const double* b, double* x, int k, int inner_its);
 
+/*
+ * Per-frequency inner budgets (P_NC2, Section 5 and Algorithm 1): frequency j
+ * (shift lambda_{j+1}) runs p[j] Chebyshev steps instead of the handle's
+ * common count.  p has ell entries with p[j] == p[ell-j] (conjugate shifts
+ * share a budget, Section 3); p[j] = 0 gives y_j = 0.  Frequencies whose
+ * budget is spent keep their iterate while the others continue (their
+ * recurrence coefficients are set to zero), so an apply runs max_j p[j]
+ * steps.  Stays in force until aao_solve is called with inner_its > 0.
+ */
+int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
+
+/*
+ * Algorithm 1 of the paper, on the host: share ell * nx * eta inner
+ * iterations among the ell shifted problems in proportion to
+ * ln(sigma_1) / ln(sigma_j), sigma_j from Theorem 4 on [mu_min, mu_max], and
+ * round each share down.  out receives ell counts.  Returns AAO_EINVAL on bad
+ * arguments (ell odd, mu_max <= mu_min, alpha^(1/ell) >= mu_min, ...).
+ */
+int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, double alpha, double eta,
+                          int32_t* out);
+
 /* Copy the statistics of the last solve into *s. */
 int aao_get_stats(aao_handle h, aao_stats* s);
 

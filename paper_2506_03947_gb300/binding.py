@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA",
 EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_apply", "aao_solve",
             "aao_solve_fixed", "aao_get_stats", "aao_get_bounds", "aao_last_error",
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
-            "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc")
+            "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
+            "aao_set_inner_alloc", "aao_assign_iterations")
 
 AAO_NPROF = 9
 PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair",
@@ -101,6 +102,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_precond_apply_noalloc.argtypes = [i32, C.POINTER(C.c_int64), vp, vp, vp, i32, dbl, i32, i32,
                                               dbl, vp, vp, vp, C.c_char_p, i32]
     lib.aao_precond_apply_noalloc.restype = i32
+    lib.aao_set_inner_alloc.argtypes = [vp, C.POINTER(C.c_int32), i32]
+    lib.aao_set_inner_alloc.restype = i32
+    lib.aao_assign_iterations.argtypes = [i32, C.c_int64, dbl, dbl, dbl, dbl, C.POINTER(C.c_int32)]
+    lib.aao_assign_iterations.restype = i32
     _lib = lib
     return lib
 
@@ -212,6 +217,20 @@ def aao_precond_apply_noalloc(dim: int, n: Sequence[int], kx, ky, kz, ell: int, 
     return rc
 
 
+def aao_set_inner_alloc(h, p) -> int:
+    arr = (C.c_int32 * len(p))(*[int(v) for v in p])
+    return _check(h, load_library().aao_set_inner_alloc(h, arr, len(p)))
+
+
+def aao_assign_iterations(ell: int, nx: int, mu_max: float, mu_min: float, alpha: float, eta: float):
+    out = (C.c_int32 * int(ell))()
+    rc = load_library().aao_assign_iterations(int(ell), int(nx), float(mu_max), float(mu_min), float(alpha),
+                                              float(eta), out)
+    if rc != AAO_OK:
+        raise AaoError(rc, "aao_assign_iterations: invalid arguments")
+    return [int(v) for v in out]
+
+
 def aao_destroy(h) -> None:
     if h:
         load_library().aao_destroy(h)
@@ -251,6 +270,9 @@ class Solver:
 
     def bounds(self):
         return aao_get_bounds(self.h)
+
+    def set_inner_alloc(self, p):
+        return aao_set_inner_alloc(self.h, p)
 
     def profile_enable(self, on=True):
         return aao_profile_enable(self.h, on)

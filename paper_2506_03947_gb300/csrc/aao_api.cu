@@ -39,7 +39,9 @@ struct aao_ctx {
   int ell = 0;
   double alpha = 0.0;
   int prec = AAO_MIXED;
-  int p = 20;
+  int p = 20;                    // Chebyshev steps run per apply (max over frequencies)
+  int palloc[aao::kMaxF] = {};   // per-frequency steps m = 0..ell/2 (NC2); all == p for NC1
+  bool nc2 = false;
   int m = 64;
   int reorth = 1;
   double mu_min = 1.0, mu_max = 0.0;
@@ -172,7 +174,10 @@ void build_tables(aao_ctx* h) {
     StepArgs<double>& s = h->steps64[k];
     for (int m = 0; m < F; ++m) {
       cd a(0.0, 0.0), gk(0.0, 0.0);
-      if (k >= 1 && delta == 0.0) {
+      const int pm = h->nc2 ? h->palloc[m] : p;
+      if (k >= 1 && k >= pm) {
+        // frequency m has used its budget (Algorithm 1): a = g = 0 keeps x_{k+1} = x_k
+      } else if (k >= 1 && delta == 0.0) {
         // single-point segment (one cell, A = I): the delta -> 0 limit is the
         // exact solve, a = 0 and g = 1/theta
         gk = 1.0 / theta[m];
@@ -182,7 +187,8 @@ void build_tables(aao_ctx* h) {
         gk = 2.0 * rho / delta;
         rho_prev[m] = rho;
       }
-      const cd it = 1.0 / theta[m];
+      // a zero budget means y_m = 0: x_1 = bhat * 0
+      const cd it = (h->nc2 && h->palloc[m] == 0) ? cd(0.0, 0.0) : 1.0 / theta[m];
       s.lam_re[m] = lam[m].real();
       s.lam_im[m] = lam[m].imag();
       s.a_re[m] = a.real();
@@ -420,7 +426,15 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
   std::memset(&st, 0, sizeof(st));
   st.mu_min = h->mu_min;
   st.mu_max = h->mu_max;
-  const int64_t per_outer = (int64_t)h->ell * h->p + h->ell;
+  int64_t inner_total = (int64_t)h->ell * h->p;  // A-matvecs of one preconditioner apply (Table 1)
+  if (h->nc2) {
+    inner_total = 0;
+    for (int j = 0; j < h->ell; ++j) {
+      const int mm = (j <= h->ell / 2) ? j : h->ell - j;  // conjugate shifts share a budget
+      inner_total += h->palloc[mm];
+    }
+  }
+  const int64_t per_outer = inner_total + h->ell;
 
   // ||b||
   AAO_CK(h, aao::launch_norm2_partials(b, L, h->partials, s));
@@ -752,8 +766,9 @@ static int solve_entry(aao_handle h, const double* b, double* x, double tol, int
   if (max_outer < 1) return fail(h, AAO_EINVAL, "max_outer must be >= 1");
   if (fixed && fixed > h->m) return fail(h, AAO_EINVAL, "fixed step count %d exceeds restart %d", fixed, h->m);
   if (inner_its < 0 || inner_its > 100000) return fail(h, AAO_EINVAL, "inner_its must be in [0, 100000]");
-  if (inner_its > 0 && inner_its != h->p) {
+  if (inner_its > 0 && (inner_its != h->p || h->nc2)) {
     h->p = inner_its;
+    h->nc2 = false;
     build_tables(h);
   }
   const bool hb = !is_device_ptr(b), hx = !is_device_ptr(x);
@@ -803,6 +818,47 @@ int aao_profile_get(aao_handle h, aao_profile* out) {
   AAO_CK(h, cudaStreamSynchronize(h->stream));
   prof_resolve(h);
   *out = h->profacc;
+  return AAO_OK;
+}
+
+int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (!p || ell != h->ell) return fail(h, AAO_EINVAL, "p must hold ell = %d counts", h->ell);
+  int pmax = 0;
+  for (int j = 0; j < ell; ++j) {
+    if (p[j] < 0 || p[j] > 100000) return fail(h, AAO_EINVAL, "step counts must be in [0, 100000]");
+    if (j > 0 && p[j] != p[ell - j])
+      return fail(h, AAO_EINVAL, "conjugate shifts need equal counts: p[%d] = %d but p[%d] = %d", j, p[j], ell - j,
+                  p[ell - j]);
+    pmax = std::max(pmax, (int)p[j]);
+  }
+  if (pmax < 1) return fail(h, AAO_EINVAL, "at least one frequency needs a step");
+  for (int m = 0; m <= ell / 2; ++m) h->palloc[m] = p[m];
+  h->nc2 = true;
+  h->p = pmax;
+  build_tables(h);
+  return AAO_OK;
+}
+
+int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, double alpha, double eta, int32_t* out) {
+  if (ell < 2 || (ell % 2) || nx < 1 || !(mu_max > mu_min) || !(alpha > 0.0) || !(eta > 0.0) || !out ||
+      !(std::pow(alpha, 1.0 / ell) < mu_min))
+    return AAO_EINVAL;
+  using cd = std::complex<double>;
+  const double pi = 3.14159265358979323846;
+  const double root = std::pow(alpha, 1.0 / ell);
+  std::vector<double> r(ell);
+  double sig1 = 0.0, sum = 0.0;
+  for (int j = 0; j < ell; ++j) {
+    const cd lam = root * std::exp(cd(0.0, -2.0 * pi * j / ell));
+    // sigma_j of Theorem 4: condition number of Re(B_j) on [mu_min, mu_max]
+    const double kap = (mu_max - lam.real()) / (mu_min - lam.real());
+    const double sig = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    if (j == 0) sig1 = sig;
+    r[j] = std::log(sig1) / std::log(sig);
+    sum += r[j];
+  }
+  for (int j = 0; j < ell; ++j) out[j] = (int32_t)std::floor(r[j] / sum * (double)ell * (double)nx * eta);
   return AAO_OK;
 }
 

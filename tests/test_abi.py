@@ -70,3 +70,19 @@ def test_no_gpu_means_loud_failure(lib):
     with pytest.raises(binding.AaoError) as ei:
         binding.aao_create(1, (8, 1, 1), np.ones(7), None, None, 10, 1e-2)
     assert ei.value.status == binding.AAO_ECUDA
+
+
+def test_assign_iterations_matches_oracle_and_tables(lib):
+    # Algorithm 1 on the host side of the library (no device needed) against the oracle,
+    # on the paper's operator (Eq. 17) settings of Tables 3 and 4
+    from oracle import operator, spectral
+    from paper_2506_03947_gb300 import binding
+    for ell, nx, alpha, eta in ((10, 100, 1.0, 0.2), (10, 500, 0.01, 0.2), (6, 100, 1.0, 0.3), (16, 100, 0.01, 0.1)):
+        mn, mx = operator.dirichlet_mu_bounds(nx, ell)
+        got = binding.aao_assign_iterations(ell, nx, mx, mn, alpha, eta)
+        ref = spectral.assign_iterations(ell, nx, mx, mn, alpha, eta)
+        assert got == [int(v) for v in ref]
+    mn, mx = operator.dirichlet_mu_bounds(100, 10)
+    assert sum(binding.aao_assign_iterations(10, 100, mx, mn, 1.0, 0.2)) == 193   # Table 3: 3248 = 16 x (10 + 193)
+    with pytest.raises(binding.AaoError):
+        binding.aao_assign_iterations(9, 100, mx, mn, 1.0, 0.2)

@@ -1,0 +1,72 @@
+"""P_NC2 (Algorithm 1's per-frequency budgets) on the GPU against the oracle."""
+import numpy as np
+import pytest
+
+from gpu_util import log_record, make_solver, oracle_ops, precond_tol, to_dev, torch_cuda
+from oracle import allatonce, precond, solve
+from paper_2506_03947_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("alloc", [[9, 4, 3, 2, 2, 1, 2, 2, 3, 4], [30, 13, 7, 5, 4, 4, 4, 5, 7, 13],
+                                   [5, 0, 2, 1, 3, 6, 3, 1, 2, 0]])
+def test_nc2_precond_parity(alloc, prec):
+    torch = torch_cuda()
+    for P in (inputs.config_2d(n=64, alpha=0.5), inputs.make_problem("r", 2, (37, 29), 10, 1e-2, 1, 0.5,
+                                                                     (16.0, 16.0), 3, 4)):
+        A, mu_max = oracle_ops(P)
+        r = np.random.default_rng(5).standard_normal((P.ell, P.N))
+        ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, alloc)
+        s = make_solver(P, prec, 7)
+        s.set_inner_alloc(alloc)
+        rd = to_dev(r)
+        zd = torch.empty_like(rd)
+        s.precond_apply(rd, zd)
+        err = np.abs(zd.cpu().numpy() - ref).max() / np.abs(ref).max()
+        tol = precond_tol(prec, max(alloc), P.ell, P.alpha)
+        log_record({"test": "nc2_precond", "n": P.n[0], "alloc": alloc, "prec": prec, "err": err, "tol": tol})
+        assert err <= tol, (err, tol)
+
+
+def test_nc2_rejects_asymmetric_alloc():
+    from paper_2506_03947_gb300 import binding
+    P = inputs.config_2d(n=16)
+    s = make_solver(P, 1, 5)
+    with pytest.raises(binding.AaoError):
+        s.set_inner_alloc([5, 4, 3, 2, 1, 1, 2, 3, 4, 6])
+    with pytest.raises(binding.AaoError):
+        s.set_inner_alloc([5, 4, 3])
+
+
+def test_nc2_solve_matches_oracle_and_spends_the_budget_better():
+    # Same total inner budget (ell * n_x * eta) split evenly (NC1) or by Algorithm 1 (NC2);
+    # alpha close to 1 makes the real shift's problem hardest, where NC2 helps most (Section 5).
+    torch = torch_cuda()
+    from oracle import spectral, operator
+    P = inputs.config_2d(n=48, alpha=0.5)
+    _, mu_max = oracle_ops(P)
+    eta, nx = 0.2, 48
+    alloc = [int(v) for v in spectral.assign_iterations(P.ell, nx, mu_max, 1.0, P.alpha, eta)]
+    p1 = int(round(P.ell * nx * eta / P.ell))
+    ref1 = solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p1, 1e-8, 64)
+    ref2 = solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, alloc, 1e-8, 64)
+    res = {}
+    for name, setup in (("nc1", lambda s: None), ("nc2", lambda s: s.set_inner_alloc(alloc))):
+        s = make_solver(P, 0, p1)
+        setup(s)
+        bd = to_dev(P.b)
+        xd = torch.zeros_like(bd)
+        s.solve(bd, xd, 1e-8, 64)
+        res[name] = (s.stats(), xd.cpu().numpy())
+    assert res["nc1"][0]["outer_its"] == ref1.outer_its
+    assert res["nc2"][0]["outer_its"] == ref2.outer_its
+    e2 = np.linalg.norm(res["nc2"][1] - ref2.x) / np.linalg.norm(ref2.x)
+    log_record({"test": "nc2_solve", "its_nc1": ref1.outer_its, "its_nc2": ref2.outer_its, "err": e2,
+                "alloc": alloc})
+    assert e2 <= 1e-10
+    assert ref2.outer_its < ref1.outer_its
+    # A-matvec accounting: ell + sum(alloc) per Arnoldi step (Table 1 with Algorithm 1)
+    st = res["nc2"][0]
+    assert st["a_matvecs"] == st["outer_its"] * (P.ell + sum(alloc)) + (st["cycles"] + 1) * P.ell
