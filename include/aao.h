@@ -194,6 +194,24 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
 int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, double alpha, double eta,
                           int32_t* out);
 
+/*
+ * The paper's own outer solver: Chebyshev semi-iteration on the
+ * preconditioned system P^{-1} script-A x = P^{-1} b (Eq. 3, Section 5) over
+ * the eigenvalue interval [l_min, l_max] of P^{-1} script-A.  Passing
+ * l_min = l_max = 0 takes Corollary 1's interval
+ * [1, mu_N^ell / (mu_N^ell - alpha)] for the exact P_alpha, kept unchanged for
+ * the inexact P_NC as in Section 5.  Each iteration costs one script-A product
+ * and one preconditioner apply (Table 1).  The residual is updated as
+ * r <- r - script-A d in FP64; convergence is ||b - script-A x|| / ||b|| < tol,
+ * certified by an explicit residual at the end.
+ *   fixed_its > 0 runs exactly that many iterations (tol ignored).
+ * Other arguments as aao_solve.  Needs restart >= 2 (it uses the Krylov
+ * workspace).  Returns AAO_ENOTCONV if max_outer iterations do not reach tol
+ * (CI can stagnate when P_NC is far from P_alpha).
+ */
+int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_outer, int inner_its, int use_x0,
+                 double l_min, double l_max, int fixed_its);
+
 /* Copy the statistics of the last solve into *s. */
 int aao_get_stats(aao_handle h, aao_stats* s);
 

@@ -26,7 +26,7 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_solve_fixed", "aao_get_stats", "aao_get_bounds", "aao_last_error",
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
-            "aao_set_inner_alloc", "aao_assign_iterations")
+            "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci")
 
 AAO_NPROF = 9
 PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair",
@@ -102,6 +102,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_precond_apply_noalloc.argtypes = [i32, C.POINTER(C.c_int64), vp, vp, vp, i32, dbl, i32, i32,
                                               dbl, vp, vp, vp, C.c_char_p, i32]
     lib.aao_precond_apply_noalloc.restype = i32
+    lib.aao_solve_ci.argtypes = [vp, vp, vp, dbl, i32, i32, i32, dbl, dbl, i32]
+    lib.aao_solve_ci.restype = i32
     lib.aao_set_inner_alloc.argtypes = [vp, C.POINTER(C.c_int32), i32]
     lib.aao_set_inner_alloc.restype = i32
     lib.aao_assign_iterations.argtypes = [i32, C.c_int64, dbl, dbl, dbl, dbl, C.POINTER(C.c_int32)]
@@ -168,6 +170,14 @@ def aao_solve(h, b, x, tol: float, max_outer: int, inner_its: int = 0, use_x0: b
 
 def aao_solve_fixed(h, b, x, k: int, inner_its: int = 0) -> int:
     return _check(h, load_library().aao_solve_fixed(h, _ptr(b), _ptr(x), int(k), int(inner_its)))
+
+
+def aao_solve_ci(h, b, x, tol: float, max_outer: int, inner_its: int = 0, use_x0: bool = False,
+                 l_min: float = 0.0, l_max: float = 0.0, fixed_its: int = 0, allow_notconv: bool = False) -> int:
+    ok = (AAO_OK, AAO_ENOTCONV) if allow_notconv else (AAO_OK,)
+    return _check(h, load_library().aao_solve_ci(h, _ptr(b), _ptr(x), float(tol), int(max_outer), int(inner_its),
+                                                 1 if use_x0 else 0, float(l_min), float(l_max), int(fixed_its)),
+                  ok)
 
 
 def aao_get_stats(h) -> dict:
@@ -261,6 +271,11 @@ class Solver:
 
     def solve(self, b, x, tol, max_outer, inner_its=0, use_x0=False, allow_notconv=False):
         return aao_solve(self.h, b, x, tol, max_outer, inner_its, use_x0, allow_notconv)
+
+    def solve_ci(self, b, x, tol, max_outer, inner_its=0, use_x0=False, l_min=0.0, l_max=0.0, fixed_its=0,
+                 allow_notconv=False):
+        return aao_solve_ci(self.h, b, x, tol, max_outer, inner_its, use_x0, l_min, l_max, fixed_its,
+                            allow_notconv)
 
     def solve_fixed(self, b, x, k, inner_its=0):
         return aao_solve_fixed(self.h, b, x, k, inner_its)

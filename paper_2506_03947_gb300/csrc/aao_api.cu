@@ -525,6 +525,87 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
   }
 }
 
+// Outer Chebyshev semi-iteration on P^{-1} script-A x = P^{-1} b over [l_min, l_max]
+// (Section 5 with Corollary 1's interval), residual updated as r -= script-A d.
+int solve_ci_impl(aao_ctx* h, const double* b, double* x, double tol, int max_its, double l_min, double l_max,
+                  int fixed) {
+  const ScLayout Lsc{h->m};
+  const int64_t L = h->L;
+  cudaStream_t s = h->stream;
+  aao_stats& st = h->stats;
+  std::memset(&st, 0, sizeof(st));
+  st.mu_min = h->mu_min;
+  st.mu_max = h->mu_max;
+  int64_t inner_total = (int64_t)h->ell * h->p;
+  if (h->nc2) {
+    inner_total = 0;
+    for (int j = 0; j < h->ell; ++j) inner_total += h->palloc[(j <= h->ell / 2) ? j : h->ell - j];
+  }
+  AAO_CK(h, aao::launch_norm2_partials(b, L, h->partials, s));
+  AAO_CK(h, aao::launch_reduce(h->partials, 1, aao::reduction_blocks(L), h->sc + Lsc.nrm2(), 0, s));
+  double bn2 = 0.0;
+  int rc = read_scalars(h, Lsc.nrm2(), 1, &bn2);
+  if (rc) return rc;
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) return fail(h, AAO_ENUMERIC, "||b|| is not finite");
+  if (bnorm == 0.0) {
+    AAO_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * L, s));
+    AAO_CK(h, cudaStreamSynchronize(s));
+    st.converged = 1;
+    return AAO_OK;
+  }
+  double* r = h->V;
+  double* r2 = h->V + L;
+  double* z = h->Z;
+  double* d = h->Z + L;
+  const double theta = 0.5 * (l_max + l_min), delta = 0.5 * (l_max - l_min);
+  const double sigma1 = delta > 0.0 ? theta / delta : 0.0;
+  double rho = delta > 0.0 ? 1.0 / sigma1 : 0.0;
+  double rn2 = 0.0;
+  rc = residual(h, b, x, r, &rn2);  // r = b - script-A x
+  if (rc) return rc;
+  st.a_matvecs += h->ell;
+  rc = precond(h, r, nullptr, z);
+  if (rc) return rc;
+  double c1 = 0.0, c2 = 1.0 / theta;
+  const int nmax = fixed ? fixed : max_its;
+  for (int it = 0; it < nmax; ++it) {
+    AAO_CK(h, aao::launch_ci_update(d, z, x, c1, c2, L, s));  // d_k, x_{k+1} = x_k + d_k
+    rc = residual(h, r, d, r2, &rn2);                           // r_{k+1} = r_k - script-A d_k
+    if (rc) return rc;
+    std::swap(r, r2);
+    st.outer_its = it + 1;
+    st.a_matvecs += h->ell + inner_total;
+    const double rel = std::sqrt(rn2) / bnorm;
+    st.resid_est = rel;
+    if (st.n_hist < AAO_MAX_HIST) st.hist[st.n_hist++] = rel;
+    if (!std::isfinite(rel)) return fail(h, AAO_ENUMERIC, "outer Chebyshev residual is not finite");
+    if (!fixed && rel < tol) break;
+    if (it + 1 == nmax) break;
+    rc = precond(h, r, nullptr, z);
+    if (rc) return rc;
+    if (delta > 0.0) {
+      const double rho_next = 1.0 / (2.0 * sigma1 - rho);
+      c1 = rho_next * rho;
+      c2 = 2.0 * rho_next / delta;
+      rho = rho_next;
+    } else {
+      c1 = 0.0;
+      c2 = 1.0 / theta;
+    }
+  }
+  // explicit residual of the final iterate
+  rc = residual(h, b, x, r2, &rn2);
+  if (rc) return rc;
+  st.a_matvecs += h->ell;
+  st.resid_explicit = std::sqrt(rn2) / bnorm;
+  st.converged = st.resid_explicit < tol;
+  if (!fixed && !st.converged)
+    return fail(h, AAO_ENOTCONV, "outer Chebyshev: no convergence in %d iterations (rel. residual %.3e)",
+                st.outer_its, st.resid_explicit);
+  return AAO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -860,6 +941,53 @@ int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, dou
   }
   for (int j = 0; j < ell; ++j) out[j] = (int32_t)std::floor(r[j] / sum * (double)ell * (double)nx * eta);
   return AAO_OK;
+}
+
+int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_outer, int inner_its, int use_x0,
+                 double l_min, double l_max, int fixed_its) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  h->err.clear();
+  if (!b || !x || b == x) return fail(h, AAO_EINVAL, "b and x must be distinct non-NULL pointers");
+  if (!fixed_its && !(tol > 0.0 && tol < 1.0)) return fail(h, AAO_EINVAL, "tol must be in (0, 1)");
+  if (max_outer < 1 && !fixed_its) return fail(h, AAO_EINVAL, "max_outer must be >= 1");
+  if (fixed_its < 0) return fail(h, AAO_EINVAL, "fixed_its must be >= 0");
+  if (h->m < 2) return fail(h, AAO_EINVAL, "the outer Chebyshev solve needs restart >= 2 (workspace)");
+  if (l_min <= 0.0 && l_max <= 0.0) {
+    // Corollary 1: [1, mu_N^ell / (mu_N^ell - alpha)]
+    const double mell = std::pow(h->mu_min, h->ell);
+    l_min = 1.0;
+    l_max = mell / (mell - h->alpha);
+  }
+  if (!(l_min > 0.0 && l_max >= l_min && std::isfinite(l_max)))
+    return fail(h, AAO_EINVAL, "need 0 < l_min <= l_max");
+  if (inner_its < 0 || inner_its > 100000) return fail(h, AAO_EINVAL, "inner_its must be in [0, 100000]");
+  if (inner_its > 0 && (inner_its != h->p || h->nc2)) {
+    h->p = inner_its;
+    h->nc2 = false;
+    build_tables(h);
+  }
+  const bool hb = !is_device_ptr(b), hx = !is_device_ptr(x);
+  int rc = (hb || hx) ? ensure_stage(h) : AAO_OK;
+  if (rc) return rc;
+  const double* db = b;
+  double* dx = x;
+  if (hb) {
+    AAO_CK(h, cudaMemcpyAsync(h->stage_a, b, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
+    db = h->stage_a;
+  }
+  if (hx) {
+    dx = h->stage_b;
+    if (use_x0) AAO_CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
+  }
+  if (!use_x0) AAO_CK(h, cudaMemsetAsync(dx, 0, sizeof(double) * h->L, h->stream));
+  rc = solve_ci_impl(h, db, dx, tol, max_outer, l_min, l_max, fixed_its);
+  if (hx && (rc == AAO_OK || rc == AAO_ENOTCONV)) {
+    cudaError_t e = cudaMemcpyAsync(x, dx, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, AAO_ECUDA, "copy of x to host: %s", cudaGetErrorString(e));
+  }
+  if (rc == AAO_OK || rc == AAO_ENOTCONV) AAO_CK(h, cudaStreamSynchronize(h->stream));
+  return rc;
 }
 
 int aao_get_stats(aao_handle h, aao_stats* s) {

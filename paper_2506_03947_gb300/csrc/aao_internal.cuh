@@ -121,6 +121,8 @@ cudaError_t launch_givens(double* sc, int j, int m, double bnorm, cudaStream_t s
 cudaError_t launch_backsolve(double* sc, int k, int m, cudaStream_t s);
 cudaError_t launch_xupdate(const double* Z, int64_t ldz, int k, const double* y, double* x, int64_t L,
                            cudaStream_t s);
+// d = c1 d + c2 z; x += d (outer Chebyshev iteration).
+cudaError_t launch_ci_update(double* d, const double* z, double* x, double c1, double c2, int64_t L, cudaStream_t s);
 // Starting vector of a cycle: sc[vscale 0] = 1/sqrt(nrm2), g[0] = sqrt(nrm2), clears H/g.
 cudaError_t launch_cycle_init(double* sc, int m, cudaStream_t s);
 

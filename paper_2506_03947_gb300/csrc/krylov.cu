@@ -415,6 +415,24 @@ cudaError_t launch_xupdate(const double* Z, int64_t ldz, int k, const double* y,
   return cudaGetLastError();
 }
 
+// Outer Chebyshev step (the paper's outer solver): d = c1 d + c2 z, then x += d.
+__global__ void __launch_bounds__(kRedThreads)
+    k_ci_update(double* __restrict__ d, const double* __restrict__ z, double* __restrict__ x, double c1, double c2,
+                int64_t L) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    const double dn = fma(c2, __ldg(z + e), c1 * d[e]);
+    d[e] = dn;
+    x[e] += dn;
+  }
+}
+
+cudaError_t launch_ci_update(double* d, const double* z, double* x, double c1, double c2, int64_t L, cudaStream_t s) {
+  k_ci_update<<<reduction_blocks(L), kRedThreads, 0, s>>>(d, z, x, c1, c2, L);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Start of a cycle: beta = sqrt(nrm2); g = (beta, 0, ..); vscale[0] = 1/beta.
 __global__ void k_cycle_init(double* sc, int m) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
