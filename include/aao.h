@@ -70,6 +70,7 @@ extern "C" {
 #define AAO_MAX_HIST 512    /* residual history entries kept in aao_stats       */
 
 typedef struct aao_ctx* aao_handle;
+typedef struct aao_batch_ctx* aao_batch;
 
 /* Options for aao_create.  Fill with aao_default_options first. */
 typedef struct {
@@ -211,6 +212,43 @@ int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, dou
  */
 int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_outer, int inner_its, int use_x0,
                  double l_min, double l_max, int fixed_its);
+
+/*
+ * Batched solve: many independent instances of Eq. 1 (different grids, ell,
+ * alpha, diffusivities and right-hand sides) solved together.  All members
+ * advance in lockstep through right-preconditioned FGMRES; every phase of an
+ * Arnoldi step (transform, each Chebyshev step, matvec, Gram-Schmidt passes,
+ * Givens) is one launch over all members (one per distinct ell for the
+ * Chebyshev kernels), each block mapped to an (instance, tile) pair; members
+ * that have converged skip their blocks.  With use_graphs != 0 each Arnoldi
+ * step is captured once as a CUDA graph and replayed.  The paper solves one
+ * instance at a time; batching is this library's addition for covariance
+ * operators applied to many fields at once.
+ *   members    count handles created with AAO_MIXED, dim 2, n[0] % 4 == 0, and
+ *              the same inner_its (>= 2) and restart; they must outlive the
+ *              batch, and the batch uses their workspace (do not use the
+ *              members concurrently with a batched solve).
+ * The batch has its own non-blocking stream.
+ */
+int aao_batch_create(aao_batch* hb, int count, const aao_handle* members, int use_graphs);
+
+/*
+ * Solve every member i: script-A_i x[i] = b[i] from x_0 = 0 to explicit
+ * relative residual < tol, at most max_outer Arnoldi steps each.  b and x
+ * are arrays of count DEVICE pointers (ell_i * N_i doubles each, block-major).
+ * Synchronises the device at entry and the batch stream at exit.  Returns
+ * AAO_ENOTCONV if any member did not converge (all x[i] hold their iterates).
+ */
+int aao_batch_solve(aao_batch hb, const double* const* b, double* const* x, double tol, int max_outer);
+
+/* Statistics of member i in the last batched solve. */
+int aao_batch_get_stats(aao_batch hb, int i, aao_stats* s);
+
+/* Message of the last failed batch call ("" if none). */
+const char* aao_batch_last_error(aao_batch hb);
+
+/* Release the batch (not its members).  NULL is allowed. */
+void aao_batch_destroy(aao_batch hb);
 
 /* Copy the statistics of the last solve into *s. */
 int aao_get_stats(aao_handle h, aao_stats* s);

@@ -26,7 +26,8 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_solve_fixed", "aao_get_stats", "aao_get_bounds", "aao_last_error",
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
-            "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci")
+            "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
+            "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy")
 
 AAO_NPROF = 9
 PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair",
@@ -102,6 +103,16 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_precond_apply_noalloc.argtypes = [i32, C.POINTER(C.c_int64), vp, vp, vp, i32, dbl, i32, i32,
                                               dbl, vp, vp, vp, C.c_char_p, i32]
     lib.aao_precond_apply_noalloc.restype = i32
+    lib.aao_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), i32]
+    lib.aao_batch_create.restype = i32
+    lib.aao_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), dbl, i32]
+    lib.aao_batch_solve.restype = i32
+    lib.aao_batch_get_stats.argtypes = [vp, i32, C.POINTER(aao_stats)]
+    lib.aao_batch_get_stats.restype = i32
+    lib.aao_batch_last_error.argtypes = [vp]
+    lib.aao_batch_last_error.restype = C.c_char_p
+    lib.aao_batch_destroy.argtypes = [vp]
+    lib.aao_batch_destroy.restype = None
     lib.aao_solve_ci.argtypes = [vp, vp, vp, dbl, i32, i32, i32, dbl, dbl, i32]
     lib.aao_solve_ci.restype = i32
     lib.aao_set_inner_alloc.argtypes = [vp, C.POINTER(C.c_int32), i32]
@@ -244,6 +255,57 @@ def aao_assign_iterations(ell: int, nx: int, mu_max: float, mu_min: float, alpha
 def aao_destroy(h) -> None:
     if h:
         load_library().aao_destroy(h)
+
+
+def _stats_dict(s):
+    return {"outer_its": s.outer_its, "cycles": s.cycles, "converged": bool(s.converged),
+            "a_matvecs": s.a_matvecs, "resid_est": s.resid_est,
+            "resid_explicit": s.resid_explicit, "mu_min": s.mu_min, "mu_max": s.mu_max,
+            "hist": [s.hist[i] for i in range(s.n_hist)]}
+
+
+class Batch:
+    """Batched solve over several Solver objects (aao_batch_*); marshalling only."""
+
+    def __init__(self, solvers, use_graphs=True):
+        lib = load_library()
+        self.solvers = list(solvers)          # members must outlive the batch
+        arr = (C.c_void_p * len(self.solvers))(*[s.h.value if hasattr(s.h, "value") else s.h
+                                                for s in self.solvers])
+        hb = C.c_void_p()
+        rc = lib.aao_batch_create(C.byref(hb), len(self.solvers), arr, 1 if use_graphs else 0)
+        if rc != AAO_OK:
+            raise AaoError(rc, (lib.aao_last_create_error() or b"").decode(errors="replace"))
+        self.hb = hb
+
+    def solve(self, bs, xs, tol, max_outer, allow_notconv=False):
+        lib = load_library()
+        n = len(self.solvers)
+        pb = (C.c_void_p * n)(*[_ptr(v) for v in bs])
+        px = (C.c_void_p * n)(*[_ptr(v) for v in xs])
+        rc = lib.aao_batch_solve(self.hb, pb, px, float(tol), int(max_outer))
+        ok = (AAO_OK, AAO_ENOTCONV) if allow_notconv else (AAO_OK,)
+        if rc not in ok:
+            raise AaoError(rc, (lib.aao_batch_last_error(self.hb) or b"").decode(errors="replace"))
+        return rc
+
+    def stats(self, i):
+        s = aao_stats()
+        rc = load_library().aao_batch_get_stats(self.hb, int(i), C.byref(s))
+        if rc != AAO_OK:
+            raise AaoError(rc, "aao_batch_get_stats")
+        return _stats_dict(s)
+
+    def close(self):
+        if getattr(self, "hb", None):
+            load_library().aao_batch_destroy(self.hb)
+            self.hb = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

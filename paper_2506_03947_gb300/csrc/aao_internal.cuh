@@ -140,6 +140,7 @@ struct ScLayout {
   __host__ __device__ int nrm2() const { return (m + 1) * m + 7 * m + 4; }
   __host__ __device__ int est() const { return (m + 1) * m + 7 * m + 5; }
   __host__ __device__ int hnext() const { return (m + 1) * m + 7 * m + 6; }
+  __host__ __device__ int bnorm() const { return (m + 1) * m + 7 * m + 7; }
   __host__ __device__ int size() const { return (m + 1) * m + 7 * m + 8; }
 };
 

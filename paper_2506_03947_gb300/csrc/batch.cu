@@ -1,0 +1,293 @@
+// Batched kernels: one launch runs a phase of the solve for many instances.
+//
+// Each launch covers a static work list: the blocks of every listed instance,
+// numbered consecutively (prefix offsets start[]); a block finds its instance
+// by binary search and runs the same device body as the single-instance
+// kernel on its own block coordinates.  Instances whose active flag is 0
+// (converged, or finished with their Krylov cycle) exit at once, so the
+// launch geometry never changes and a whole Arnoldi step can be captured in a
+// CUDA graph.  The Chebyshev kernels are templated on ell, so their lists are
+// split by ell; the FP64 kernels take ell at run time.
+#include "batch.cuh"
+#include "cheb_kernels.cuh"
+#include "krylov_bodies.cuh"
+
+namespace aao {
+
+__device__ __forceinline__ int wl_find(const WorkList& wl, int b) {
+  int lo = 0, hi = wl.cnt;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (wl.start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---- preconditioner: forward transform and Chebyshev steps (FP32, 2D, v4) ----
+
+template <int ELL>
+__global__ void __launch_bounds__(256) kb_dft(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl,
+                                               int j) {
+  __shared__ float gs[ELL];
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  dft_body<float, ELL>(b.g.N, blockIdx.x - wl.start[li], b.V + (int64_t)j * b.L, b.sc + L.vscale(j), b.bhat, *b.da,
+                       gs);
+}
+
+template <int ELL, int KSRC, int PSRC, bool LAST>
+__global__ void __launch_bounds__(256) kb_step(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl,
+                                                int k, int j) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const int lb = blockIdx.x - wl.start[li];
+  const int gx = (b.g.n0 + 127) / 128;
+  const float* xk;
+  float* xio;
+  if (k == 1) {
+    xk = nullptr;
+    xio = b.xa;
+  } else if (k == 2) {
+    xk = b.xa;
+    xio = b.xb;
+  } else {
+    xk = (k % 2 == 1) ? b.xb : b.xa;
+    xio = (k % 2 == 1) ? b.xa : b.xb;
+  }
+  cheb_step_v4_body<ELL, 2, KSRC, PSRC, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, xk, xio,
+                                              b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
+}
+
+// ---- FP64 outer solve ----------------------------------------------------------
+
+// mode 0: V_{j+1} = script-A Z_j; mode 1: V_0 = b - script-A x with norm partials
+template <int MODE>
+__global__ void __launch_bounds__(256) kb_matvec(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl,
+                                                  int j) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const int lb = blockIdx.x - wl.start[li];
+  const int gx = (b.g.n0 + 31) / 32;
+  if (MODE == 0)
+    aao_matvec_body<2, 0>(b.g, b.ell, lb % gx, lb / gx, 0, lb, b.cx64, b.cy64, nullptr, b.Z + (int64_t)j * b.L,
+                          nullptr, b.V + (int64_t)(j + 1) * b.L, nullptr);
+  else
+    aao_matvec_body<2, 1>(b.g, b.ell, lb % gx, lb / gx, 0, lb, b.cx64, b.cy64, nullptr, b.x, b.b, b.V, b.partials);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kRedThreads) kb_multidot(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                            WorkList wl, int j, int i0) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  multidot_body<G>(blockIdx.x - wl.start[li], b.nbred, b.V, b.L, i0, b.sc + L.vscale(0), b.V + (int64_t)(j + 1) * b.L,
+                   b.L, b.partials);
+}
+
+__global__ void __launch_bounds__(kRedThreads) kb_orth_update(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                               WorkList wl, int j, int second) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  orth_update_body(blockIdx.x - wl.start[li], b.nbred, b.V, b.L, j + 1, b.sc + (second ? L.h2(0) : L.h1(0)),
+                   b.sc + L.vscale(0), b.V + (int64_t)(j + 1) * b.L, b.L,
+                   second ? b.partials + (int64_t)(b.m + 1) * b.nbred : nullptr);
+}
+
+__global__ void __launch_bounds__(kRedThreads) kb_norm2(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                         WorkList wl) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  norm2_body(blockIdx.x - wl.start[li], b.nbred, b.b, b.L, b.partials);
+}
+
+// grid (nout, instances of wl): what = 0 -> h1[i], 1 -> h2[i] from the multi-dot
+// partials; 2 -> nrm2 from the update's norm partials; 3 -> nrm2 from the residual
+// matvec partials; 4 -> nrm2 from kb_norm2's partials.
+__global__ void __launch_bounds__(kRedThreads) kb_reduce(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                          WorkList wl, int what) {
+  const int inst = wl.inst[blockIdx.y];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  const int i = blockIdx.x;
+  if (what <= 1) {
+    reduce_body(b.partials + (int64_t)i * b.nbred, b.nbred, b.sc + (what == 0 ? L.h1(i) : L.h2(i)), 0);
+  } else if (i == 0) {
+    const double* src = (what == 2) ? b.partials + (int64_t)(b.m + 1) * b.nbred : b.partials;
+    const int nb = (what == 3) ? b.nbmv : b.nbred;
+    reduce_body(src, nb, b.sc + L.nrm2(), 0);
+  }
+}
+
+// one block per instance, thread 0: op 0 givens(j), 1 cycle_init, 2 backsolve(kvec),
+// 3 gather (est, hnext) -> out[2 inst], 4 gather sqrt(nrm2) -> out[2 inst] and store it as bnorm,
+// 5 gather sqrt(nrm2) -> out[2 inst]
+__global__ void kb_small(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl, int op, int j,
+                         const int* __restrict__ kvec, double* __restrict__ out) {
+  const int inst = wl.inst[blockIdx.x];
+  if (threadIdx.x != 0 || !act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  switch (op) {
+    case 0: givens_body(b.sc, j, b.m, b.sc[L.bnorm()]); break;
+    case 1: cycle_init_body(b.sc, b.m); break;
+    case 2: backsolve_body(b.sc, kvec[inst], b.m); break;
+    case 3:
+      out[2 * inst] = b.sc[L.est()];
+      out[2 * inst + 1] = b.sc[L.hnext()];
+      break;
+    case 4:
+      b.sc[L.bnorm()] = sqrt(b.sc[L.nrm2()]);
+      out[2 * inst] = b.sc[L.bnorm()];
+      break;
+    case 5: out[2 * inst] = sqrt(b.sc[L.nrm2()]); break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) kb_xupdate(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                           WorkList wl, const int* __restrict__ kvec) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  xupdate_body(blockIdx.x - wl.start[li], b.nbred, b.Z, b.L, kvec[inst], b.sc + L.y(0), b.x, b.L);
+}
+
+// ---- launchers -------------------------------------------------------------------
+
+#define AAO_BCHECK()        \
+  do {                      \
+    count_launch();         \
+    cudaError_t e_ = cudaGetLastError(); \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+template <int ELL>
+cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wdft, const WorkList& wstep, int p, int j,
+                              cudaStream_t s) {
+  if (wdft.cnt == 0) return cudaSuccess;
+  if (p < 2) return cudaErrorInvalidValue;  // the batch runs p >= 2
+  kb_dft<ELL><<<wdft.total, 256, 0, s>>>(I, act, wdft, j);
+  AAO_BCHECK();
+  const dim3 blk(32, 8, 1);
+  if (p == 2) {
+    // step 1 is the last one: transform straight to Z_j
+    kb_step<ELL, 0, 0, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, 1, j);
+    AAO_BCHECK();
+    return cudaSuccess;
+  }
+  kb_step<ELL, 0, 0, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, 1, j);
+  AAO_BCHECK();
+  if (p == 3) {
+    kb_step<ELL, 1, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, 2, j);
+    AAO_BCHECK();
+    return cudaSuccess;
+  }
+  kb_step<ELL, 1, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, 2, j);
+  AAO_BCHECK();
+  for (int k = 3; k <= p - 1; ++k) {
+    if (k == p - 1) kb_step<ELL, 1, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j);
+    else kb_step<ELL, 1, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j);
+    AAO_BCHECK();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep, int p,
+                          int j, cudaStream_t s) {
+  switch (ell) {
+    case 4: return batch_precond_ell<4>(I, act, wdft, wstep, p, j, s);
+    case 6: return batch_precond_ell<6>(I, act, wdft, wstep, p, j, s);
+    case 8: return batch_precond_ell<8>(I, act, wdft, wstep, p, j, s);
+    case 10: return batch_precond_ell<10>(I, act, wdft, wstep, p, j, s);
+    case 12: return batch_precond_ell<12>(I, act, wdft, wstep, p, j, s);
+    case 14: return batch_precond_ell<14>(I, act, wdft, wstep, p, j, s);
+    case 16: return batch_precond_ell<16>(I, act, wdft, wstep, p, j, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, cudaStream_t s) {
+  const dim3 blk(32, 8, 1);
+  if (mode == 0) kb_matvec<0><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+  else kb_matvec<1><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& wred, const WorkList& wone, int j,
+                               cudaStream_t s) {
+  const int nv = j + 1;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i0 = 0; i0 < nv; i0 += kDotGroup) {
+      const int g = (nv - i0 < kDotGroup) ? nv - i0 : kDotGroup;
+      switch (g) {
+#define AAO_BMD(G) \
+  case G: kb_multidot<G><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, i0); break;
+        AAO_BMD(1)
+        AAO_BMD(2)
+        AAO_BMD(3)
+        AAO_BMD(4)
+        AAO_BMD(5)
+        AAO_BMD(6)
+        AAO_BMD(7)
+        AAO_BMD(8)
+#undef AAO_BMD
+        default: return cudaErrorInvalidValue;
+      }
+      AAO_BCHECK();
+    }
+    kb_reduce<<<dim3(nv, wone.cnt, 1), kRedThreads, 0, s>>>(I, act, wone, pass);
+    AAO_BCHECK();
+    kb_orth_update<<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, pass);
+    AAO_BCHECK();
+  }
+  kb_reduce<<<dim3(1, wone.cnt, 1), kRedThreads, 0, s>>>(I, act, wone, 2);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_reduce(const BInst* I, const int* act, const WorkList& wone, int what, cudaStream_t s) {
+  kb_reduce<<<dim3(1, wone.cnt, 1), kRedThreads, 0, s>>>(I, act, wone, what);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_small(const BInst* I, const int* act, const WorkList& wone, int op, int j, const int* kvec,
+                        double* out, cudaStream_t s) {
+  kb_small<<<wone.cnt, 32, 0, s>>>(I, act, wone, op, j, kvec, out);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_norm2_b(const BInst* I, const int* act, const WorkList& wred, cudaStream_t s) {
+  kb_norm2<<<wred.total, kRedThreads, 0, s>>>(I, act, wred);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_xupdate(const BInst* I, const int* act, const WorkList& wred, const int* kvec, cudaStream_t s) {
+  kb_xupdate<<<wred.total, kRedThreads, 0, s>>>(I, act, wred, kvec);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+}  // namespace aao

@@ -1,0 +1,44 @@
+// Declarations of the batched launchers (batch.cu) used by the host driver.
+#pragma once
+
+#include "aao_internal.cuh"
+
+namespace aao {
+
+// Blocks of the listed instances, numbered consecutively: instance inst[i] owns
+// blocks [start[i], start[i+1]); total = start[cnt].  Device arrays.
+struct WorkList {
+  const int* start;
+  const int* inst;
+  int cnt;
+  int total;
+};
+
+// Everything a batched kernel needs about one instance (device array, one entry per member).
+struct BInst {
+  GridDesc g;
+  int ell, m, nbred, nbmv;
+  int64_t L;
+  const float *cx32, *cy32;
+  const double *cx64, *cy64;
+  float *bhat, *xa, *xb;
+  double *V, *Z, *sc, *partials;
+  const StepArgs<float>* steps;  // p entries
+  const DftArgs<float>* da;
+  const IdftArgs<float>* ia;
+  const double* b;
+  double* x;
+};
+
+cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep, int p,
+                          int j, cudaStream_t s);
+cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, cudaStream_t s);
+cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& wred, const WorkList& wone, int j,
+                               cudaStream_t s);
+cudaError_t batch_reduce(const BInst* I, const int* act, const WorkList& wone, int what, cudaStream_t s);
+cudaError_t batch_small(const BInst* I, const int* act, const WorkList& wone, int op, int j, const int* kvec,
+                        double* out, cudaStream_t s);
+cudaError_t batch_norm2_b(const BInst* I, const int* act, const WorkList& wred, cudaStream_t s);
+cudaError_t batch_xupdate(const BInst* I, const int* act, const WorkList& wred, const int* kvec, cudaStream_t s);
+
+}  // namespace aao

@@ -207,14 +207,15 @@ __device__ __forceinline__ void dft_point(int64_t N, int64_t c, const double* __
   }
 }
 
+// Body of one block (cell block cb) of the forward transform; gs is the block's
+// shared array of ELL scalings.  Shared by the single-instance and batched kernels.
 template <typename T, int ELL>
-__global__ void __launch_bounds__(256)
-    k_dft(int64_t N, const double* __restrict__ r, const double* __restrict__ rscale, T* __restrict__ bhat,
-          DftArgs<T> da) {
-  __shared__ T gs[ELL];
+__device__ __forceinline__ void dft_body(int64_t N, int64_t cb, const double* __restrict__ r,
+                                         const double* __restrict__ rscale, T* __restrict__ bhat,
+                                         const DftArgs<T>& da, T* gs) {
   if (threadIdx.x < ELL) gs[threadIdx.x] = (T)(da.gamma[threadIdx.x] * (rscale ? *rscale : 1.0));
   __syncthreads();
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = cb * blockDim.x + threadIdx.x;
   if (c >= N) return;
   T fre[ELL / 2 + 1], fim[ELL / 2 + 1];
   dft_point<T, ELL>(N, c, r, gs, da, fre, fim);
@@ -225,6 +226,14 @@ __global__ void __launch_bounds__(256)
     bhat[(int64_t)(2 * m) * N + c] = fre[m];
     bhat[(int64_t)(2 * m + 1) * N + c] = fim[m];
   }
+}
+
+template <typename T, int ELL>
+__global__ void __launch_bounds__(256)
+    k_dft(int64_t N, const double* __restrict__ r, const double* __restrict__ rscale, T* __restrict__ bhat,
+          const __grid_constant__ DftArgs<T> da) {
+  __shared__ T gs[ELL];
+  dft_body<T, ELL>(N, blockIdx.x, r, rscale, bhat, da, gs);
 }
 
 // p = 1: z = Gamma^{-1} U (bhat / theta) with no stencil work (x_1 = bhat/theta).

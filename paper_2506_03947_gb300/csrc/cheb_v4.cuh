@@ -77,15 +77,19 @@ __device__ __forceinline__ F4 apply_A4(const float* __restrict__ p, int64_t c, i
   return a;
 }
 
+// Body of one block (bx, by, bz) of the step; shared by the single-instance and
+// the batched kernels.
 template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
-__global__ void __launch_bounds__(256)
-    k_cheb_step_v4(GridDesc g, const float* __restrict__ cx, const float* __restrict__ cy,
-                   const float* __restrict__ cz, const float* __restrict__ bhat, const float* __restrict__ xk,
-                   float* xio, double* __restrict__ z, StepArgs<float> sa, IdftArgs<float> ia) {
+__device__ __forceinline__ void cheb_step_v4_body(const GridDesc& g, int bx, int by, int bz,
+                                                  const float* __restrict__ cx, const float* __restrict__ cy,
+                                                  const float* __restrict__ cz, const float* __restrict__ bhat,
+                                                  const float* __restrict__ xk, float* xio,
+                                                  double* __restrict__ z, const StepArgs<float>& sa,
+                                                  const IdftArgs<float>& ia) {
   const int lane = threadIdx.x & 31;
-  const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+  const int i0 = (bx * blockDim.x + threadIdx.x) * 4;
+  const int j = by * blockDim.y + threadIdx.y;
+  const int k = bz;
   if (j >= g.n1) return;  // uniform across the warp (a warp shares j and k)
   const int64_t N = g.N;
   const int64_t pl = (int64_t)g.n0 * g.n1;
@@ -237,6 +241,16 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
+}
+
+template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
+__global__ void __launch_bounds__(256)
+    k_cheb_step_v4(GridDesc g, const float* __restrict__ cx, const float* __restrict__ cy,
+                   const float* __restrict__ cz, const float* __restrict__ bhat, const float* __restrict__ xk,
+                   float* xio, double* __restrict__ z, const __grid_constant__ StepArgs<float> sa,
+                   const __grid_constant__ IdftArgs<float> ia) {
+  cheb_step_v4_body<ELL, DIM, KSRC, PSRC, LAST>(g, blockIdx.x, blockIdx.y, blockIdx.z, cx, cy, cz, bhat, xk, xio, z,
+                                                sa, ia);
 }
 
 }  // namespace aao

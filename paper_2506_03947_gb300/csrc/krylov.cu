@@ -5,7 +5,7 @@
 // Reductions are deterministic: every flat-vector reduction uses a block count
 // that depends on the vector length only, writes one partial sum per block,
 // and a second kernel adds the partials in a fixed order.
-#include "aao_internal.cuh"
+#include "krylov_bodies.cuh"
 
 #include <atomic>
 
@@ -13,30 +13,8 @@ namespace aao {
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch_add(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
-
-constexpr int kRedThreads = 256;
-constexpr int kRedWarps = kRedThreads / 32;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-wide sum; every thread gets the result.  `sh` holds kRedWarps doubles.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int lane = tid & 31, warp = tid >> 5;
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < kRedWarps; ++w) t += sh[w];  // fixed order
-  return t;
-}
 
 // ---- script-A matvec --------------------------------------------------------
 
@@ -48,62 +26,9 @@ __global__ void __launch_bounds__(256)
     k_aao_matvec(GridDesc g, int ell, const double* __restrict__ cx, const double* __restrict__ cy,
                  const double* __restrict__ cz, const double* __restrict__ x, const double* __restrict__ b,
                  double* __restrict__ y, double* __restrict__ partials) {
-  __shared__ double sh[kRedWarps];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  double acc2 = 0.0;
-  if (i < g.n0 && j < g.n1) {
-    const int64_t N = g.N;
-    const int64_t c = i + (int64_t)g.n0 * (j + (int64_t)g.n1 * k);
-    double kap[2 * DIM];
-    int64_t nb[2 * DIM];
-    kap[0] = __ldg(cx + c);
-    kap[1] = (i > 0) ? __ldg(cx + c - 1) : 0.0;
-    nb[0] = (i < g.n0 - 1) ? c + 1 : c;
-    nb[1] = (i > 0) ? c - 1 : c;
-    if constexpr (DIM >= 2) {
-      kap[2] = __ldg(cy + c);
-      kap[3] = (j > 0) ? __ldg(cy + c - g.n0) : 0.0;
-      nb[2] = (j < g.n1 - 1) ? c + g.n0 : c;
-      nb[3] = (j > 0) ? c - g.n0 : c;
-    }
-    if constexpr (DIM == 3) {
-      const int64_t pl = (int64_t)g.n0 * g.n1;
-      kap[4] = __ldg(cz + c);
-      kap[5] = (k > 0) ? __ldg(cz + c - pl) : 0.0;
-      nb[4] = (k < g.n2 - 1) ? c + pl : c;
-      nb[5] = (k > 0) ? c - pl : c;
-    }
-    // diagonal form (1 + sum kappa) x_c - sum kappa x_nbr: the diagonal is formed
-    // once per cell and reused for all ell blocks (FP64 arithmetic is the
-    // scarce resource here, not bandwidth)
-    double diag = 1.0;
-#pragma unroll
-    for (int q = 0; q < 2 * DIM; ++q) diag += kap[q];
-    double prev = 0.0;
-    for (int t = 0; t < ell; ++t) {
-      const double* xt = x + (int64_t)t * N;
-      const double xc = __ldg(xt + c);
-      double a = diag * xc - prev;
-#pragma unroll
-      for (int q = 0; q < 2 * DIM; ++q) a -= kap[q] * __ldg(xt + nb[q]);
-      double v = a;
-      prev = xc;
-      if constexpr (MODE == 1) {
-        v = __ldg(b + (int64_t)t * N + c) - v;
-        acc2 += v * v;
-      }
-      y[(int64_t)t * N + c] = v;
-    }
-  }
-  if constexpr (MODE == 1) {
-    const double s = block_sum(acc2, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-      const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-      partials[blk] = s;
-    }
-  }
+  aao_matvec_body<DIM, MODE>(g, ell, blockIdx.x, blockIdx.y, blockIdx.z,
+                             blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z), cx, cy, cz, x, b, y,
+                             partials);
 }
 
 cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,
@@ -144,16 +69,6 @@ int reduction_blocks(int64_t L) {
   return (int)nb;
 }
 
-constexpr int kDotGroup = 8;  // dot products accumulated per pass over w
-
-// The flat-vector kernels below walk the vectors two doubles at a time
-// (16-byte loads) and unroll by two, so each thread keeps several independent
-// loads in flight; L (= ell N) is even whenever N is even, and an odd tail is
-// handled separately.
-__device__ __forceinline__ double2 ld2(const double* __restrict__ p) {
-  return __ldg(reinterpret_cast<const double2*>(p));
-}
-
 // partials[i*NB + blk] = vscale[i] * sum_{e in block slice} V_i[e] w[e], for i in [i0, i0+G).
 // G is the exact number of vectors of this launch: a runtime bound inside the
 // unrolled loop would let the compiler turn the guards into selects and issue
@@ -162,56 +77,7 @@ template <int G>
 __global__ void __launch_bounds__(kRedThreads)
     k_multidot(const double* __restrict__ V, int64_t ldv, int i0, const double* __restrict__ vscale,
                const double* __restrict__ w, int64_t L, double* __restrict__ partials) {
-  __shared__ double sh[G][kRedWarps];
-  double acc[G];
-#pragma unroll
-  for (int q = 0; q < G; ++q) acc[q] = 0.0;
-  const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  const double* V0 = V + (int64_t)i0 * ldv;
-  if (vec) {
-    const int64_t L2 = L / 2;
-    int64_t e2 = tid;
-    for (; e2 + nthr < L2; e2 += 2 * nthr) {
-      const double2 wa = ld2(w + 2 * e2), wb = ld2(w + 2 * (e2 + nthr));
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        const double* vq = V0 + (int64_t)q * ldv;
-        const double2 va = ld2(vq + 2 * e2), vb = ld2(vq + 2 * (e2 + nthr));
-        acc[q] += va.x * wa.x + va.y * wa.y + vb.x * wb.x + vb.y * wb.y;
-      }
-    }
-    for (; e2 < L2; e2 += nthr) {
-      const double2 wa = ld2(w + 2 * e2);
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        const double2 va = ld2(V0 + (int64_t)q * ldv + 2 * e2);
-        acc[q] += va.x * wa.x + va.y * wa.y;
-      }
-    }
-  } else {
-    for (int64_t e = tid; e < L; e += nthr) {
-      const double we = __ldg(w + e);
-#pragma unroll
-      for (int q = 0; q < G; ++q) acc[q] += __ldg(V0 + (int64_t)q * ldv + e) * we;
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < G; ++q) {
-    const double v = warp_sum(acc[q]);
-    if (lane == 0) sh[q][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < G) {
-    const int q = threadIdx.x;
-    double t = 0.0;
-#pragma unroll
-    for (int w2 = 0; w2 < kRedWarps; ++w2) t += sh[q][w2];
-    const double scl = vscale ? vscale[i0 + q] : 1.0;
-    partials[(int64_t)(i0 + q) * gridDim.x + blockIdx.x] = t * scl;
-  }
+  multidot_body<G>(blockIdx.x, gridDim.x, V, ldv, i0, vscale, w, L, partials);
 }
 
 cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* vscale, const double* w,
@@ -246,49 +112,7 @@ __global__ void __launch_bounds__(kRedThreads)
     k_orth_update(const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ h,
                   const double* __restrict__ vscale, double* __restrict__ w, int64_t L,
                   double* __restrict__ partials) {
-  __shared__ double coef[kMaxRestart + 1];
-  __shared__ double sh[kRedWarps];
-  for (int q = threadIdx.x; q < nv; q += blockDim.x) coef[q] = h[q] * (vscale ? vscale[q] : 1.0);
-  __syncthreads();
-  double acc2 = 0.0;
-  const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  if (vec) {
-    const int64_t L2 = L / 2;
-    for (int64_t e2 = tid; e2 < L2; e2 += nthr) {
-      double2 v = *reinterpret_cast<const double2*>(w + 2 * e2);
-      int q = 0;
-      for (; q + 4 <= nv; q += 4) {
-        const double2 a0 = ld2(V + (int64_t)q * ldv + 2 * e2);
-        const double2 a1 = ld2(V + (int64_t)(q + 1) * ldv + 2 * e2);
-        const double2 a2 = ld2(V + (int64_t)(q + 2) * ldv + 2 * e2);
-        const double2 a3 = ld2(V + (int64_t)(q + 3) * ldv + 2 * e2);
-        v.x -= coef[q] * a0.x; v.y -= coef[q] * a0.y;
-        v.x -= coef[q + 1] * a1.x; v.y -= coef[q + 1] * a1.y;
-        v.x -= coef[q + 2] * a2.x; v.y -= coef[q + 2] * a2.y;
-        v.x -= coef[q + 3] * a3.x; v.y -= coef[q + 3] * a3.y;
-      }
-      for (; q < nv; ++q) {
-        const double2 a = ld2(V + (int64_t)q * ldv + 2 * e2);
-        v.x -= coef[q] * a.x;
-        v.y -= coef[q] * a.y;
-      }
-      *reinterpret_cast<double2*>(w + 2 * e2) = v;
-      acc2 += v.x * v.x + v.y * v.y;
-    }
-  } else {
-    for (int64_t e = tid; e < L; e += nthr) {
-      double v = w[e];
-      for (int q = 0; q < nv; ++q) v -= coef[q] * __ldg(V + (int64_t)q * ldv + e);
-      w[e] = v;
-      acc2 += v * v;
-    }
-  }
-  if (partials) {
-    const double t = block_sum(acc2, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
-  }
+  orth_update_body(blockIdx.x, gridDim.x, V, ldv, nv, h, vscale, w, L, partials);
 }
 
 cudaError_t launch_orth_update(const double* V, int64_t ldv, int nv, const double* h, const double* vscale,
@@ -301,15 +125,7 @@ cudaError_t launch_orth_update(const double* V, int64_t ldv, int nv, const doubl
 
 __global__ void __launch_bounds__(kRedThreads)
     k_norm2_partials(const double* __restrict__ v, int64_t L, double* __restrict__ partials) {
-  __shared__ double sh[kRedWarps];
-  double acc2 = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
-    const double a = __ldg(v + e);
-    acc2 += a * a;
-  }
-  const double t = block_sum(acc2, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  norm2_body(blockIdx.x, gridDim.x, v, L, partials);
 }
 
 cudaError_t launch_norm2_partials(const double* v, int64_t L, double* partials, cudaStream_t s) {
@@ -321,12 +137,7 @@ cudaError_t launch_norm2_partials(const double* v, int64_t L, double* partials, 
 // out[i] (+)= sum_b partials[i*nb + b]: one block per i, fixed summation order.
 __global__ void __launch_bounds__(kRedThreads)
     k_reduce(const double* __restrict__ partials, int nb, double* __restrict__ out, int accumulate) {
-  __shared__ double sh[kRedWarps];
-  const int i = blockIdx.x;
-  double a = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += partials[(int64_t)i * nb + b];
-  const double t = block_sum(a, sh);
-  if (threadIdx.x == 0) out[i] = accumulate ? out[i] + t : t;
+  reduce_body(partials + (int64_t)blockIdx.x * nb, nb, out + blockIdx.x, accumulate);
 }
 
 cudaError_t launch_reduce(const double* partials, int nv, int nb, double* out, int accumulate, cudaStream_t s) {
@@ -338,37 +149,9 @@ cudaError_t launch_reduce(const double* partials, int nv, int nb, double* out, i
 
 // ---- small dense FGMRES steps (one thread; sizes <= kMaxRestart) ---------------
 
-// Column j of the Hessenberg matrix: H[i][j] = h1[i] + h2[i] (i <= j), H[j+1][j] = sqrt(nrm2);
-// apply the stored rotations, build the new one, update g, and record the
-// relative residual estimate |g[j+1]| / bnorm.  vscale[j+1] = 1/H[j+1][j].
 __global__ void k_givens(double* sc, int j, int m, double bnorm) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const ScLayout L{m};
-  for (int i = 0; i <= j; ++i) sc[L.H(i, j)] = sc[L.h1(i)] + sc[L.h2(i)];
-  const double hn = sqrt(sc[L.nrm2()]);
-  sc[L.hnext()] = hn;
-  sc[L.vscale(j + 1)] = (hn > 0.0) ? 1.0 / hn : 0.0;
-  const double hj1 = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = sc[L.H(i, j)], b = sc[L.H(i + 1, j)];
-    sc[L.H(i, j)] = sc[L.cs(i)] * a + sc[L.sn(i)] * b;
-    sc[L.H(i + 1, j)] = -sc[L.sn(i)] * a + sc[L.cs(i)] * b;
-  }
-  const double hjj = sc[L.H(j, j)];
-  const double r = hypot(hjj, hj1);
-  double c = 1.0, s = 0.0;
-  if (r != 0.0) {
-    c = hjj / r;
-    s = hj1 / r;
-  }
-  sc[L.cs(j)] = c;
-  sc[L.sn(j)] = s;
-  sc[L.H(j, j)] = r;
-  sc[L.H(j + 1, j)] = 0.0;
-  const double gj = sc[L.gv(j)];
-  sc[L.gv(j + 1)] = -s * gj;
-  sc[L.gv(j)] = c * gj;
-  sc[L.est()] = fabs(sc[L.gv(j + 1)]) / bnorm;
+  givens_body(sc, j, m, bnorm);
 }
 
 cudaError_t launch_givens(double* sc, int j, int m, double bnorm, cudaStream_t s) {
@@ -379,12 +162,7 @@ cudaError_t launch_givens(double* sc, int j, int m, double bnorm, cudaStream_t s
 
 __global__ void k_backsolve(double* sc, int k, int m) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const ScLayout L{m};
-  for (int i = k - 1; i >= 0; --i) {
-    double v = sc[L.gv(i)];
-    for (int q = i + 1; q < k; ++q) v -= sc[L.H(i, q)] * sc[L.y(q)];
-    sc[L.y(i)] = v / sc[L.H(i, i)];
-  }
+  backsolve_body(sc, k, m);
 }
 
 cudaError_t launch_backsolve(double* sc, int k, int m, cudaStream_t s) {
@@ -396,15 +174,7 @@ cudaError_t launch_backsolve(double* sc, int k, int m, cudaStream_t s) {
 __global__ void __launch_bounds__(kRedThreads)
     k_xupdate(const double* __restrict__ Z, int64_t ldz, int k, const double* __restrict__ y,
               double* __restrict__ x, int64_t L) {
-  __shared__ double coef[kMaxRestart];
-  for (int q = threadIdx.x; q < k; q += blockDim.x) coef[q] = y[q];
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
-    double v = x[e];
-    for (int q = 0; q < k; ++q) v += coef[q] * __ldg(Z + (int64_t)q * ldz + e);
-    x[e] = v;
-  }
+  xupdate_body(blockIdx.x, gridDim.x, Z, ldz, k, y, x, L);
 }
 
 cudaError_t launch_xupdate(const double* Z, int64_t ldz, int k, const double* y, double* x, int64_t L,
@@ -433,14 +203,9 @@ cudaError_t launch_ci_update(double* d, const double* z, double* x, double c1, d
   return cudaGetLastError();
 }
 
-// Start of a cycle: beta = sqrt(nrm2); g = (beta, 0, ..); vscale[0] = 1/beta.
 __global__ void k_cycle_init(double* sc, int m) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const ScLayout L{m};
-  const double beta = sqrt(sc[L.nrm2()]);
-  for (int i = 0; i <= m; ++i) sc[L.gv(i)] = 0.0;
-  sc[L.gv(0)] = beta;
-  sc[L.vscale(0)] = (beta > 0.0) ? 1.0 / beta : 0.0;
+  cycle_init_body(sc, m);
 }
 
 cudaError_t launch_cycle_init(double* sc, int m, cudaStream_t s) {
