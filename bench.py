@@ -73,7 +73,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("cheb_kernels.cuh", "cheb_v4.cuh", "cheb_pair.cuh", "cheb_quad.cuh", "aao_internal.cuh"):
+    for f in ("cheb_kernels.cuh", "cheb_v4.cuh", "cheb_pair.cuh", "cheb_quad.cuh", "cheb_quad_tma.cu",
+              "aao_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2506_03947_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -219,6 +220,7 @@ def run_ours(args):
     s32 = binding.Solver(P.dim, P.n, kx, ky, None, P.ell, P.alpha, prec=binding.AAO_MIXED, inner_its=p,
                          restart=64, stream=sptr)
     sampler = ClockSampler(local) if not args.no_clocks else None
+    quad_kind = s32.step_kernel()
     ms, wall, launches, prof, clocks, st32 = timed_solves(s32, args.steps, args.warmup, profile=True,
                                                           sampler=sampler)
     walls32 = list(timed_solves.walls)
@@ -268,7 +270,10 @@ def run_ours(args):
     avg_ms = mid["ms"] / max(1, mid["launches"])
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     total_ms_prof = sum(v["ms"] for v in prof.values())
-    kernels = {"step_quad": "k_cheb_quad<10,16,2> (four fused multi-frequency Chebyshev steps, FP32, shared-memory tile)",
+    kernels = {"step_quad": ("k_cheb_quad_tma<10,2,2> (four fused multi-frequency Chebyshev steps, FP32, "
+                             "persistent, TMA-fed)" if quad_kind == binding.AAO_STEP_TMA else
+                             "k_cheb_quad<10,16,2> (four fused multi-frequency Chebyshev steps, FP32, "
+                             "shared-memory tile)"),
                "step_pair": "k_cheb_pair_v4<10,2> (two fused multi-frequency Chebyshev steps, FP32)",
                "step_mid": "k_cheb_step_v4<10,2,1,2,false> (fused multi-frequency Chebyshev step, FP32)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -186,6 +186,27 @@ int aao_solve_fixed(aao_handle h, const double* b, double* x, int k, int inner_i
 int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
 
 /*
+ * Kernel that runs the fused four-step Chebyshev sweeps of the 2D mixed path
+ * (no counterpart in the paper; both compute the same steps of Eq. 7):
+ *   AAO_STEP_AUTO  the persistent TMA kernel when its descriptors could be
+ *                  built at aao_create, else the shared-memory tile kernel;
+ *   AAO_STEP_TILE  the shared-memory tile kernel (one CTA per 120 x 16 tile);
+ *   AAO_STEP_TMA   the persistent TMA-fed kernel (one CTA per SM).
+ * Returns AAO_EINVAL for an unknown kind, or when the handle has no fused
+ * 2D path (FP64, 1D/3D, n0 % 4 != 0) or, for AAO_STEP_TMA, no descriptors.
+ * A TMA wait in the persistent kernel that does not finish within about a
+ * second of SM clock makes the enclosing aao_solve / aao_solve_ci /
+ * aao_precond_apply return AAO_ECUDA (the flag is per device).
+ */
+#define AAO_STEP_AUTO 0
+#define AAO_STEP_TILE 1
+#define AAO_STEP_TMA 2
+int aao_set_step_kernel(aao_handle h, int kind);
+/* The kernel in use: AAO_STEP_TMA or AAO_STEP_TILE on the fused 2D path,
+ * AAO_STEP_AUTO when the handle has none; -1 for a NULL handle. */
+int aao_get_step_kernel(aao_handle h);
+
+/*
  * Algorithm 1 of the paper, on the host: share ell * nx * eta inner
  * iterations among the ell shifted problems in proportion to
  * ln(sigma_1) / ln(sigma_j), sigma_j from Theorem 4 on [mu_min, mu_max], and

@@ -27,7 +27,11 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_last_create_error", "aao_kernel_launch_count", "aao_destroy",
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
             "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
-            "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy")
+            "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
+            "aao_set_step_kernel", "aao_get_step_kernel")
+
+# four-step kernel selection (aao_set_step_kernel)
+AAO_STEP_AUTO, AAO_STEP_TILE, AAO_STEP_TMA = 0, 1, 2
 
 AAO_NPROF = 9
 PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair",
@@ -119,6 +123,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_set_inner_alloc.restype = i32
     lib.aao_assign_iterations.argtypes = [i32, C.c_int64, dbl, dbl, dbl, dbl, C.POINTER(C.c_int32)]
     lib.aao_assign_iterations.restype = i32
+    lib.aao_set_step_kernel.argtypes = [vp, i32]
+    lib.aao_set_step_kernel.restype = i32
+    lib.aao_get_step_kernel.argtypes = [vp]
+    lib.aao_get_step_kernel.restype = i32
     _lib = lib
     return lib
 
@@ -243,6 +251,14 @@ def aao_set_inner_alloc(h, p) -> int:
     return _check(h, load_library().aao_set_inner_alloc(h, arr, len(p)))
 
 
+def aao_set_step_kernel(h, kind: int) -> int:
+    return _check(h, load_library().aao_set_step_kernel(h, int(kind)))
+
+
+def aao_get_step_kernel(h) -> int:
+    return load_library().aao_get_step_kernel(h)
+
+
 def aao_assign_iterations(ell: int, nx: int, mu_max: float, mu_min: float, alpha: float, eta: float):
     out = (C.c_int32 * int(ell))()
     rc = load_library().aao_assign_iterations(int(ell), int(nx), float(mu_max), float(mu_min), float(alpha),
@@ -350,6 +366,12 @@ class Solver:
 
     def set_inner_alloc(self, p):
         return aao_set_inner_alloc(self.h, p)
+
+    def set_step_kernel(self, kind):
+        return aao_set_step_kernel(self.h, kind)
+
+    def step_kernel(self):
+        return aao_get_step_kernel(self.h)
 
     def profile_enable(self, on=True):
         return aao_profile_enable(self.h, on)

@@ -55,6 +55,10 @@ struct aao_ctx {
   void *bhat = nullptr, *xa = nullptr, *xb = nullptr;  // Chebyshev fields (float or double)
   void *xc = nullptr, *xd = nullptr;                   // extra fields for fused step pairs (2D mixed)
   bool pairs = false;                                  // fused two-step kernels in use
+  aao::FieldMap fmap[5];                               // TMA descriptors of xa, xb, xc, xd, bhat
+  bool tma = false;                                    // descriptors built: persistent four-step kernel usable
+  int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
+  bool tma_used = false;                               // TMA kernel launched since the last fault check
   double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
   double* sc = nullptr;                                // small scalars, ScLayout
   double* partials = nullptr;                          // reduction partials
@@ -335,8 +339,14 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
     aao::QuadSteps qs;
     for (int q = 0; q < 4; ++q) qs.s[q] = st[k + q];
     pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
-    AAO_CK(h, aao::launch_quad(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
-                               X[o[0]], X[o[1]], qs, s));
+    if (h->tma && h->step_kernel != AAO_STEP_TILE) {
+      AAO_CK(h, aao::launch_quad_tma(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, h->fmap[cur], h->fmap[prev < 0 ? cur : prev],
+                                     h->fmap[4], X[o[0]], X[o[1]], qs, s));
+      h->tma_used = true;
+    } else {
+      AAO_CK(h, aao::launch_quad(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
+                                 X[o[0]], X[o[1]], qs, s));
+    }
     prof_end(h, pi);
     prev = o[0];
     cur = o[1];
@@ -377,6 +387,19 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
   AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 1, psrc, true, cx, cy, cz, bhat, X[cur],
                                     prev < 0 ? X[cur] : X[prev], z, st[k], ia, s));
   prof_end(h, pi);
+  return AAO_OK;
+}
+
+// Read (and clear) the device flag the persistent four-step kernel raises
+// when one of its bounded TMA waits expires; synchronises the stream.
+int check_tma(aao_ctx* h) {
+  if (!h->tma_used) return AAO_OK;
+  h->tma_used = false;
+  unsigned flag = 0;
+  AAO_CK(h, aao::quad_tma_fault(&flag, h->stream));
+  if (flag)
+    return fail(h, AAO_ECUDA, "four-step TMA kernel: %s",
+                (flag & 2u) ? "shared-memory base not 128-byte aligned" : "a TMA wait expired");
   return AAO_OK;
 }
 
@@ -899,6 +922,14 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   if (h->pairs) {
     AAO_CK_CREATE(cudaMalloc(&h->xc, fsz * h->L));
     AAO_CK_CREATE(cudaMalloc(&h->xd, fsz * h->L));
+    // TMA descriptors for the persistent four-step kernel; without them the
+    // shared-memory tile kernel runs the same steps.
+    const float* fields[5] = {(const float*)h->xa, (const float*)h->xb, (const float*)h->xc, (const float*)h->xd,
+                              (const float*)h->bhat};
+    bool ok = true;
+    for (int i = 0; i < 5 && ok; ++i) ok = aao::encode_field_map(&h->fmap[i], fields[i], h->g, ell) == cudaSuccess;
+    cudaGetLastError();
+    h->tma = ok;
   }
   AAO_CK_CREATE(cudaMalloc(&h->V, sizeof(double) * h->L * (h->m + 1)));
   AAO_CK_CREATE(cudaMalloc(&h->Z, sizeof(double) * h->L * h->m));
@@ -951,6 +982,7 @@ int aao_precond_apply(aao_handle h, const double* r, double* z) {
   }
   if (hz) dz = h->stage_b;
   rc = precond(h, dr, nullptr, dz);
+  if (rc == AAO_OK) rc = check_tma(h);
   if (rc) return rc;
   if (hz) AAO_CK(h, cudaMemcpyAsync(z, dz, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
   AAO_CK(h, cudaStreamSynchronize(h->stream));
@@ -986,6 +1018,10 @@ static int solve_entry(aao_handle h, const double* b, double* x, double tol, int
   }
   if (!use_x0) AAO_CK(h, cudaMemsetAsync(dx, 0, sizeof(double) * h->L, h->stream));
   rc = solve_impl(h, db, dx, fixed ? 1.0 : tol, fixed ? fixed : max_outer, fixed);
+  if (rc == AAO_OK || rc == AAO_ENOTCONV) {
+    const int rt = check_tma(h);
+    if (rt) return rt;
+  }
   if (hx && (rc == AAO_OK || rc == AAO_ENOTCONV)) {
     cudaError_t e = cudaMemcpyAsync(x, dx, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1038,6 +1074,24 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell) {
   h->p = pmax;
   build_tables(h);
   return AAO_OK;
+}
+
+int aao_set_step_kernel(aao_handle h, int kind) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (kind != AAO_STEP_AUTO && kind != AAO_STEP_TILE && kind != AAO_STEP_TMA)
+    return fail(h, AAO_EINVAL, "unknown step kernel %d", kind);
+  if (kind == AAO_STEP_TMA && !h->tma)
+    return fail(h, AAO_EINVAL, "the persistent TMA kernel needs the 2D mixed path with n0 %% 4 == 0 and TMA descriptors");
+  if (kind == AAO_STEP_TILE && !h->pairs)
+    return fail(h, AAO_EINVAL, "the fused tile kernels need the 2D mixed path with n0 %% 4 == 0");
+  h->step_kernel = kind;
+  return AAO_OK;
+}
+
+int aao_get_step_kernel(aao_handle h) {
+  if (!h) return -1;
+  if (!h->pairs) return AAO_STEP_AUTO;
+  return (h->tma && h->step_kernel != AAO_STEP_TILE) ? AAO_STEP_TMA : AAO_STEP_TILE;
 }
 
 int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, double alpha, double eta, int32_t* out) {
@@ -1100,6 +1154,10 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
   }
   if (!use_x0) AAO_CK(h, cudaMemsetAsync(dx, 0, sizeof(double) * h->L, h->stream));
   rc = solve_ci_impl(h, db, dx, tol, max_outer, l_min, l_max, fixed_its);
+  if (rc == AAO_OK || rc == AAO_ENOTCONV) {
+    const int rt = check_tma(h);
+    if (rt) return rt;
+  }
   if (hx && (rc == AAO_OK || rc == AAO_ENOTCONV)) {
     cudaError_t e = cudaMemcpyAsync(x, dx, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -97,6 +97,26 @@ cudaError_t launch_quad(const GridDesc& g, int ell, int psrc, const float* cx, c
                         const float* xk, const float* xkm1, float* out3, float* out4, const QuadSteps& qs,
                         cudaStream_t s);
 
+// Persistent TMA-fed variant of the four-step kernel (cheb_quad_tma.cu):
+// tiles of 120 x kQuadTmaTY interior cells, kQuadTmaR staged rows per warp.
+// Its x_k, x_{k-1} and bhat arrive through TMA descriptors of the ell-plane
+// FP32 fields (3D: n0, n1, ell; box 128 x (kQuadTmaTY + 8) x 2).
+constexpr int kQuadTmaTY = 16;
+constexpr int kQuadTmaR = 2;
+struct alignas(64) FieldMap {
+  unsigned long long opaque[16];  // a CUtensorMap
+};
+// Encode the descriptor of one field (base: ell planes of N floats, 16-byte aligned).
+cudaError_t encode_field_map(FieldMap* out, const float* base, const GridDesc& g, int ell);
+// Same contract as launch_quad; xk, xkm1 (psrc == 2 only) and bhat are given by
+// their descriptors.
+cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const float* cx, const float* cy,
+                            const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3,
+                            float* out4, const QuadSteps& qs, cudaStream_t s);
+// Read and clear the device flag of expired TMA waits (bit 0) or a misaligned
+// shared-memory base (bit 1); synchronises s.
+cudaError_t quad_tma_fault(unsigned* flag, cudaStream_t s);
+
 // FP64 Krylov kernels (krylov.cu).
 // y = script-A x (mode 0) or y = b - script-A x with per-block partial sums of y^2 (mode 1).
 cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,

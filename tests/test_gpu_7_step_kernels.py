@@ -1,0 +1,115 @@
+"""The two kernels of the fused four-step Chebyshev sweep (2D mixed path).
+
+aao_set_step_kernel selects the shared-memory tile kernel or the persistent
+TMA-fed kernel; both compute Chebyshev steps k .. k+3 of Eq. 7 on every
+frequency.  Each is compared with the oracle's P_NC^{-1} (Eq. 5 with p
+Chebyshev steps per frequency) on grids that span several 120 x 16 tiles
+with ragged right and bottom edges, and with each other.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import ensure_lib, log_record, make_solver, oracle_ops, precond_tol, to_dev, torch_cuda
+from oracle import precond
+from paper_2506_03947_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# (n0, n1, ell): n0 % 4 == 0 keeps the fused path; tiles are 120 x 16 interior cells
+GRIDS = [
+    (260, 70, 10),   # 3 x 5 tiles, ragged both ways
+    (128, 33, 4),    # two tile columns, one 8-column tail
+    (376, 17, 16),   # 4 x 2 tiles, one-row tail
+    (120, 16, 6),    # exactly one tile
+    (64, 64, 8),     # narrower than a tile
+]
+
+
+def _problem(n0, n1, ell, seed):
+    return inputs.make_problem("g%dx%d" % (n0, n1), 2, (n0, n1), ell, 1e-2, 1, 0.6, (16.0, 16.0), seed, seed + 1)
+
+
+def _apply(s, r):
+    torch = torch_cuda()
+    rd = to_dev(r)
+    zd = torch.empty_like(rd)
+    s.precond_apply(rd, zd)
+    return zd.cpu().numpy()
+
+
+@pytest.mark.parametrize("p", [7, 12, 21])
+@pytest.mark.parametrize("n0,n1,ell", GRIDS, ids=["%dx%d_l%d" % g for g in GRIDS])
+def test_step_kernels_match_oracle_and_each_other(n0, n1, ell, p):
+    binding = ensure_lib()
+    P = _problem(n0, n1, ell, 100 + n0 + n1 + ell)
+    A, mu_max = oracle_ops(P)
+    r = np.random.default_rng(7).standard_normal((P.ell, P.N))
+    ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, p)
+    s = make_solver(P, 1, p)
+    assert s.step_kernel() == binding.AAO_STEP_TMA
+    z_tma = _apply(s, r)
+    s.set_step_kernel(binding.AAO_STEP_TILE)
+    assert s.step_kernel() == binding.AAO_STEP_TILE
+    z_tile = _apply(s, r)
+    tol = precond_tol(1, p, P.ell, P.alpha)
+    scale = np.abs(ref).max()
+    e_tma = np.abs(z_tma - ref).max() / scale
+    e_tile = np.abs(z_tile - ref).max() / scale
+    e_pair = np.abs(z_tma - z_tile).max() / scale
+    log_record({"test": "step_kernels", "case": "%dx%d_l%d" % (n0, n1, ell), "p": p, "err_tma": e_tma,
+                "err_tile": e_tile, "tma_vs_tile": e_pair, "bitwise": bool(np.array_equal(z_tma, z_tile)),
+                "tol": tol})
+    assert e_tma <= tol, (e_tma, tol)
+    assert e_tile <= tol, (e_tile, tol)
+    # same FP32 operations in the same order: at most rounding-order noise
+    assert e_pair <= 64 * np.finfo(np.float32).eps, e_pair
+
+
+def test_tma_kernel_is_deterministic_and_repeatable():
+    P = _problem(260, 70, 10, 5)
+    r = np.random.default_rng(8).standard_normal((P.ell, P.N))
+    s = make_solver(P, 1, 20)
+    z1 = _apply(s, r)
+    z2 = _apply(s, r)
+    np.testing.assert_array_equal(z1, z2)
+
+
+def test_step_kernel_selection_rules():
+    binding = ensure_lib()
+    P2 = _problem(64, 64, 8, 9)
+    s64 = make_solver(P2, 0, 9)             # FP64: no fused path
+    assert s64.step_kernel() == binding.AAO_STEP_AUTO
+    with pytest.raises(binding.AaoError):
+        s64.set_step_kernel(binding.AAO_STEP_TMA)
+    with pytest.raises(binding.AaoError):
+        s64.set_step_kernel(binding.AAO_STEP_TILE)
+    P3 = inputs.make_problem("odd", 2, (30, 12), 6, 1e-2, 1, 0.5, (8.0, 8.0), 3, 4)   # n0 % 4 != 0
+    s_odd = make_solver(P3, 1, 9)
+    assert s_odd.step_kernel() == binding.AAO_STEP_AUTO
+    with pytest.raises(binding.AaoError):
+        s_odd.set_step_kernel(binding.AAO_STEP_TMA)
+    sm = make_solver(P2, 1, 9)
+    with pytest.raises(binding.AaoError):
+        sm.set_step_kernel(7)
+    sm.set_step_kernel(binding.AAO_STEP_TILE)
+    sm.set_step_kernel(binding.AAO_STEP_AUTO)
+    assert sm.step_kernel() == binding.AAO_STEP_TMA
+
+
+def test_full_solve_with_either_kernel_agrees():
+    # whole FGMRES solve (Section 5) with each kernel: same iterations, same solution to solver tolerance
+    torch = torch_cuda()
+    binding = ensure_lib()
+    P = _problem(260, 70, 10, 11)
+    b = to_dev(P.b)
+    out = {}
+    for kind in (binding.AAO_STEP_TMA, binding.AAO_STEP_TILE):
+        s = make_solver(P, 1, 20)
+        s.set_step_kernel(kind)
+        x = torch.zeros_like(b)
+        s.solve(b, x, 1e-8, 60)
+        out[kind] = (x.cpu().numpy(), s.stats()["outer_its"])
+    xa, ia = out[binding.AAO_STEP_TMA]
+    xb, ib = out[binding.AAO_STEP_TILE]
+    assert ia == ib
+    assert np.abs(xa - xb).max() / np.abs(xb).max() < 1e-7
