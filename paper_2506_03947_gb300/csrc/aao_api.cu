@@ -55,7 +55,7 @@ struct aao_ctx {
   void *bhat = nullptr, *xa = nullptr, *xb = nullptr;  // Chebyshev fields (float or double)
   void *xc = nullptr, *xd = nullptr;                   // extra fields for fused step pairs (2D mixed)
   bool pairs = false;                                  // fused two-step kernels in use
-  aao::FieldMap fmap[5];                               // TMA descriptors of xa, xb, xc, xd, bhat
+  aao::FieldMap fmap[7];                               // TMA descriptors of xa, xb, xc, xd, bhat, cx32, cy32
   bool tma = false;                                    // descriptors built: persistent four-step kernel usable
   int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
   bool tma_used = false;                               // TMA kernel launched since the last fault check
@@ -340,8 +340,8 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
     for (int q = 0; q < 4; ++q) qs.s[q] = st[k + q];
     pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
     if (h->tma && h->step_kernel != AAO_STEP_TILE) {
-      AAO_CK(h, aao::launch_quad_tma(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, h->fmap[cur], h->fmap[prev < 0 ? cur : prev],
-                                     h->fmap[4], X[o[0]], X[o[1]], qs, s));
+      AAO_CK(h, aao::launch_quad_tma(h->g, h->ell, prev < 0 ? 1 : 2, h->fmap[5], h->fmap[6], h->fmap[cur],
+                                     h->fmap[prev < 0 ? cur : prev], h->fmap[4], X[o[0]], X[o[1]], qs, s));
       h->tma_used = true;
     } else {
       AAO_CK(h, aao::launch_quad(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
@@ -928,6 +928,8 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
                               (const float*)h->bhat};
     bool ok = true;
     for (int i = 0; i < 5 && ok; ++i) ok = aao::encode_field_map(&h->fmap[i], fields[i], h->g, ell) == cudaSuccess;
+    if (ok) ok = aao::encode_coef_map(&h->fmap[5], h->cx32, h->g) == cudaSuccess;
+    if (ok) ok = aao::encode_coef_map(&h->fmap[6], h->cy32, h->g) == cudaSuccess;
     cudaGetLastError();
     h->tma = ok;
   }

@@ -108,9 +108,11 @@ struct alignas(64) FieldMap {
 };
 // Encode the descriptor of one field (base: ell planes of N floats, 16-byte aligned).
 cudaError_t encode_field_map(FieldMap* out, const float* base, const GridDesc& g, int ell);
-// Same contract as launch_quad; xk, xkm1 (psrc == 2 only) and bhat are given by
-// their descriptors.
-cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const float* cx, const float* cy,
+// Descriptor of one FP32 face-coefficient array (N floats; box 128 x (kQuadTmaTY + 9)).
+cudaError_t encode_coef_map(FieldMap* out, const float* base, const GridDesc& g);
+// Same contract as launch_quad; the face arrays cx, cy and the fields xk, xkm1
+// (psrc == 2 only) and bhat are given by their descriptors.
+cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap& mcx, const FieldMap& mcy,
                             const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3,
                             float* out4, const QuadSteps& qs, cudaStream_t s);
 // Read and clear the device flag of expired TMA waits (bit 0) or a misaligned

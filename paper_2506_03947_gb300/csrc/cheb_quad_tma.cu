@@ -48,7 +48,10 @@ constexpr int kPlane = kRows * kCols;   // floats of one staged plane
 constexpr int kBox = 2 * kPlane;        // floats of one box (two planes)
 constexpr unsigned kBoxBytes = kBox * 4u;
 constexpr int kStage = 3 * kBox;        // x_k, x_{k-1}, bhat boxes
-constexpr size_t kSmemBytes = (size_t)2 * kStage * 4 + 64;
+constexpr int kCoefRows = kRows + 1;    // face coefficients: the staged rows and the row above them
+constexpr int kCoef = kCoefRows * kCols;
+constexpr unsigned kCoefBytes = 2u * kCoef * 4u;  // cx and cy boxes
+constexpr size_t kSmemBytes = (size_t)2 * kStage * 4 + (size_t)kCoefBytes + 64;
 
 __device__ unsigned int g_quad_tma_fault = 0;
 
@@ -92,6 +95,14 @@ __device__ __forceinline__ void tma_load_box(unsigned dst, const FieldMap* map, 
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(dst),
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const FieldMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
 
@@ -208,17 +219,29 @@ __device__ __forceinline__ void issue_pass(int it, float* sm, unsigned long long
   tma_load_box(smem_u32(st + 2 * kBox), mbhat, x, y, z, bar);
 }
 
+// Thread 0: issue the face-coefficient boxes of the block's j-th tile (rows gy0-1 .. gy0+kRows-1).
+__device__ __forceinline__ void issue_coef(int j, float* coef, unsigned long long* bars, int ntx, const FieldMap* mcx,
+                                           const FieldMap* mcy) {
+  const int tile = (int)blockIdx.x + j * (int)gridDim.x;
+  const int tx = tile % ntx, ty = tile / ntx;
+  const unsigned bar = smem_u32(&bars[2]);
+  mbar_arrive_tx(bar, kCoefBytes);
+  tma_load_2d(smem_u32(coef), mcx, tx * kInX - kS, ty * kTY - kS - 1, bar);
+  tma_load_2d(smem_u32(coef + kCoef), mcy, tx * kInX - kS, ty * kTY - kS - 1, bar);
+}
+
 // PSRC: x_{k-1} = bhat/theta (1, first fused step is k = 2) or the staged x_{k-1} box (2).
 template <int ELL, int R, int PSRC>
 __global__ void __launch_bounds__(32 * kRows / R, 1)
-    k_cheb_quad_tma(GridDesc g, int ntx, int ntiles, const float* __restrict__ cx, const float* __restrict__ cy,
-                    const __grid_constant__ FieldMap mxk, const __grid_constant__ FieldMap mxkm1,
-                    const __grid_constant__ FieldMap mbhat, float* __restrict__ out3, float* __restrict__ out4,
-                    QuadSteps qa) {
+    k_cheb_quad_tma(GridDesc g, int ntx, int ntiles, const __grid_constant__ FieldMap mcx,
+                    const __grid_constant__ FieldMap mcy, const __grid_constant__ FieldMap mxk,
+                    const __grid_constant__ FieldMap mxkm1, const __grid_constant__ FieldMap mbhat,
+                    float* __restrict__ out3, float* __restrict__ out4, QuadSteps qa) {
   constexpr int NPASS = ELL / 2;
   extern __shared__ __align__(1024) float sm[];
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm + 2 * kStage);
-  volatile int* s_abort = reinterpret_cast<volatile int*>(bars + 2);
+  float* coef = sm + 2 * kStage;  // cx box, then cy box: [kCoefRows][kCols], row j = staged row j - 1
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(coef + 2 * kCoef);  // stage 0, stage 1, coef
+  volatile int* s_abort = reinterpret_cast<volatile int*>(bars + 3);
   const int lane = threadIdx.x & 31;
   const int ly0 = (threadIdx.x >> 5) * R;
   const int64_t N = g.N;
@@ -229,6 +252,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     *s_abort = (smem_u32(sm) & 127u) ? 1 : 0;
     mbar_init(smem_u32(&bars[0]), 1);
     mbar_init(smem_u32(&bars[1]), 1);
+    mbar_init(smem_u32(&bars[2]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_async_smem();
   }
@@ -238,51 +262,53 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     return;
   }
 
-  if (threadIdx.x == 0 && total > 0) issue_pass<NPASS, PSRC>(0, sm, bars, ntx, &mxk, &mxkm1, &mbhat);
+  if (threadIdx.x == 0 && total > 0) {
+    issue_pass<NPASS, PSRC>(0, sm, bars, ntx, &mxk, &mxkm1, &mbhat);
+    issue_coef(0, coef, bars, ntx, &mcx, &mcy);
+  }
 
   TileCoef<R> tc;
   float kW0[R];
   int it = 0;
+  bool coef_wait_failed = false;
   for (; it < total; ++it) {
-    const int tile = (int)blockIdx.x + (it / NPASS) * (int)gridDim.x;
-    const int pass = it % NPASS;
+    const int j = it / NPASS;  // the block's tile counter
+    const int tile = (int)blockIdx.x + j * (int)gridDim.x;
+    const int pass = it - j * NPASS;
     const int tx = tile % ntx, ty = tile / ntx;
     const int gx = tx * kInX - kS + 4 * lane;
     const int gy0 = ty * kTY - kS;
     const bool colok = gx >= 0 && gx < g.n0;  // the four cells are all in or all out (n0 % 4 == 0)
     if (pass == 0) {
-      // face coefficients and diagonal of the thread's cells (zero outside the grid)
+      // Face coefficients of the thread's cells (zero outside the grid, by the TMA fill) and the
+      // diagonal d = 1 + sum of the four faces.  Lane 0's west face belongs to staged column 0,
+      // whose new levels are never used; it is taken as 0.
+      if (!mbar_wait(smem_u32(&bars[2]), (unsigned)j & 1u)) {
+        *s_abort = 1;
+        coef_wait_failed = true;
+      }
+      const float* CX = coef;
+      const float* CY = coef + kCoef;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const int gy = gy0 + ly0 + r;
-        const bool ok = colok && gy >= 0 && gy < g.n1;
-        const int64_t c = (int64_t)g.n0 * gy + gx;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (ok) {
-          a = __ldg(reinterpret_cast<const float4*>(cx + c));
-          b = __ldg(reinterpret_cast<const float4*>(cy + c));
-        }
+        const float4 a = lds4(CX + (ly0 + r + 1) * kCols + 4 * lane);
+        const float4 b = lds4(CY + (ly0 + r + 1) * kCols + 4 * lane);
         tc.kE[r][0] = a.x, tc.kE[r][1] = a.y, tc.kE[r][2] = a.z, tc.kE[r][3] = a.w;
         tc.kN[r][0] = b.x, tc.kN[r][1] = b.y, tc.kN[r][2] = b.z, tc.kN[r][3] = b.w;
-        float w = __shfl_up_sync(0xffffffffu, a.w, 1);
-        if (lane == 0) w = (ok && gx > 0) ? __ldg(cx + c - 1) : 0.f;
-        kW0[r] = w;
+        const float w = __shfl_up_sync(0xffffffffu, a.w, 1);
+        kW0[r] = (lane == 0) ? 0.f : w;
         if (r == 0) {
-          const int gs = gy - 1;
-          float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (colok && gs >= 0 && gs < g.n1) s = __ldg(reinterpret_cast<const float4*>(cy + (int64_t)g.n0 * gs + gx));
-          tc.kS0[0] = s.x, tc.kS0[1] = s.y, tc.kS0[2] = s.z, tc.kS0[3] = s.w;
+          const float4 sv = lds4(CY + ly0 * kCols + 4 * lane);
+          tc.kS0[0] = sv.x, tc.kS0[1] = sv.y, tc.kS0[2] = sv.z, tc.kS0[3] = sv.w;
         }
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const int gy = gy0 + ly0 + r;
-        const bool ok = colok && gy >= 0 && gy < g.n1;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const float kw = (e > 0) ? tc.kE[r][e - 1] : kW0[r];
           const float ks = (r > 0) ? tc.kN[r - 1][e] : tc.kS0[e];
-          tc.kD[r][e] = ok ? 1.f + ((tc.kE[r][e] + kw) + (tc.kN[r][e] + ks)) : 0.f;
+          tc.kD[r][e] = 1.f + ((tc.kE[r][e] + kw) + (tc.kN[r][e] + ks));
         }
       }
     }
@@ -291,7 +317,11 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     fence_async_smem();
     __syncthreads();
     if (*s_abort) break;
-    if (threadIdx.x == 0 && it + 1 < total) issue_pass<NPASS, PSRC>(it + 1, sm, bars, ntx, &mxk, &mxkm1, &mbhat);
+    if (threadIdx.x == 0) {
+      if (it + 1 < total) issue_pass<NPASS, PSRC>(it + 1, sm, bars, ntx, &mxk, &mxkm1, &mbhat);
+      // everyone has read this tile's coefficients (pass 0, before the barrier above)
+      if (pass == 1 && j + 1 < my_tiles) issue_coef(j + 1, coef, bars, ntx, &mcx, &mcy);
+    }
 
     float* X = sm + (it & 1) * kStage;  // x_k box; then the x_{k-1} box (M) and the bhat box (H)
     float* M = X + kBox;
@@ -370,16 +400,21 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     }
   }
   if (it < total) {
-    // a wait expired: wait (bounded) for the copy in flight into this iteration's stage, record, return
+    // A wait expired: wait (bounded) for the copies in flight, record, return.  In flight are
+    // this iteration's stage and, between pass 1 of a tile and pass 0 of the next, the
+    // coefficient boxes of the next tile.
     if (threadIdx.x == 0) {
+      const int j = it / NPASS, pass = it - j * NPASS;
       mbar_wait(smem_u32(&bars[it & 1]), (unsigned)(it >> 1) & 1u);
+      if (pass == 0 && coef_wait_failed) mbar_wait(smem_u32(&bars[2]), (unsigned)j & 1u);
+      else if (pass >= 1 && j + 1 < my_tiles) mbar_wait(smem_u32(&bars[2]), (unsigned)(j + 1) & 1u);
       atomicOr(&g_quad_tma_fault, 1u);
     }
   }
 }
 
 template <int ELL, int R>
-cudaError_t launch_qt(const GridDesc& g, int psrc, const float* cx, const float* cy, const FieldMap& mxk,
+cudaError_t launch_qt(const GridDesc& g, int psrc, const FieldMap& mcx, const FieldMap& mcy, const FieldMap& mxk,
                       const FieldMap& mxkm1, const FieldMap& mbhat, float* out3, float* out4, const QuadSteps& qs,
                       cudaStream_t s) {
   constexpr int NT = 32 * kRows / R;
@@ -395,12 +430,12 @@ cudaError_t launch_qt(const GridDesc& g, int psrc, const float* cx, const float*
     auto k = k_cheb_quad_tma<ELL, R, 1>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, cx, cy, mxk, mxkm1, mbhat, out3, out4, qs);
+    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs);
   } else {
     auto k = k_cheb_quad_tma<ELL, R, 2>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, cx, cy, mxk, mxkm1, mbhat, out3, out4, qs);
+    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs);
   }
   count_launch();
   return cudaGetLastError();
@@ -412,35 +447,65 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
 
 }  // namespace
 
-cudaError_t encode_field_map(FieldMap* out, const float* base, const GridDesc& g, int ell) {
+namespace {
+
+EncodeTiledFn encode_fn(cudaError_t* err) {
   static EncodeTiledFn fn = nullptr;
+  *err = cudaSuccess;
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    if (e != cudaSuccess) {
+      *err = e;
+      return nullptr;
+    }
+    if (q != cudaDriverEntryPointSuccess || !p) {
+      *err = cudaErrorNotSupported;
+      return nullptr;
+    }
     fn = reinterpret_cast<EncodeTiledFn>(p);
   }
-  if (!out || !base || g.n0 % 4 != 0 || ell < 2 || (reinterpret_cast<uintptr_t>(base) & 15u)) return cudaErrorInvalidValue;
+  return fn;
+}
+
+// FP32 tensor of rank 2 (n0, n1) or 3 (n0, n1, ell), zero fill outside, no swizzle.
+cudaError_t encode(FieldMap* out, const float* base, const GridDesc& g, int rank, int ell, const cuuint32_t* box) {
+  cudaError_t e;
+  EncodeTiledFn fn = encode_fn(&e);
+  if (!fn) return e;
+  if (!out || !base || g.n0 % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u)) return cudaErrorInvalidValue;
   const cuuint64_t dims[3] = {(cuuint64_t)g.n0, (cuuint64_t)g.n1, (cuuint64_t)ell};
   const cuuint64_t strides[2] = {(cuuint64_t)g.n0 * 4u, (cuuint64_t)g.N * 4u};
-  const cuuint32_t box[3] = {(cuuint32_t)kCols, (cuuint32_t)kRows, 2u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
-  const CUresult r = fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base),
-                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = fn(reinterpret_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+                        const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const float* cx, const float* cy,
+}  // namespace
+
+cudaError_t encode_field_map(FieldMap* out, const float* base, const GridDesc& g, int ell) {
+  if (ell < 2) return cudaErrorInvalidValue;
+  const cuuint32_t box[3] = {(cuuint32_t)kCols, (cuuint32_t)kRows, 2u};
+  return encode(out, base, g, 3, ell, box);
+}
+
+cudaError_t encode_coef_map(FieldMap* out, const float* base, const GridDesc& g) {
+  const cuuint32_t box[2] = {(cuuint32_t)kCols, (cuuint32_t)kCoefRows};
+  return encode(out, base, g, 2, 1, box);
+}
+
+cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap& mcx, const FieldMap& mcy,
                             const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3, float* out4,
                             const QuadSteps& qs, cudaStream_t s) {
   if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2)) return cudaErrorInvalidValue;
   switch (ell) {
 #define AAO_QT_CASE(L) \
   case L:              \
-    return launch_qt<L, kQuadTmaR>(g, psrc, cx, cy, mxk, mxkm1, mbhat, out3, out4, qs, s);
+    return launch_qt<L, kQuadTmaR>(g, psrc, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, s);
     AAO_QT_CASE(4)
     AAO_QT_CASE(6)
     AAO_QT_CASE(8)
