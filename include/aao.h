@@ -18,8 +18,8 @@
  * Chebyshev semi-iteration steps over the segment of Lemma 2 (P_NC1,
  * Section 5), inverse DFT and unscaling.  Only the ell/2+1 frequencies that
  * are distinct for real input and even ell are computed (Section 3).
- * Outer solver: right-preconditioned flexible GMRES with classical
- * Gram-Schmidt plus one re-orthogonalisation; convergence is the paper's
+ * Outer solver: right-preconditioned flexible GMRES with modified
+ * Gram-Schmidt (classical, once or twice, on request); convergence is the paper's
  * relative residual ||b - script-A x|| / ||b|| (Section 5), certified by an
  * explicit FP64 residual.
  *
@@ -65,6 +65,9 @@ extern "C" {
                            script-A, Arnoldi, Givens, residuals in FP64         */
 
 /* ---- limits -------------------------------------------------------------- */
+#define AAO_ORTH_CGS 0   /* classical Gram-Schmidt, one pass                      */
+#define AAO_ORTH_CGS2 1  /* classical Gram-Schmidt with one re-orthogonalisation  */
+#define AAO_ORTH_MGS 2   /* modified Gram-Schmidt (one fused kernel per vector)   */
 #define AAO_MAX_ELL 16      /* ell must be even, 4 <= ell <= AAO_MAX_ELL        */
 #define AAO_MAX_RESTART 64  /* Krylov cycle length limit                        */
 #define AAO_MAX_HIST 512    /* residual history entries kept in aao_stats       */
@@ -77,7 +80,8 @@ typedef struct {
   int32_t prec;            /* AAO_FP64 or AAO_MIXED (default AAO_MIXED)                 */
   int32_t inner_its;       /* p >= 1: Chebyshev steps per frequency (default 20)         */
   int32_t restart;         /* Krylov cycle length m, 1..AAO_MAX_RESTART (default 64)     */
-  int32_t reorth;          /* 1: CGS with one re-orthogonalisation (default); 0: CGS once */
+  int32_t orth;            /* Arnoldi orthogonalisation: AAO_ORTH_MGS (default),
+                              AAO_ORTH_CGS2 or AAO_ORTH_CGS                           */
   double mu_max_override;  /* > 0: upper spectral bound of A to use instead of the
                               Gershgorin bound max_c (1 + 2 sum_f kappa_f) (default 0)   */
   void* stream;            /* cudaStream_t for all work of the handle (NULL = default)  */

@@ -30,6 +30,9 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
             "aao_set_step_kernel", "aao_get_step_kernel")
 
+# Arnoldi orthogonalisation (aao_options.orth)
+AAO_ORTH_CGS, AAO_ORTH_CGS2, AAO_ORTH_MGS = 0, 1, 2
+
 # four-step kernel selection (aao_set_step_kernel)
 AAO_STEP_AUTO, AAO_STEP_TILE, AAO_STEP_TMA = 0, 1, 2
 
@@ -46,7 +49,7 @@ class AaoError(RuntimeError):
 
 class aao_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("inner_its", C.c_int32), ("restart", C.c_int32),
-                ("reorth", C.c_int32), ("mu_max_override", C.c_double), ("stream", C.c_void_p)]
+                ("orth", C.c_int32), ("mu_max_override", C.c_double), ("stream", C.c_void_p)]
 
 
 class aao_stats(C.Structure):
@@ -328,12 +331,13 @@ class Solver:
     """Owns one handle; methods forward to the C ABI (marshalling only)."""
 
     def __init__(self, dim, n, kx, ky, kz, ell, alpha, prec=AAO_MIXED, inner_its=20, restart=64,
-                 reorth=True, mu_max_override=0.0, stream=None):
+                 orth=None, mu_max_override=0.0, stream=None):
         opt = aao_default_options()
         opt.prec = int(prec)
         opt.inner_its = int(inner_its)
         opt.restart = int(restart)
-        opt.reorth = 1 if reorth else 0
+        if orth is not None:
+            opt.orth = int(orth)
         opt.mu_max_override = float(mu_max_override)
         opt.stream = stream
         self.ell = int(ell)

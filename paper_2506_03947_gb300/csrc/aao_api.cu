@@ -45,7 +45,7 @@ struct aao_ctx {
   int palloc[aao::kMaxF] = {};   // per-frequency steps m = 0..ell/2 (NC2); all == p for NC1
   bool nc2 = false;
   int m = 64;
-  int reorth = 1;
+  int orth = AAO_ORTH_MGS;
   double mu_min = 1.0, mu_max = 0.0;
   cudaStream_t stream = nullptr;
   GridDesc g{};
@@ -61,6 +61,7 @@ struct aao_ctx {
   bool tma_used = false;                               // TMA kernel launched since the last fault check
   double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
   double* sc = nullptr;                                // small scalars, ScLayout
+  unsigned* counter = nullptr;                         // last-block ticket of the MGS steps (0 at rest)
   double* partials = nullptr;                          // reduction partials
   int64_t part_cap = 0;
   double *stage_a = nullptr, *stage_b = nullptr;       // staging for host pointers (L each)
@@ -443,6 +444,57 @@ int residual(aao_ctx* h, const double* b, const double* x, double* r, double* rn
   return read_scalars(h, Lsc.nrm2(), 1, rn2);
 }
 
+// Orthogonalise w = V_{j+1} against V_0 .. V_j (Arnoldi step j): the coefficients
+// go to h1 (and h2 for the second classical pass), ||w||^2 of the result to nrm2.
+int orthogonalize(aao_ctx* h, int j, double* w) {
+  const ScLayout Lsc{h->m};
+  const int64_t L = h->L;
+  cudaStream_t s = h->stream;
+  const int nv = j + 1;
+  const int nb = aao::reduction_blocks(L);
+  double* normpart = h->partials + (int64_t)(h->m + 1) * nb;
+  if (h->orth == AAO_ORTH_MGS) {
+    // modified Gram-Schmidt, one fused kernel per basis vector: step i subtracts the
+    // projection on V_{i-1} and forms V_i . w; its last block writes h_i.  Bytes: the first
+    // step reads V_0 and w, the middle ones read V_{i-1}, V_i, w and write w, the last
+    // reads V_j and w and writes w (and forms ||w||^2).
+    const double bytes = 8.0 * (double)L * (2.0 + 4.0 * (nv - 1) + 3.0);
+    const int pi = prof_begin(h, AAO_PROF_ORTH, bytes, nv + 1);
+    const double* vs = h->sc + Lsc.vscale(0);
+    AAO_CK(h, aao::launch_mgs_step(h->V, L, -1, 0, vs, nullptr, h->sc + Lsc.h1(0), w, L, h->partials, h->counter,
+                                   s));
+    for (int i = 1; i < nv; ++i)
+      AAO_CK(h, aao::launch_mgs_step(h->V, L, i - 1, i, vs, h->sc + Lsc.h1(i - 1), h->sc + Lsc.h1(i), w, L,
+                                     h->partials, h->counter, s));
+    AAO_CK(h, aao::launch_mgs_step(h->V, L, nv - 1, -1, vs, h->sc + Lsc.h1(nv - 1), h->sc + Lsc.nrm2(), w, L,
+                                   h->partials, h->counter, s));
+    prof_end(h, pi);
+    return AAO_OK;
+  }
+  // classical Gram-Schmidt (once, or twice for CGS2): algorithmic bytes = each V_i read
+  // once per pass plus w
+  const int ndot = (nv + 7) / 8;
+  const double dot_bytes = 8.0 * (double)L * (nv + ndot);
+  const double upd_bytes = 8.0 * (double)L * (nv + 2);
+  const bool reorth = h->orth == AAO_ORTH_CGS2;
+  const int passes = reorth ? 2 : 1;
+  const int pi = prof_begin(h, AAO_PROF_ORTH, passes * (dot_bytes + upd_bytes), passes * (ndot + 2) + 1);
+  AAO_CK(h, aao::launch_multidot(h->V, L, nv, h->sc + Lsc.vscale(0), w, L, h->partials, s));
+  AAO_CK(h, aao::launch_reduce(h->partials, nv, nb, h->sc + Lsc.h1(0), 0, s));
+  if (reorth) {
+    AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h1(0), h->sc + Lsc.vscale(0), w, L, nullptr, s));
+    AAO_CK(h, aao::launch_multidot(h->V, L, nv, h->sc + Lsc.vscale(0), w, L, h->partials, s));
+    AAO_CK(h, aao::launch_reduce(h->partials, nv, nb, h->sc + Lsc.h2(0), 0, s));
+    AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h2(0), h->sc + Lsc.vscale(0), w, L, normpart, s));
+  } else {
+    AAO_CK(h, cudaMemsetAsync(h->sc + Lsc.h2(0), 0, sizeof(double) * nv, s));
+    AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h1(0), h->sc + Lsc.vscale(0), w, L, normpart, s));
+  }
+  AAO_CK(h, aao::launch_reduce(normpart, 1, nb, h->sc + Lsc.nrm2(), 0, s));
+  prof_end(h, pi);
+  return AAO_OK;
+}
+
 int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer, int fixed) {
   const ScLayout Lsc{h->m};
   const int64_t L = h->L;
@@ -507,28 +559,8 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
       if (rc) return rc;
       rc = matvec(h, Zj, nullptr, w, nullptr);
       if (rc) return rc;
-      const int nv = j + 1;
-      const int nb = aao::reduction_blocks(L);
-      // Gram-Schmidt: algorithmic bytes = each V_i read once per pass plus w
-      const int ndot = (nv + 7) / 8;
-      const double dot_bytes = 8.0 * (double)L * (nv + ndot);
-      const double upd_bytes = 8.0 * (double)L * (nv + 2);
-      const int passes = h->reorth ? 2 : 1;
-      const int pi = prof_begin(h, AAO_PROF_ORTH, passes * (dot_bytes + upd_bytes), passes * (ndot + 2) + 1);
-      AAO_CK(h, aao::launch_multidot(h->V, L, nv, h->sc + Lsc.vscale(0), w, L, h->partials, s));
-      AAO_CK(h, aao::launch_reduce(h->partials, nv, nb, h->sc + Lsc.h1(0), 0, s));
-      double* normpart = h->partials + (int64_t)(h->m + 1) * nb;
-      if (h->reorth) {
-        AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h1(0), h->sc + Lsc.vscale(0), w, L, nullptr, s));
-        AAO_CK(h, aao::launch_multidot(h->V, L, nv, h->sc + Lsc.vscale(0), w, L, h->partials, s));
-        AAO_CK(h, aao::launch_reduce(h->partials, nv, nb, h->sc + Lsc.h2(0), 0, s));
-        AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h2(0), h->sc + Lsc.vscale(0), w, L, normpart, s));
-      } else {
-        AAO_CK(h, cudaMemsetAsync(h->sc + Lsc.h2(0), 0, sizeof(double) * nv, s));
-        AAO_CK(h, aao::launch_orth_update(h->V, L, nv, h->sc + Lsc.h1(0), h->sc + Lsc.vscale(0), w, L, normpart, s));
-      }
-      AAO_CK(h, aao::launch_reduce(normpart, 1, nb, h->sc + Lsc.nrm2(), 0, s));
-      prof_end(h, pi);
+      rc = orthogonalize(h, j, w);
+      if (rc) return rc;
       AAO_CK(h, aao::launch_givens(h->sc, j, h->m, bnorm, s));
       double eh[2];
       rc = read_scalars(h, Lsc.est(), 2, eh);
@@ -757,7 +789,7 @@ void aao_default_options(aao_options* opt) {
   opt->prec = AAO_MIXED;
   opt->inner_its = 20;
   opt->restart = 64;
-  opt->reorth = 1;
+  opt->orth = AAO_ORTH_MGS;
   opt->mu_max_override = 0.0;
   opt->stream = nullptr;
 }
@@ -773,7 +805,7 @@ void aao_destroy(aao_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   void* dev[] = {h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32, h->bhat, h->xa, h->xb, h->xc,
-                 h->xd,   h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b};
+                 h->xd,   h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b, h->counter};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -805,6 +837,8 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
     return fail(nullptr, AAO_EINVAL, "alpha must satisfy 0 < alpha < mu_min^ell = 1 (got %g)", alpha);
   if (opt.prec != AAO_FP64 && opt.prec != AAO_MIXED) return fail(nullptr, AAO_EINVAL, "bad precision mode %d", opt.prec);
   if (opt.inner_its < 1 || opt.inner_its > 100000) return fail(nullptr, AAO_EINVAL, "inner_its must be in [1, 100000]");
+  if (opt.orth != AAO_ORTH_CGS && opt.orth != AAO_ORTH_CGS2 && opt.orth != AAO_ORTH_MGS)
+    return fail(nullptr, AAO_EINVAL, "bad orthogonalisation mode %d", opt.orth);
   if (opt.restart < 1 || opt.restart > AAO_MAX_RESTART)
     return fail(nullptr, AAO_EINVAL, "restart must be in [1, %d]", AAO_MAX_RESTART);
   if (!(opt.mu_max_override >= 0.0) || !std::isfinite(opt.mu_max_override))
@@ -828,7 +862,7 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   h->prec = opt.prec;
   h->p = opt.inner_its;
   h->m = opt.restart;
-  h->reorth = opt.reorth ? 1 : 0;
+  h->orth = opt.orth;
   h->stream = (cudaStream_t)opt.stream;
   h->g.n0 = (int)n[0];
   h->g.n1 = (int)n[1];
@@ -865,6 +899,8 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   const ScLayout Lsc{h->m};
   AAO_CK_CREATE(cudaMalloc(&h->sc, sizeof(double) * Lsc.size()));
   AAO_CK_CREATE(cudaMemset(h->sc, 0, sizeof(double) * Lsc.size()));
+  AAO_CK_CREATE(cudaMalloc(&h->counter, sizeof(unsigned)));
+  AAO_CK_CREATE(cudaMemset(h->counter, 0, sizeof(unsigned)));
   AAO_CK_CREATE(cudaMallocHost(&h->pinned, sizeof(double) * 16));
 
   // face arrays: device pointers are used in place, host arrays are staged

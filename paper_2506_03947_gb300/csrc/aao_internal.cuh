@@ -132,6 +132,14 @@ cudaError_t launch_multidot(const double* V, int64_t ldv, int nv, const double* 
 // w -= sum_i (h[i] * vscale[i]) V_i for i < nv; optional per-block partial sums of w^2.
 cudaError_t launch_orth_update(const double* V, int64_t ldv, int nv, const double* h, const double* vscale,
                                double* w, int64_t L, double* partials_norm, cudaStream_t s);
+// One fused modified Gram-Schmidt step (see mgs_step_body): with iprev >= 0,
+// w -= (*hprev) vscale[iprev] V_iprev; then *hnext = vscale[inext] * V_inext . w
+// (inext >= 0) or w . w (inext < 0), summed by the last block to finish over
+// mgs_blocks(L) partials in part.  counter: one unsigned, zero between launches.
+int mgs_blocks(int64_t L);
+cudaError_t launch_mgs_step(const double* V, int64_t ldv, int iprev, int inext, const double* vscale,
+                            const double* hprev, double* hnext, double* w, int64_t L, double* part,
+                            unsigned* counter, cudaStream_t s);
 // partial sums of v^2 per block.
 cudaError_t launch_norm2_partials(const double* v, int64_t L, double* partials, cudaStream_t s);
 // out[i] (+)= sum_b partials[i*NB + b] for i < nv, fixed order (deterministic).

@@ -124,6 +124,37 @@ cudaError_t launch_orth_update(const double* V, int64_t ldv, int nv, const doubl
 }
 
 __global__ void __launch_bounds__(kRedThreads)
+    k_mgs_step(const double* __restrict__ V, int64_t ldv, int iprev, int inext, const double* __restrict__ vscale,
+               const double* __restrict__ hprev, double* __restrict__ hnext, double* __restrict__ w, int64_t L,
+               double* __restrict__ part, unsigned* __restrict__ counter) {
+  mgs_step_body(blockIdx.x, gridDim.x, V, ldv, iprev, inext, vscale, hprev, hnext, w, L, part, counter);
+}
+
+// Blocks of the modified Gram-Schmidt steps: three per SM (the kernel is bound by the FP64
+// pipe, and fewer blocks mean fewer partial sums), at most reduction_blocks(L).
+int mgs_blocks(int64_t L) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm <= 0) {
+      cudaGetLastError();
+      nsm = 152;
+    }
+  }
+  const int nb = reduction_blocks(L);
+  return nb < 3 * nsm ? nb : 3 * nsm;
+}
+
+cudaError_t launch_mgs_step(const double* V, int64_t ldv, int iprev, int inext, const double* vscale,
+                            const double* hprev, double* hnext, double* w, int64_t L, double* part,
+                            unsigned* counter, cudaStream_t s) {
+  k_mgs_step<<<mgs_blocks(L), kRedThreads, 0, s>>>(V, ldv, iprev, inext, vscale, hprev, hnext, w, L, part, counter);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads)
     k_norm2_partials(const double* __restrict__ v, int64_t L, double* __restrict__ partials) {
   norm2_body(blockIdx.x, gridDim.x, v, L, partials);
 }

@@ -106,6 +106,9 @@ __device__ __forceinline__ void aao_matvec_body(const GridDesc& g, int ell, int 
   }
 }
 
+// Dot products accumulate as explicit FMA chains: on GB300 the FP64 pipe is the
+// limit of these kernels, and a*b + c*d + acc would cost a multiply, an FMA and
+// an add instead of two FMAs.
 template <int G>
 __device__ __forceinline__ void multidot_body(int blk, int nblk, const double* __restrict__ V, int64_t ldv, int i0,
                                               const double* __restrict__ vscale, const double* __restrict__ w,
@@ -127,7 +130,7 @@ __device__ __forceinline__ void multidot_body(int blk, int nblk, const double* _
       for (int q = 0; q < G; ++q) {
         const double* vq = V0 + (int64_t)q * ldv;
         const double2 va = ld2(vq + 2 * e2), vb = ld2(vq + 2 * (e2 + nthr));
-        acc[q] += va.x * wa.x + va.y * wa.y + vb.x * wb.x + vb.y * wb.y;
+        acc[q] = fma(vb.y, wb.y, fma(vb.x, wb.x, fma(va.y, wa.y, fma(va.x, wa.x, acc[q]))));
       }
     }
     for (; e2 < L2; e2 += nthr) {
@@ -135,7 +138,7 @@ __device__ __forceinline__ void multidot_body(int blk, int nblk, const double* _
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         const double2 va = ld2(V0 + (int64_t)q * ldv + 2 * e2);
-        acc[q] += va.x * wa.x + va.y * wa.y;
+        acc[q] = fma(va.y, wa.y, fma(va.x, wa.x, acc[q]));
       }
     }
   } else {
@@ -194,7 +197,7 @@ __device__ __forceinline__ void orth_update_body(int blk, int nblk, const double
         v.y -= coef[q] * a.y;
       }
       *reinterpret_cast<double2*>(w + 2 * e2) = v;
-      acc2 += v.x * v.x + v.y * v.y;
+      acc2 = fma(v.y, v.y, fma(v.x, v.x, acc2));
     }
   } else {
     for (int64_t e = tid; e < L; e += nthr) {
@@ -210,6 +213,103 @@ __device__ __forceinline__ void orth_update_body(int blk, int nblk, const double
   }
 }
 
+
+// L2 eviction-priority policies (PTX createpolicy): the vector being orthogonalised is
+// re-read by every modified Gram-Schmidt step and is kept (evict_last); the basis
+// vectors stream past it (evict_first).
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ double2 ld2_pol(const double* p, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld2_ro_pol(const double* p, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st2_pol(double* p, double2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
+}
+
+// One fused step of modified Gram-Schmidt on w (block-major FP64, length L):
+//   iprev >= 0: w -= (hprev * vscale[iprev]) V_iprev;
+//   then the block's partial of V_inext . w (inext >= 0) or of w . w (inext < 0) goes to
+//   part[blk]; the last block to finish (ticket on *counter) sums the nblk partials in a
+//   fixed order and writes *hnext = vscale[inext] * sum (or the plain sum for w . w),
+//   then resets the counter for the next launch.
+// Every block owns the same element slice in every step, so w needs no grid-wide sync.
+__device__ __forceinline__ void mgs_step_body(int blk, int nblk, const double* __restrict__ V, int64_t ldv, int iprev,
+                                              int inext, const double* __restrict__ vscale,
+                                              const double* __restrict__ hprev, double* __restrict__ hnext,
+                                              double* __restrict__ w, int64_t L, double* __restrict__ part,
+                                              unsigned* __restrict__ counter) {
+  __shared__ double sh[kRedWarps];
+  __shared__ int s_last;
+  const double coef = (iprev >= 0) ? *hprev * (vscale ? vscale[iprev] : 1.0) : 0.0;
+  const double* Vp = V + (int64_t)(iprev >= 0 ? iprev : 0) * ldv;
+  const double* Vn = V + (int64_t)(inext >= 0 ? inext : 0) * ldv;
+  double acc = 0.0;
+  const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  const int64_t tid = (int64_t)blk * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)nblk * blockDim.x;
+  if (vec) {
+    const uint64_t keep = l2_policy_keep(), stream = l2_policy_stream();
+    const int64_t L2 = L / 2;
+    for (int64_t e2 = tid; e2 < L2; e2 += nthr) {
+      double2 v = ld2_pol(w + 2 * e2, keep);
+      if (iprev >= 0) {
+        const double2 a = ld2_ro_pol(Vp + 2 * e2, stream);
+        v.x = fma(-coef, a.x, v.x);
+        v.y = fma(-coef, a.y, v.y);
+        st2_pol(w + 2 * e2, v, keep);
+      }
+      if (inext >= 0) {
+        const double2 b = ld2_ro_pol(Vn + 2 * e2, stream);
+        acc = fma(b.y, v.y, fma(b.x, v.x, acc));
+      } else {
+        acc = fma(v.y, v.y, fma(v.x, v.x, acc));
+      }
+    }
+  } else {
+    for (int64_t e = tid; e < L; e += nthr) {
+      double v = w[e];
+      if (iprev >= 0) {
+        v = fma(-coef, __ldg(Vp + e), v);
+        w[e] = v;
+      }
+      acc = (inext >= 0) ? fma(__ldg(Vn + e), v, acc) : fma(v, v, acc);
+    }
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    part[blk] = t;
+    __threadfence();
+    s_last = (atomicAdd(counter, 1u) == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double u = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) u += __ldcg(part + q);
+    u = block_sum(u, sh);
+    if (threadIdx.x == 0) {
+      *hnext = (inext >= 0) ? u * (vscale ? vscale[inext] : 1.0) : u;
+      *counter = 0u;
+    }
+  }
+}
 
 __device__ __forceinline__ void norm2_body(int blk, int nblk, const double* __restrict__ v, int64_t L,
                                            double* __restrict__ partials) {
@@ -292,6 +392,7 @@ __device__ __forceinline__ void cycle_init_body(double* sc, int m) {
   const ScLayout L{m};
   const double beta = sqrt(sc[L.nrm2()]);
   for (int i = 0; i <= m; ++i) sc[L.gv(i)] = 0.0;
+  for (int i = 0; i <= m; ++i) sc[L.h2(i)] = 0.0;   // the single-pass orthogonalisations leave h2 at zero
   sc[L.gv(0)] = beta;
   sc[L.vscale(0)] = (beta > 0.0) ? 1.0 / beta : 0.0;
 }

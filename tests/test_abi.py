@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_default_options(lib):
     from paper_2506_03947_gb300 import binding
     o = binding.aao_default_options()
-    assert (o.prec, o.inner_its, o.restart, o.reorth) == (binding.AAO_MIXED, 20, 64, 1)
+    assert (o.prec, o.inner_its, o.restart, o.orth) == (binding.AAO_MIXED, 20, 64, binding.AAO_ORTH_MGS)
     assert o.mu_max_override == 0.0
 
 
@@ -60,6 +60,11 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     with pytest.raises(binding.AaoError) as ei:
         binding.aao_create(2, (4, 4, 1), np.ones(12), None, None, 10, 1e-2)
     assert "ky" in str(ei.value)
+    opt = binding.aao_default_options()
+    opt.orth = 7
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_create(1, (8, 1, 1), kx, None, None, 10, 1e-2, opt)
+    assert ei.value.status == binding.AAO_EINVAL and "orthogonalisation" in str(ei.value)
 
 
 def test_no_gpu_means_loud_failure(lib):
