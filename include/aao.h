@@ -58,6 +58,7 @@ extern "C" {
 #define AAO_ECUDA 3     /* a CUDA call failed (no device, launch error, ...)    */
 #define AAO_ENOTCONV 4  /* solve hit max_outer; x holds the last iterate        */
 #define AAO_ENUMERIC 5  /* a NaN or Inf appeared in a residual or norm          */
+#define AAO_ETIMEOUT 6  /* a bounded device-side wait expired (see aao_set_wait_limit) */
 
 /* ---- precision modes ----------------------------------------------------- */
 #define AAO_FP64 0      /* every step in FP64                                   */
@@ -198,14 +199,27 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
  *   AAO_STEP_TMA   the persistent TMA-fed kernel (one CTA per SM).
  * Returns AAO_EINVAL for an unknown kind, or when the handle has no fused
  * 2D path (FP64, 1D/3D, n0 % 4 != 0) or, for AAO_STEP_TMA, no descriptors.
- * A TMA wait in the persistent kernel that does not finish within about a
- * second of SM clock makes the enclosing aao_solve / aao_solve_ci /
- * aao_precond_apply return AAO_ECUDA (the flag is per device).
+ * A TMA wait in the persistent kernel that does not finish within the wait
+ * limit (about a second of SM clock by default) makes the enclosing
+ * aao_solve / aao_solve_ci / aao_precond_apply return AAO_ETIMEOUT; the
+ * kernel first lets its own copies land, so the handle stays usable.  The
+ * fault flag is per device.
  */
 #define AAO_STEP_AUTO 0
 #define AAO_STEP_TILE 1
 #define AAO_STEP_TMA 2
 int aao_set_step_kernel(aao_handle h, int kind);
+/*
+ * Bound, in SM clock cycles, of each wait of the persistent TMA kernel on its
+ * copies (no counterpart in the paper).  Default 2e9 (about a second).  A
+ * small value makes the waits expire before the copies land: the kernel then
+ * records the expiry, waits for its copies with the default bound, returns,
+ * and the call reports AAO_ETIMEOUT.  This is the fault-injection hook for
+ * testing that path without faulting or hanging the GPU.  Returns AAO_EINVAL
+ * for cycles < 0.
+ */
+int aao_set_wait_limit(aao_handle h, int64_t cycles);
+
 /* The kernel in use: AAO_STEP_TMA or AAO_STEP_TILE on the fused 2D path,
  * AAO_STEP_AUTO when the handle has none; -1 for a NULL handle. */
 int aao_get_step_kernel(aao_handle h);

@@ -14,12 +14,12 @@ from typing import Optional, Sequence
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libaao.so")
 
-AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOTCONV, AAO_ENUMERIC = 0, 1, 2, 3, 4, 5
+AAO_OK, AAO_EINVAL, AAO_ENOMEM, AAO_ECUDA, AAO_ENOTCONV, AAO_ENUMERIC, AAO_ETIMEOUT = 0, 1, 2, 3, 4, 5, 6
 AAO_FP64, AAO_MIXED = 0, 1
 AAO_MAX_ELL, AAO_MAX_RESTART, AAO_MAX_HIST = 16, 64, 512
 
 STATUS_NAMES = {0: "AAO_OK", 1: "AAO_EINVAL", 2: "AAO_ENOMEM", 3: "AAO_ECUDA",
-                4: "AAO_ENOTCONV", 5: "AAO_ENUMERIC"}
+                4: "AAO_ENOTCONV", 5: "AAO_ENUMERIC", 6: "AAO_ETIMEOUT"}
 
 # every symbol include/aao.h declares (checked by the CPU test suite)
 EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_apply", "aao_solve",
@@ -28,7 +28,10 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
             "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
-            "aao_set_step_kernel", "aao_get_step_kernel")
+            "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit")
+
+# default bound of the persistent kernel's device-side waits, SM clocks
+DEFAULT_WAIT_CYCLES = 2000000000
 
 # Arnoldi orthogonalisation (aao_options.orth)
 AAO_ORTH_CGS, AAO_ORTH_CGS2, AAO_ORTH_MGS = 0, 1, 2
@@ -130,6 +133,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_set_step_kernel.restype = i32
     lib.aao_get_step_kernel.argtypes = [vp]
     lib.aao_get_step_kernel.restype = i32
+    lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
+    lib.aao_set_wait_limit.restype = i32
     _lib = lib
     return lib
 
@@ -258,6 +263,10 @@ def aao_set_step_kernel(h, kind: int) -> int:
     return _check(h, load_library().aao_set_step_kernel(h, int(kind)))
 
 
+def aao_set_wait_limit(h, cycles: int) -> int:
+    return _check(h, load_library().aao_set_wait_limit(h, int(cycles)))
+
+
 def aao_get_step_kernel(h) -> int:
     return load_library().aao_get_step_kernel(h)
 
@@ -376,6 +385,9 @@ class Solver:
 
     def step_kernel(self):
         return aao_get_step_kernel(self.h)
+
+    def set_wait_limit(self, cycles):
+        return aao_set_wait_limit(self.h, cycles)
 
     def profile_enable(self, on=True):
         return aao_profile_enable(self.h, on)

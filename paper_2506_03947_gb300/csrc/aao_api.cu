@@ -59,6 +59,7 @@ struct aao_ctx {
   bool tma = false;                                    // descriptors built: persistent four-step kernel usable
   int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
   bool tma_used = false;                               // TMA kernel launched since the last fault check
+  long long wait_limit = aao::kQuadTmaWaitCycles;      // bound of the TMA waits (aao_set_wait_limit)
   double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
   double* sc = nullptr;                                // small scalars, ScLayout
   unsigned* counter = nullptr;                         // last-block ticket of the MGS steps (0 at rest)
@@ -342,7 +343,8 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
     pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
     if (h->tma && h->step_kernel != AAO_STEP_TILE) {
       AAO_CK(h, aao::launch_quad_tma(h->g, h->ell, prev < 0 ? 1 : 2, h->fmap[5], h->fmap[6], h->fmap[cur],
-                                     h->fmap[prev < 0 ? cur : prev], h->fmap[4], X[o[0]], X[o[1]], qs, s));
+                                     h->fmap[prev < 0 ? cur : prev], h->fmap[4], X[o[0]], X[o[1]], qs,
+                                     h->wait_limit, s));
       h->tma_used = true;
     } else {
       AAO_CK(h, aao::launch_quad(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
@@ -398,9 +400,8 @@ int check_tma(aao_ctx* h) {
   h->tma_used = false;
   unsigned flag = 0;
   AAO_CK(h, aao::quad_tma_fault(&flag, h->stream));
-  if (flag)
-    return fail(h, AAO_ECUDA, "four-step TMA kernel: %s",
-                (flag & 2u) ? "shared-memory base not 128-byte aligned" : "a TMA wait expired");
+  if (flag & 2u) return fail(h, AAO_ECUDA, "four-step TMA kernel: shared-memory base not 128-byte aligned");
+  if (flag) return fail(h, AAO_ETIMEOUT, "four-step TMA kernel: a bounded TMA wait expired");
   return AAO_OK;
 }
 
@@ -1123,6 +1124,13 @@ int aao_set_step_kernel(aao_handle h, int kind) {
   if (kind == AAO_STEP_TILE && !h->pairs)
     return fail(h, AAO_EINVAL, "the fused tile kernels need the 2D mixed path with n0 %% 4 == 0");
   h->step_kernel = kind;
+  return AAO_OK;
+}
+
+int aao_set_wait_limit(aao_handle h, int64_t cycles) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (cycles < 0) return fail(h, AAO_EINVAL, "wait limit must be >= 0 SM clocks");
+  h->wait_limit = cycles;
   return AAO_OK;
 }
 

@@ -103,6 +103,7 @@ cudaError_t launch_quad(const GridDesc& g, int ell, int psrc, const float* cx, c
 // FP32 fields (3D: n0, n1, ell; box 128 x (kQuadTmaTY + 8) x 2).
 constexpr int kQuadTmaTY = 16;
 constexpr int kQuadTmaR = 2;
+constexpr long long kQuadTmaWaitCycles = 2000000000ll;  // bound of one TMA wait (~1 s at 2 GHz)
 struct alignas(64) FieldMap {
   unsigned long long opaque[16];  // a CUtensorMap
 };
@@ -112,9 +113,10 @@ cudaError_t encode_field_map(FieldMap* out, const float* base, const GridDesc& g
 cudaError_t encode_coef_map(FieldMap* out, const float* base, const GridDesc& g);
 // Same contract as launch_quad; the face arrays cx, cy and the fields xk, xkm1
 // (psrc == 2 only) and bhat are given by their descriptors.
+// wait_limit: bound of each TMA wait in SM clocks (kQuadTmaWaitCycles normally).
 cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap& mcx, const FieldMap& mcy,
                             const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3,
-                            float* out4, const QuadSteps& qs, cudaStream_t s);
+                            float* out4, const QuadSteps& qs, long long wait_limit, cudaStream_t s);
 // Read and clear the device flag of expired TMA waits (bit 0) or a misaligned
 // shared-memory base (bit 1); synchronises s.
 cudaError_t quad_tma_fault(unsigned* flag, cudaStream_t s);

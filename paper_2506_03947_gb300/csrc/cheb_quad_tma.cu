@@ -25,9 +25,9 @@
 //    loads per plane; east/west neighbours come from warp shuffles.
 //  * After four levels the interior (lanes 1..30, rows 4..19) holds x_{k+3}
 //    and x_{k+4}; both are stored straight from registers.
-// Every wait on a TMA transaction is bounded (about a second of SM clock);
-// on expiry the block records the fault in a device flag, waits (bounded)
-// for its copy in flight and returns.
+// Every wait on a TMA transaction is bounded (wait_limit SM clocks, about a
+// second by default); on expiry the block records the fault in a device flag,
+// waits (with the default bound) for its copies in flight and returns.
 #include <cuda.h>
 
 #include "aao_internal.cuh"
@@ -77,13 +77,28 @@ __device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
   return done != 0;
 }
 
-// Wait for the phase of the given parity, for at most ~1 s of SM clocks.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+// Non-blocking test (try_wait above may suspend the thread for a while in hardware).
+__device__ __forceinline__ bool mbar_peek(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for the phase of the given parity, for at most `limit` SM clocks (and 2^24 polls);
+// a zero limit only tests once, without blocking.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit = kQuadTmaWaitCycles) {
+  if (limit <= 0) return mbar_peek(bar, parity);
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   for (int i = 0; i < (1 << 24); ++i) {
     if (mbar_test(bar, parity)) return true;
-    if (clock64() - t0 > 2000000000ll) break;
+    if (clock64() - t0 > limit) break;
   }
   return false;
 }
@@ -236,7 +251,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     k_cheb_quad_tma(GridDesc g, int ntx, int ntiles, const __grid_constant__ FieldMap mcx,
                     const __grid_constant__ FieldMap mcy, const __grid_constant__ FieldMap mxk,
                     const __grid_constant__ FieldMap mxkm1, const __grid_constant__ FieldMap mbhat,
-                    float* __restrict__ out3, float* __restrict__ out4, QuadSteps qa) {
+                    float* __restrict__ out3, float* __restrict__ out4, QuadSteps qa, long long wait_limit) {
   constexpr int NPASS = ELL / 2;
   extern __shared__ __align__(1024) float sm[];
   float* coef = sm + 2 * kStage;  // cx box, then cy box: [kCoefRows][kCols], row j = staged row j - 1
@@ -283,7 +298,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
       // Face coefficients of the thread's cells (zero outside the grid, by the TMA fill) and the
       // diagonal d = 1 + sum of the four faces.  Lane 0's west face belongs to staged column 0,
       // whose new levels are never used; it is taken as 0.
-      if (!mbar_wait(smem_u32(&bars[2]), (unsigned)j & 1u)) {
+      if (!mbar_wait(smem_u32(&bars[2]), (unsigned)j & 1u, wait_limit)) {
         *s_abort = 1;
         coef_wait_failed = true;
       }
@@ -313,7 +328,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
       }
     }
     // this iteration's boxes have landed; everyone is done with the other stage
-    if (!mbar_wait(smem_u32(&bars[it & 1]), (unsigned)(it >> 1) & 1u)) *s_abort = 1;
+    if (!mbar_wait(smem_u32(&bars[it & 1]), (unsigned)(it >> 1) & 1u, wait_limit)) *s_abort = 1;
     fence_async_smem();
     __syncthreads();
     if (*s_abort) break;
@@ -416,7 +431,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
 template <int ELL, int R>
 cudaError_t launch_qt(const GridDesc& g, int psrc, const FieldMap& mcx, const FieldMap& mcy, const FieldMap& mxk,
                       const FieldMap& mxkm1, const FieldMap& mbhat, float* out3, float* out4, const QuadSteps& qs,
-                      cudaStream_t s) {
+                      long long wait_limit, cudaStream_t s) {
   constexpr int NT = 32 * kRows / R;
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -430,12 +445,12 @@ cudaError_t launch_qt(const GridDesc& g, int psrc, const FieldMap& mcx, const Fi
     auto k = k_cheb_quad_tma<ELL, R, 1>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs);
+    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit);
   } else {
     auto k = k_cheb_quad_tma<ELL, R, 2>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs);
+    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit);
   }
   count_launch();
   return cudaGetLastError();
@@ -500,12 +515,12 @@ cudaError_t encode_coef_map(FieldMap* out, const float* base, const GridDesc& g)
 
 cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap& mcx, const FieldMap& mcy,
                             const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3, float* out4,
-                            const QuadSteps& qs, cudaStream_t s) {
-  if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2)) return cudaErrorInvalidValue;
+                            const QuadSteps& qs, long long wait_limit, cudaStream_t s) {
+  if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2) || wait_limit < 0) return cudaErrorInvalidValue;
   switch (ell) {
 #define AAO_QT_CASE(L) \
   case L:              \
-    return launch_qt<L, kQuadTmaR>(g, psrc, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, s);
+    return launch_qt<L, kQuadTmaR>(g, psrc, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit, s);
     AAO_QT_CASE(4)
     AAO_QT_CASE(6)
     AAO_QT_CASE(8)

@@ -113,3 +113,23 @@ def test_full_solve_with_either_kernel_agrees():
     xb, ib = out[binding.AAO_STEP_TILE]
     assert ia == ib
     assert np.abs(xa - xb).max() / np.abs(xb).max() < 1e-7
+
+
+def test_expired_tma_wait_reports_timeout_and_handle_recovers():
+    # fault injection without a GPU fault: a zero wait limit makes the persistent kernel's
+    # first wait on its copies expire; it lets the copies land, records the expiry and
+    # returns; the call reports AAO_ETIMEOUT, and with the default limit the same handle
+    # again produces the reference result
+    binding = ensure_lib()
+    P = _problem(260, 70, 10, 13)
+    r = np.random.default_rng(9).standard_normal((P.ell, P.N))
+    s = make_solver(P, 1, 20)
+    z_ref = _apply(s, r)
+    s.set_wait_limit(0)
+    with pytest.raises(binding.AaoError) as ei:
+        _apply(s, r)
+    assert ei.value.status == binding.AAO_ETIMEOUT
+    s.set_wait_limit(binding.DEFAULT_WAIT_CYCLES)
+    np.testing.assert_array_equal(_apply(s, r), z_ref)
+    with pytest.raises(binding.AaoError):
+        s.set_wait_limit(-1)
