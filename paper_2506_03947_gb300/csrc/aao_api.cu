@@ -496,7 +496,8 @@ int orthogonalize(aao_ctx* h, int j, double* w) {
   return AAO_OK;
 }
 
-int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer, int fixed) {
+// x_zero: x holds x_0 = 0 on entry, so the first residual is b itself (no script-A product).
+int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer, int fixed, bool x_zero) {
   const ScLayout Lsc{h->m};
   const int64_t L = h->L;
   cudaStream_t s = h->stream;
@@ -532,9 +533,15 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
   const int m = fixed ? fixed : h->m;
   while (true) {
     double rn2 = 0.0;
-    rc = residual(h, b, x, h->V, &rn2);
-    if (rc) return rc;
-    st.a_matvecs += h->ell;
+    if (x_zero && st.cycles == 0) {
+      // r_0 = b; sc[nrm2] still holds ||b||^2 from above for the cycle initialisation
+      AAO_CK(h, cudaMemcpyAsync(h->V, b, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+      rn2 = bn2;
+    } else {
+      rc = residual(h, b, x, h->V, &rn2);
+      if (rc) return rc;
+      st.a_matvecs += h->ell;
+    }
     const double rel = std::sqrt(rn2) / bnorm;
     st.resid_explicit = rel;
     if (!std::isfinite(rel)) return fail(h, AAO_ENUMERIC, "residual is not finite");
@@ -1056,7 +1063,7 @@ static int solve_entry(aao_handle h, const double* b, double* x, double tol, int
     if (use_x0) AAO_CK(h, cudaMemcpyAsync(dx, x, sizeof(double) * h->L, cudaMemcpyHostToDevice, h->stream));
   }
   if (!use_x0) AAO_CK(h, cudaMemsetAsync(dx, 0, sizeof(double) * h->L, h->stream));
-  rc = solve_impl(h, db, dx, fixed ? 1.0 : tol, fixed ? fixed : max_outer, fixed);
+  rc = solve_impl(h, db, dx, fixed ? 1.0 : tol, fixed ? fixed : max_outer, fixed, !use_x0);
   if (rc == AAO_OK || rc == AAO_ENOTCONV) {
     const int rt = check_tma(h);
     if (rt) return rt;

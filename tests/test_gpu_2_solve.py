@@ -154,8 +154,9 @@ def test_matvec_count_follows_table1():
     P = inputs.config_2d(n=32)
     _, st = _gpu_solve(P, 1, 12, 1e-8)
     its, cyc = st["outer_its"], st["cycles"]
-    # per Arnoldi step: ell (script-A) + ell*p (P_NC); plus ell per explicit residual
-    assert st["a_matvecs"] == its * (P.ell + P.ell * 12) + (cyc + 1) * P.ell
+    # per Arnoldi step: ell (script-A) + ell*p (P_NC); plus ell per explicit residual,
+    # except the first one, which is b itself for x_0 = 0
+    assert st["a_matvecs"] == its * (P.ell + P.ell * 12) + cyc * P.ell
 
 
 def test_zero_rhs_and_solve_determinism():
