@@ -85,6 +85,8 @@ __device__ __forceinline__ void aao_matvec_body(const GridDesc& g, int ell, int 
 #pragma unroll
     for (int q = 0; q < 2 * DIM; ++q) diag += kap[q];
     double prev = 0.0;
+    // two time blocks per iteration (ell is even): their loads are in flight together
+#pragma unroll 2
     for (int t = 0; t < ell; ++t) {
       const double* xt = x + (int64_t)t * N;
       const double xc = __ldg(xt + c);
@@ -243,23 +245,30 @@ __device__ __forceinline__ void st2_pol(double* p, double2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
 }
 
-// One fused step of modified Gram-Schmidt on w (block-major FP64, length L):
-//   iprev >= 0: w -= (hprev * vscale[iprev]) V_iprev;
-//   then the block's partial of V_inext . w (inext >= 0) or of w . w (inext < 0) goes to
-//   part[blk]; the last block to finish (ticket on *counter) sums the nblk partials in a
-//   fixed order and writes *hnext = vscale[inext] * sum (or the plain sum for w . w),
-//   then resets the counter for the next launch.
-// Every block owns the same element slice in every step, so w needs no grid-wide sync.
+// One fused step of modified Gram-Schmidt on w (block-major FP64, length L).  MODE:
+//   kMgsDot    (first step of a column): partial sums of V_inext . w;
+//   kMgsUpdDot (middle steps): w -= (hprev * vscale[iprev]) V_iprev, then V_inext . w;
+//   kMgsUpdNrm (last step):    the same update, then w . w.
+// Per-block partials go to part[blk]; the last block to finish (ticket on *counter) sums the
+// nblk partials in a fixed order and writes *hnext = vscale[inext] * sum (the plain sum for
+// w . w), then resets the counter for the next launch.  Every block owns the same element
+// slice in every step, so w needs no grid-wide sync.  The mode is a template parameter:
+// with runtime branches in the streaming loop the kernel ran at half its bandwidth.
+constexpr int kMgsDot = 0, kMgsUpdDot = 1, kMgsUpdNrm = 2;
+
+template <int MODE>
 __device__ __forceinline__ void mgs_step_body(int blk, int nblk, const double* __restrict__ V, int64_t ldv, int iprev,
                                               int inext, const double* __restrict__ vscale,
                                               const double* __restrict__ hprev, double* __restrict__ hnext,
                                               double* __restrict__ w, int64_t L, double* __restrict__ part,
                                               unsigned* __restrict__ counter) {
+  constexpr bool UPD = MODE != kMgsDot;
+  constexpr bool DOT = MODE != kMgsUpdNrm;
   __shared__ double sh[kRedWarps];
   __shared__ int s_last;
-  const double coef = (iprev >= 0) ? *hprev * (vscale ? vscale[iprev] : 1.0) : 0.0;
-  const double* Vp = V + (int64_t)(iprev >= 0 ? iprev : 0) * ldv;
-  const double* Vn = V + (int64_t)(inext >= 0 ? inext : 0) * ldv;
+  const double coef = UPD ? *hprev * (vscale ? vscale[iprev] : 1.0) : 0.0;
+  const double* Vp = V + (int64_t)(UPD ? iprev : 0) * ldv;
+  const double* Vn = V + (int64_t)(DOT ? inext : 0) * ldv;
   double acc = 0.0;
   const bool vec = ((L | ldv) & 1) == 0 && ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
   const int64_t tid = (int64_t)blk * blockDim.x + threadIdx.x;
@@ -267,29 +276,33 @@ __device__ __forceinline__ void mgs_step_body(int blk, int nblk, const double* _
   if (vec) {
     const uint64_t keep = l2_policy_keep(), stream = l2_policy_stream();
     const int64_t L2 = L / 2;
+    double a0 = 0.0, a1 = 0.0;
     for (int64_t e2 = tid; e2 < L2; e2 += nthr) {
       double2 v = ld2_pol(w + 2 * e2, keep);
-      if (iprev >= 0) {
+      if (UPD) {
         const double2 a = ld2_ro_pol(Vp + 2 * e2, stream);
         v.x = fma(-coef, a.x, v.x);
         v.y = fma(-coef, a.y, v.y);
         st2_pol(w + 2 * e2, v, keep);
       }
-      if (inext >= 0) {
+      if (DOT) {
         const double2 b = ld2_ro_pol(Vn + 2 * e2, stream);
-        acc = fma(b.y, v.y, fma(b.x, v.x, acc));
+        a0 = fma(b.x, v.x, a0);
+        a1 = fma(b.y, v.y, a1);
       } else {
-        acc = fma(v.y, v.y, fma(v.x, v.x, acc));
+        a0 = fma(v.x, v.x, a0);
+        a1 = fma(v.y, v.y, a1);
       }
     }
+    acc = a0 + a1;
   } else {
     for (int64_t e = tid; e < L; e += nthr) {
       double v = w[e];
-      if (iprev >= 0) {
+      if (UPD) {
         v = fma(-coef, __ldg(Vp + e), v);
         w[e] = v;
       }
-      acc = (inext >= 0) ? fma(__ldg(Vn + e), v, acc) : fma(v, v, acc);
+      acc = DOT ? fma(__ldg(Vn + e), v, acc) : fma(v, v, acc);
     }
   }
   const double t = block_sum(acc, sh);
@@ -305,7 +318,7 @@ __device__ __forceinline__ void mgs_step_body(int blk, int nblk, const double* _
     for (int q = threadIdx.x; q < nblk; q += blockDim.x) u += __ldcg(part + q);
     u = block_sum(u, sh);
     if (threadIdx.x == 0) {
-      *hnext = (inext >= 0) ? u * (vscale ? vscale[inext] : 1.0) : u;
+      *hnext = DOT ? u * (vscale ? vscale[inext] : 1.0) : u;
       *counter = 0u;
     }
   }
