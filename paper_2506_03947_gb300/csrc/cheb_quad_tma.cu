@@ -133,11 +133,10 @@ struct TileCoef {
 
 // One level for the warp's R rows: cur (level q) -> prv (level q-1, overwritten by level q+1).
 // nS / nN: level q of the rows just above and below the warp's rows.
-template <int R>
+template <int R, bool CPLX>
 __device__ __forceinline__ void quad_level(float (&cur)[R][2][4], float (&prv)[R][2][4], const float (&hh)[R][2][4],
                                            const float (&nS)[2][4], const float (&nN)[2][4], const TileCoef<R>& tc,
-                                           const float (&kW0)[R], const StepArgs<float>& st, bool cplx, int m0,
-                                           int m1) {
+                                           const float (&kW0)[R], const StepArgs<float>& st, int m0, int m1) {
   float nb[R][2][4];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -161,7 +160,7 @@ __device__ __forceinline__ void quad_level(float (&cur)[R][2][4], float (&prv)[R
       }
     }
   }
-  if (cplx) {
+  if (CPLX) {
     const float lr = st.lam_re[m0], li = st.lam_im[m0];
     const float ar = st.a_re[m0], ai = st.a_im[m0], gr = st.g_re[m0], gi = st.g_im[m0];
 #pragma unroll
@@ -245,6 +244,84 @@ __device__ __forceinline__ void issue_coef(int j, float* coef, unsigned long lon
   tma_load_2d(smem_u32(coef + kCoef), mcy, tx * kInX - kS, ty * kTY - kS - 1, bar);
 }
 
+// One pass: the four levels on one plane pair, from the staged boxes to the interior outputs.
+// CPLX: the pair is Re/Im of the complex frequency m0 (else the real frequencies m0 and m1);
+// the choice is made once per pass, outside the level code.
+template <int ELL, int R, int PSRC, bool CPLX>
+__device__ __forceinline__ void quad_pass(const float* X, float* M, float* H, int ly0, int lane, const TileCoef<R>& tc,
+                                          const float (&kW0)[R], const QuadSteps& qa, int m0, int m1, bool colok,
+                                          int gy0, int gx, const GridDesc& g, int p0, float* __restrict__ out3,
+                                          float* __restrict__ out4) {
+  const int64_t N = g.N;
+  float xa[R][2][4], xb[R][2][4], hh[R][2][4];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int o = (ly0 + r) * kCols + 4 * lane;
+#pragma unroll
+    for (int pl = 0; pl < 2; ++pl) {
+      const float4 x = lds4(X + pl * kPlane + o);
+      const float4 h = lds4(H + pl * kPlane + o);
+      xa[r][pl][0] = x.x, xa[r][pl][1] = x.y, xa[r][pl][2] = x.z, xa[r][pl][3] = x.w;
+      hh[r][pl][0] = h.x, hh[r][pl][1] = h.y, hh[r][pl][2] = h.z, hh[r][pl][3] = h.w;
+      if (PSRC == 2) {
+        const float4 m = lds4(M + pl * kPlane + o);
+        xb[r][pl][0] = m.x, xb[r][pl][1] = m.y, xb[r][pl][2] = m.z, xb[r][pl][3] = m.w;
+      }
+    }
+    if (PSRC != 2) {
+      // x_1 = bhat / theta (complex division for a complex frequency)
+      const StepArgs<float>& s0 = qa.s[0];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float h0 = hh[r][0][e], h1 = hh[r][1][e];
+        if (CPLX) {
+          xb[r][0][e] = h0 * s0.it_re[m0] - h1 * s0.it_im[m0];
+          xb[r][1][e] = h0 * s0.it_im[m0] + h1 * s0.it_re[m0];
+        } else {
+          xb[r][0][e] = h0 * s0.it_re[m0];
+          xb[r][1][e] = h1 * s0.it_re[m1];
+        }
+      }
+    }
+  }
+  float nS[2][4], nN[2][4];
+  // level 0 -> 1 (neighbours from the x_k box), edge rows of level 1 into M
+  load_halo_rows<R>(X, ly0, lane, nS, nN);
+  quad_level<R, CPLX>(xa, xb, hh, nS, nN, tc, kW0, qa.s[0], m0, m1);
+  store_edge_rows<R>(M, ly0, lane, xb);
+  __syncthreads();
+  // level 1 -> 2, edge rows into H
+  load_halo_rows<R>(M, ly0, lane, nS, nN);
+  quad_level<R, CPLX>(xb, xa, hh, nS, nN, tc, kW0, qa.s[1], m0, m1);
+  store_edge_rows<R>(H, ly0, lane, xa);
+  __syncthreads();
+  // level 2 -> 3, edge rows into M (level 1 there has been read by everyone)
+  load_halo_rows<R>(H, ly0, lane, nS, nN);
+  quad_level<R, CPLX>(xa, xb, hh, nS, nN, tc, kW0, qa.s[2], m0, m1);
+  store_edge_rows<R>(M, ly0, lane, xb);
+  __syncthreads();
+  // level 3 -> 4
+  load_halo_rows<R>(M, ly0, lane, nS, nN);
+  quad_level<R, CPLX>(xb, xa, hh, nS, nN, tc, kW0, qa.s[3], m0, m1);
+
+  // interior: level 4 (xa) -> out4, level 3 (xb) -> out3
+  if (lane >= 1 && lane <= 30 && colok) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int ly = ly0 + r;
+      const int gy = gy0 + ly;
+      if (ly < kS || ly >= kS + kTY || gy >= g.n1) continue;
+      const int64_t c = (int64_t)g.n0 * gy + gx;
+#pragma unroll
+      for (int pl = 0; pl < 2; ++pl) {
+        const int64_t o = (int64_t)(p0 + pl) * N + c;
+        *reinterpret_cast<float4*>(out4 + o) = make_float4(xa[r][pl][0], xa[r][pl][1], xa[r][pl][2], xa[r][pl][3]);
+        *reinterpret_cast<float4*>(out3 + o) = make_float4(xb[r][pl][0], xb[r][pl][1], xb[r][pl][2], xb[r][pl][3]);
+      }
+    }
+  }
+}
+
 // PSRC: x_{k-1} = bhat/theta (1, first fused step is k = 2) or the staged x_{k-1} box (2).
 template <int ELL, int R, int PSRC>
 __global__ void __launch_bounds__(32 * kRows / R, 1)
@@ -259,7 +336,6 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
   volatile int* s_abort = reinterpret_cast<volatile int*>(bars + 3);
   const int lane = threadIdx.x & 31;
   const int ly0 = (threadIdx.x >> 5) * R;
-  const int64_t N = g.N;
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int total = my_tiles * NPASS;
 
@@ -341,78 +417,12 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     float* X = sm + (it & 1) * kStage;  // x_k box; then the x_{k-1} box (M) and the bhat box (H)
     float* M = X + kBox;
     float* H = M + kBox;
-    const bool cplx = pass > 0;
-    const int m0 = pass;                          // frequency of the pair's first plane
-    const int m1 = (pass == 0) ? ELL / 2 : pass;  // and of its second
 
-    float xa[R][2][4], xb[R][2][4], hh[R][2][4];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int o = (ly0 + r) * kCols + 4 * lane;
-#pragma unroll
-      for (int pl = 0; pl < 2; ++pl) {
-        const float4 x = lds4(X + pl * kPlane + o);
-        const float4 h = lds4(H + pl * kPlane + o);
-        xa[r][pl][0] = x.x, xa[r][pl][1] = x.y, xa[r][pl][2] = x.z, xa[r][pl][3] = x.w;
-        hh[r][pl][0] = h.x, hh[r][pl][1] = h.y, hh[r][pl][2] = h.z, hh[r][pl][3] = h.w;
-        if (PSRC == 2) {
-          const float4 m = lds4(M + pl * kPlane + o);
-          xb[r][pl][0] = m.x, xb[r][pl][1] = m.y, xb[r][pl][2] = m.z, xb[r][pl][3] = m.w;
-        }
-      }
-      if (PSRC != 2) {
-        // x_1 = bhat / theta (complex division for a complex frequency)
-        const StepArgs<float>& s0 = qa.s[0];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float h0 = hh[r][0][e], h1 = hh[r][1][e];
-          if (cplx) {
-            xb[r][0][e] = h0 * s0.it_re[m0] - h1 * s0.it_im[m0];
-            xb[r][1][e] = h0 * s0.it_im[m0] + h1 * s0.it_re[m0];
-          } else {
-            xb[r][0][e] = h0 * s0.it_re[m0];
-            xb[r][1][e] = h1 * s0.it_re[m1];
-          }
-        }
-      }
-    }
-    float nS[2][4], nN[2][4];
-    // level 0 -> 1 (neighbours from the x_k box), edge rows of level 1 into M
-    load_halo_rows<R>(X, ly0, lane, nS, nN);
-    quad_level<R>(xa, xb, hh, nS, nN, tc, kW0, qa.s[0], cplx, m0, m1);
-    store_edge_rows<R>(M, ly0, lane, xb);
-    __syncthreads();
-    // level 1 -> 2, edge rows into H
-    load_halo_rows<R>(M, ly0, lane, nS, nN);
-    quad_level<R>(xb, xa, hh, nS, nN, tc, kW0, qa.s[1], cplx, m0, m1);
-    store_edge_rows<R>(H, ly0, lane, xa);
-    __syncthreads();
-    // level 2 -> 3, edge rows into M (level 1 there has been read by everyone)
-    load_halo_rows<R>(H, ly0, lane, nS, nN);
-    quad_level<R>(xa, xb, hh, nS, nN, tc, kW0, qa.s[2], cplx, m0, m1);
-    store_edge_rows<R>(M, ly0, lane, xb);
-    __syncthreads();
-    // level 3 -> 4
-    load_halo_rows<R>(M, ly0, lane, nS, nN);
-    quad_level<R>(xb, xa, hh, nS, nN, tc, kW0, qa.s[3], cplx, m0, m1);
-
-    // interior: level 4 (xa) -> out4, level 3 (xb) -> out3
-    if (lane >= 1 && lane <= 30 && colok) {
-      const int p0 = (pass == 0) ? 0 : 2 * pass;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int ly = ly0 + r;
-        const int gy = gy0 + ly;
-        if (ly < kS || ly >= kS + kTY || gy >= g.n1) continue;
-        const int64_t c = (int64_t)g.n0 * gy + gx;
-#pragma unroll
-        for (int pl = 0; pl < 2; ++pl) {
-          const int64_t o = (int64_t)(p0 + pl) * N + c;
-          *reinterpret_cast<float4*>(out4 + o) = make_float4(xa[r][pl][0], xa[r][pl][1], xa[r][pl][2], xa[r][pl][3]);
-          *reinterpret_cast<float4*>(out3 + o) = make_float4(xb[r][pl][0], xb[r][pl][1], xb[r][pl][2], xb[r][pl][3]);
-        }
-      }
-    }
+    if (pass == 0)
+      quad_pass<ELL, R, PSRC, false>(X, M, H, ly0, lane, tc, kW0, qa, 0, ELL / 2, colok, gy0, gx, g, 0, out3, out4);
+    else
+      quad_pass<ELL, R, PSRC, true>(X, M, H, ly0, lane, tc, kW0, qa, pass, pass, colok, gy0, gx, g, 2 * pass, out3,
+                                    out4);
   }
   if (it < total) {
     // A wait expired: wait (bounded) for the copies in flight, record, return.  In flight are
