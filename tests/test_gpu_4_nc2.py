@@ -69,4 +69,5 @@ def test_nc2_solve_matches_oracle_and_spends_the_budget_better():
     assert ref2.outer_its < ref1.outer_its
     # A-matvec accounting: ell + sum(alloc) per Arnoldi step (Table 1 with Algorithm 1)
     st = res["nc2"][0]
-    assert st["a_matvecs"] == st["outer_its"] * (P.ell + sum(alloc)) + (st["cycles"] + 1) * P.ell
+    # plus ell per explicit residual except the first (b itself for x_0 = 0)
+    assert st["a_matvecs"] == st["outer_its"] * (P.ell + sum(alloc)) + st["cycles"] * P.ell
