@@ -221,12 +221,17 @@ def run_ours(args):
                          restart=64, stream=sptr)
     sampler = ClockSampler(local) if not args.no_clocks else None
     quad_kind = s32.step_kernel()
-    ms, wall, launches, prof, clocks, st32 = timed_solves(s32, args.steps, args.warmup, profile=True,
-                                                          sampler=sampler)
+    # timed solves run as the library runs them by default (each Arnoldi step replayed from
+    # its CUDA graph); the per-kernel-class breakdown comes from a separate profiled pass,
+    # where every class is bracketed by CUDA events on the launching stream
+    ms, wall, launches, _, clocks, st32 = timed_solves(s32, args.steps, args.warmup, profile=False,
+                                                       sampler=sampler)
     walls32 = list(timed_solves.walls)
     ms_max = max_over_ranks(ms)
     value = world * args.steps / (ms_max / 1e3)
     x32 = x.clone()
+    prof_steps = max(3, args.steps // 2)
+    ms_prof, _, _, prof, _, _ = timed_solves(s32, prof_steps, 1, profile=True)
 
     # --- end to end through the C ABI with pinned host buffers (copies timed) ---
     bh = torch.from_numpy(P.b).pin_memory()
@@ -282,6 +287,8 @@ def run_ours(args):
                 "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
                 "launches": mid["launches"], "peak_source": peak_src + " hbm_gbs",
                 "share_of_profiled_time": mid["ms"] / total_ms_prof if total_ms_prof > 0 else None,
+                "profile_pass": {"steps": prof_steps, "ms_per_step": ms_prof / prof_steps,
+                                 "note": "kernel classes timed by CUDA events in separate solves, without graphs"},
                 "classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                                 "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None)}
                             for k, v in prof.items()}}

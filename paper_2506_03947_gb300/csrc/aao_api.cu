@@ -60,6 +60,15 @@ struct aao_ctx {
   int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
   bool tma_used = false;                               // TMA kernel launched since the last fault check
   long long wait_limit = aao::kQuadTmaWaitCycles;      // bound of the TMA waits (aao_set_wait_limit)
+
+  // CUDA graphs of Arnoldi step j (preconditioner, script-A product, Gram-Schmidt, Givens,
+  // read-back of the residual estimate), captured on first use and replayed; dropped when
+  // the tables, the step kernel or the wait limit change.
+  std::vector<cudaGraphExec_t> step_graphs;
+  cudaStream_t gstream = nullptr;  // non-blocking stream the graphs are captured on and run on
+  cudaEvent_t gevent = nullptr;    // orders gstream after the caller's stream
+  std::vector<long long> step_graph_launches;
+  std::vector<char> step_graph_tma;
   double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
   double* sc = nullptr;                                // small scalars, ScLayout
   unsigned* counter = nullptr;                         // last-block ticket of the MGS steps (0 at rest)
@@ -162,7 +171,10 @@ void prof_resolve(aao_ctx* h) {
 // Lemma 2): lambda_m = alpha^{1/ell} exp(-2 pi i m/ell) paired with the forward
 // transform exp(-2 pi i t m/ell); theta_m = (mu_max+mu_min)/2 - lambda_m,
 // delta = (mu_max-mu_min)/2; rho_0 = delta/theta, rho_k = 1/(2 theta/delta - rho_{k-1}).
+void reset_graphs(aao_ctx* h);
+
 void build_tables(aao_ctx* h) {
+  reset_graphs(h);
   using cd = std::complex<double>;
   const int ell = h->ell, F = ell / 2 + 1, p = h->p;
   const double pi = 3.14159265358979323846;
@@ -497,6 +509,91 @@ int orthogonalize(aao_ctx* h, int j, double* w) {
 }
 
 // x_zero: x holds x_0 = 0 on entry, so the first residual is b itself (no script-A product).
+void reset_graphs(aao_ctx* h) {
+  for (cudaGraphExec_t g : h->step_graphs)
+    if (g) cudaGraphExecDestroy(g);
+  h->step_graphs.clear();
+  h->step_graph_launches.clear();
+  h->step_graph_tma.clear();
+}
+
+// Arnoldi step j in stream order; ends with the 16-byte copy of (estimate, h_{j+1,j}) to
+// pinned memory.  Givens reads ||b|| from sc[bnorm] (set at the start of the solve).
+int arnoldi_step_launches(aao_ctx* h, int j) {
+  const ScLayout Lsc{h->m};
+  const int64_t L = h->L;
+  double* Vj = h->V + (int64_t)j * L;
+  double* Zj = h->Z + (int64_t)j * L;
+  double* w = h->V + (int64_t)(j + 1) * L;
+  int rc = precond(h, Vj, h->sc + Lsc.vscale(j), Zj);
+  if (rc) return rc;
+  rc = matvec(h, Zj, nullptr, w, nullptr);
+  if (rc) return rc;
+  rc = orthogonalize(h, j, w);
+  if (rc) return rc;
+  AAO_CK(h, aao::launch_givens(h->sc, j, h->m, -1.0, h->stream));
+  AAO_CK(h, cudaMemcpyAsync(h->pinned, h->sc + Lsc.est(), sizeof(double) * 2, cudaMemcpyDeviceToHost, h->stream));
+  return AAO_OK;
+}
+
+// Run Arnoldi step j (through its CUDA graph unless the event profiler is on) and read back
+// eh = (residual estimate, h_{j+1,j}).
+int arnoldi_step(aao_ctx* h, int j, double* eh) {
+  if (h->prof) {
+    const int rc = arnoldi_step_launches(h, j);
+    if (rc) return rc;
+  } else {
+    // The caller's stream may be the legacy default stream, which cannot be captured: the
+    // step is captured on, and replayed on, the handle's own stream, ordered after the
+    // caller's stream by an event (the host synchronises after every step).
+    if (!h->gstream) AAO_CK(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    if (!h->gevent) AAO_CK(h, cudaEventCreateWithFlags(&h->gevent, cudaEventDisableTiming));
+    AAO_CK(h, cudaEventRecord(h->gevent, h->stream));
+    AAO_CK(h, cudaStreamWaitEvent(h->gstream, h->gevent, 0));
+    if ((int)h->step_graphs.size() <= j) {
+      h->step_graphs.resize(j + 1, nullptr);
+      h->step_graph_launches.resize(j + 1, 0);
+      h->step_graph_tma.resize(j + 1, 0);
+    }
+    if (!h->step_graphs[j]) {
+      const long long c0 = aao::launch_count();
+      const bool tma0 = h->tma_used;
+      h->tma_used = false;
+      AAO_CK(h, cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+      cudaStream_t user = h->stream;
+      h->stream = h->gstream;  // the launchers use the handle's stream
+      const int rc = arnoldi_step_launches(h, j);
+      h->stream = user;
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h->gstream, &graph);
+      const bool tma_in = h->tma_used;
+      h->tma_used = tma0;
+      if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      AAO_CK(h, ec);
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      AAO_CK(h, ei);
+      h->step_graphs[j] = exec;
+      h->step_graph_launches[j] = aao::launch_count() - c0;
+      h->step_graph_tma[j] = tma_in ? 1 : 0;
+      aao::count_launch_add(-h->step_graph_launches[j]);  // captured, not run: counted at each replay
+    }
+    AAO_CK(h, cudaGraphLaunch(h->step_graphs[j], h->gstream));
+    aao::count_launch_add(h->step_graph_launches[j]);
+    if (h->step_graph_tma[j]) h->tma_used = true;
+    AAO_CK(h, cudaStreamSynchronize(h->gstream));
+  }
+  AAO_CK(h, cudaStreamSynchronize(h->stream));
+  eh[0] = h->pinned[0];
+  eh[1] = h->pinned[1];
+  prof_resolve(h);
+  return AAO_OK;
+}
+
 int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer, int fixed, bool x_zero) {
   const ScLayout Lsc{h->m};
   const int64_t L = h->L;
@@ -529,6 +626,8 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
     st.converged = 1;
     return AAO_OK;
   }
+  h->pinned[2] = bnorm;  // for the Givens steps (the stream is idle: read_scalars synchronised)
+  AAO_CK(h, cudaMemcpyAsync(h->sc + Lsc.bnorm(), h->pinned + 2, sizeof(double), cudaMemcpyHostToDevice, s));
   int total = 0;
   const int m = fixed ? fixed : h->m;
   while (true) {
@@ -560,18 +659,8 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
     const double beta = std::sqrt(rn2);
     int k = 0;
     for (int j = 0; j < m && total < max_outer; ++j) {
-      double* Vj = h->V + (int64_t)j * L;
-      double* Zj = h->Z + (int64_t)j * L;
-      double* w = h->V + (int64_t)(j + 1) * L;
-      rc = precond(h, Vj, h->sc + Lsc.vscale(j), Zj);
-      if (rc) return rc;
-      rc = matvec(h, Zj, nullptr, w, nullptr);
-      if (rc) return rc;
-      rc = orthogonalize(h, j, w);
-      if (rc) return rc;
-      AAO_CK(h, aao::launch_givens(h->sc, j, h->m, bnorm, s));
       double eh[2];
-      rc = read_scalars(h, Lsc.est(), 2, eh);
+      rc = arnoldi_step(h, j, eh);
       if (rc) return rc;
       k = j + 1;
       total++;
@@ -818,6 +907,9 @@ void aao_destroy(aao_handle h) {
     if (p) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  reset_graphs(h);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
+  if (h->gevent) cudaEventDestroy(h->gevent);
   delete h;
 }
 
@@ -1131,6 +1223,7 @@ int aao_set_step_kernel(aao_handle h, int kind) {
   if (kind == AAO_STEP_TILE && !h->pairs)
     return fail(h, AAO_EINVAL, "the fused tile kernels need the 2D mixed path with n0 %% 4 == 0");
   h->step_kernel = kind;
+  reset_graphs(h);
   return AAO_OK;
 }
 
@@ -1138,6 +1231,7 @@ int aao_set_wait_limit(aao_handle h, int64_t cycles) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   if (cycles < 0) return fail(h, AAO_EINVAL, "wait limit must be >= 0 SM clocks");
   h->wait_limit = cycles;
+  reset_graphs(h);
   return AAO_OK;
 }
 

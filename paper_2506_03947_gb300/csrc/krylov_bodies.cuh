@@ -350,8 +350,10 @@ __device__ __forceinline__ void reduce_body(const double* __restrict__ partials,
 // Column j of the Hessenberg matrix: H[i][j] = h1[i] + h2[i] (i <= j), H[j+1][j] = sqrt(nrm2);
 // apply the stored rotations, build the new one, update g, and record the
 // relative residual estimate |g[j+1]| / bnorm.  vscale[j+1] = 1/H[j+1][j].
+// bnorm <= 0: ||b|| is read from sc[bnorm()] (so a captured step serves any right-hand side).
 __device__ __forceinline__ void givens_body(double* sc, int j, int m, double bnorm) {
   const ScLayout L{m};
+  if (!(bnorm > 0.0)) bnorm = sc[L.bnorm()];
   for (int i = 0; i <= j; ++i) sc[L.H(i, j)] = sc[L.h1(i)] + sc[L.h2(i)];
   const double hn = sqrt(sc[L.nrm2()]);
   sc[L.hnext()] = hn;
@@ -393,9 +395,30 @@ __device__ __forceinline__ void xupdate_body(int blk, int nblk, const double* __
   for (int q = threadIdx.x; q < k; q += blockDim.x) coef[q] = y[q];
   __syncthreads();
   const int64_t stride = (int64_t)nblk * blockDim.x;
+  const bool vec = ((L | ldz) & 1) == 0 && ((reinterpret_cast<uintptr_t>(Z) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
+  if (vec) {
+    // 16-byte elements, four basis vectors loaded together; the sum runs in the order q = 0 .. k-1
+    for (int64_t e2 = (int64_t)blk * blockDim.x + threadIdx.x; e2 < L / 2; e2 += stride) {
+      double2 v = *reinterpret_cast<const double2*>(x + 2 * e2);
+      int q = 0;
+      for (; q + 4 <= k; q += 4) {
+        const double2 z0 = ld2(Z + (int64_t)q * ldz + 2 * e2), z1 = ld2(Z + (int64_t)(q + 1) * ldz + 2 * e2);
+        const double2 z2 = ld2(Z + (int64_t)(q + 2) * ldz + 2 * e2), z3 = ld2(Z + (int64_t)(q + 3) * ldz + 2 * e2);
+        v.x = fma(coef[q + 3], z3.x, fma(coef[q + 2], z2.x, fma(coef[q + 1], z1.x, fma(coef[q], z0.x, v.x))));
+        v.y = fma(coef[q + 3], z3.y, fma(coef[q + 2], z2.y, fma(coef[q + 1], z1.y, fma(coef[q], z0.y, v.y))));
+      }
+      for (; q < k; ++q) {
+        const double2 z = ld2(Z + (int64_t)q * ldz + 2 * e2);
+        v.x = fma(coef[q], z.x, v.x);
+        v.y = fma(coef[q], z.y, v.y);
+      }
+      *reinterpret_cast<double2*>(x + 2 * e2) = v;
+    }
+    return;
+  }
   for (int64_t e = (int64_t)blk * blockDim.x + threadIdx.x; e < L; e += stride) {
     double v = x[e];
-    for (int q = 0; q < k; ++q) v += coef[q] * __ldg(Z + (int64_t)q * ldz + e);
+    for (int q = 0; q < k; ++q) v = fma(coef[q], __ldg(Z + (int64_t)q * ldz + e), v);
     x[e] = v;
   }
 }
