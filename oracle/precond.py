@@ -81,3 +81,44 @@ def palpha_exact_apply(A_dense: np.ndarray, r: np.ndarray, alpha: float) -> np.n
     for j in range(ell):
         y[j] = np.linalg.solve(A_dense - lam[j] * np.eye(N), v[j])
     return inverse_transform(y, alpha)
+
+
+def neumann_dct_eigenvalues(kappa: Sequence[float], shape) -> np.ndarray:
+    """Eigenvalues of A = I + K for spatially constant face diffusivities, one per axis.
+
+    The finite-volume Neumann operator with constant kappa_a on axis a is a sum of scaled 1D
+    Neumann Laplacians (diagonal 2, ends 1, off-diagonals -1), each diagonalised by the
+    orthonormal DCT-II with eigenvalues 4 sin^2(pi k / (2 n_a)), k = 0..n_a-1; A is
+    diagonalised by their tensor product (the decomposition A = X Phi X^T of Section 2.2).
+    shape = (n2, n1, n0); kappa = (kappa_x, kappa_y, kappa_z); returns Phi with that shape.
+    """
+    n2, n1, n0 = shape
+    ev = [4.0 * np.sin(np.pi * np.arange(n) / (2.0 * n)) ** 2 for n in (n0, n1, n2)]
+    phi = np.ones(shape)
+    phi += kappa[0] * ev[0][None, None, :]
+    phi += kappa[1] * ev[1][None, :, None]
+    phi += kappa[2] * ev[2][:, None, None]
+    return phi
+
+
+def palpha_dct_apply(kappa: Sequence[float], shape, r: np.ndarray, alpha: float) -> np.ndarray:
+    """z = P_alpha^{-1} r exactly, for spatially constant face diffusivities (Section 2.2).
+
+    Eq. 5 with A = X Phi X^T: the shifted solves (A - lambda_j I) y_j = v_j become
+    y_j = X (Phi - lambda_j)^{-1} X^T v_j, X the orthonormal DCT-II along every axis
+    (scipy.fft.dctn / idctn, type 2, norm 'ortho').  This is the paper's best-case
+    preconditioner, applied without a dense factorisation.
+    """
+    from scipy.fft import dctn, idctn
+
+    ell = r.shape[0]
+    lam = scaled_roots(ell, alpha)
+    phi = neumann_dct_eigenvalues(kappa, shape)
+    v = forward_transform(r, alpha)
+    y = np.zeros_like(v)
+    for j in range(ell):
+        vj = v[j].reshape(shape)
+        vh = dctn(vj.real, type=2, norm="ortho") + 1j * dctn(vj.imag, type=2, norm="ortho")
+        yh = vh / (phi - lam[j])
+        y[j] = (idctn(yh.real, type=2, norm="ortho") + 1j * idctn(yh.imag, type=2, norm="ortho")).reshape(-1)
+    return inverse_transform(y, alpha)

@@ -95,3 +95,38 @@ def test_single_cell_degenerate_segment_is_exact():
     for p in (1, 2, 5):
         z = pc.pnc_apply(lambda v: A @ v, r, 0.3, 1.0, 1.0, p)
         np.testing.assert_allclose(z, pc.palpha_exact_apply(A, r, 0.3), atol=1e-13)
+
+
+def _constant_faces(shape, kap):
+    n2, n1, n0 = shape
+    kx = np.full((n2, n1, max(n0 - 1, 0)), kap[0])
+    ky = np.full((n2, max(n1 - 1, 0), n0), kap[1])
+    kz = np.full((max(n2 - 1, 0), n1, n0), kap[2])
+    return kx, ky, kz
+
+
+@pytest.mark.parametrize("shape,kap", [((1, 1, 9), (4.0, 0.0, 0.0)), ((1, 6, 7), (3.0, 2.0, 0.0)),
+                                       ((3, 4, 5), (1.5, 2.5, 0.7))])
+def test_dct_eigenvalues_are_the_spectrum_of_constant_kappa_A(shape, kap):
+    # the closed form of the separable Neumann operator against a dense symmetric eigensolver
+    kx, ky, kz = _constant_faces(shape, kap)
+    ev = np.sort(np.linalg.eigvalsh(op.fv_dense(kx, ky, kz, shape)))
+    phi = np.sort(pc.neumann_dct_eigenvalues(kap, shape).ravel())
+    assert np.abs(ev - phi).max() < 1e-12 * ev.max()
+    assert abs(phi.min() - 1.0) < 1e-15   # mu_min = 1 (the constant mode)
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1e-2])
+@pytest.mark.parametrize("shape,kap", [((1, 6, 7), (3.0, 2.0, 0.0)), ((3, 4, 5), (1.5, 2.5, 0.7))])
+def test_dct_palpha_equals_dense_palpha_and_inverts_palpha(shape, kap, alpha):
+    # best-case P_alpha^{-1} through the spatial DCT equals the dense-solve path of Eq. 5 and
+    # is the inverse of P_alpha (Eq. 2) applied as script-A plus the circulant corner
+    ell = 6
+    kx, ky, kz = _constant_faces(shape, kap)
+    A = op.fv_dense(kx, ky, kz, shape)
+    r = np.random.default_rng(4).standard_normal((ell, A.shape[0]))
+    z_dct = pc.palpha_dct_apply(kap, shape, r, alpha)
+    z_dense = pc.palpha_exact_apply(A, r, alpha)
+    assert np.abs(z_dct - z_dense).max() < 1e-12 * np.abs(z_dense).max()
+    back = aao.p_alpha_apply(lambda v: A @ v, z_dct, alpha)
+    assert np.abs(back - r).max() < 1e-11 * np.abs(r).max()
