@@ -210,6 +210,23 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
 #define AAO_STEP_TMA 2
 int aao_set_step_kernel(aao_handle h, int kind);
 /*
+ * Preconditioner of the outer solve (aao_solve, aao_solve_ci, aao_precond_apply):
+ *   AAO_PRECOND_NC         P_NC, Eq. 5 with Chebyshev inner solves (default);
+ *   AAO_PRECOND_EXACT_DCT  the paper's best-case P_alpha applied exactly (Section 5's
+ *                          comparison), through A = X Phi X^T (Section 2.2): for face
+ *                          diffusivities that are constant along each axis, X is the
+ *                          orthonormal DCT-II along every axis and
+ *                          Phi = 1 + sum_a kappa_a 4 sin^2(pi k_a / (2 n_a)).  The spatial
+ *                          transforms run as batched FP64 GEMMs (cuBLAS); FP64 handles only.
+ * Returns AAO_EINVAL for an unknown mode, a mixed-precision handle, or face diffusivities
+ * that vary along an axis (relative spread > 1e-12).  With the exact mode the statistics count
+ * ell A-products per outer iteration (P_alpha^{-1} uses none).
+ */
+#define AAO_PRECOND_NC 0
+#define AAO_PRECOND_EXACT_DCT 1
+int aao_set_precond_mode(aao_handle h, int mode);
+
+/*
  * Bound, in SM clock cycles, of each wait of the persistent TMA kernel on its
  * copies (no counterpart in the paper).  Default 2e9 (about a second).  A
  * small value makes the waits expire before the copies land: the kernel then

@@ -28,7 +28,10 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
             "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
-            "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit")
+            "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode")
+
+# preconditioner of the outer solve (aao_set_precond_mode)
+AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT = 0, 1
 
 # default bound of the persistent kernel's device-side waits, SM clocks
 DEFAULT_WAIT_CYCLES = 2000000000
@@ -135,6 +138,8 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_get_step_kernel.restype = i32
     lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.aao_set_wait_limit.restype = i32
+    lib.aao_set_precond_mode.argtypes = [vp, i32]
+    lib.aao_set_precond_mode.restype = i32
     _lib = lib
     return lib
 
@@ -263,6 +268,10 @@ def aao_set_step_kernel(h, kind: int) -> int:
     return _check(h, load_library().aao_set_step_kernel(h, int(kind)))
 
 
+def aao_set_precond_mode(h, mode: int) -> int:
+    return _check(h, load_library().aao_set_precond_mode(h, int(mode)))
+
+
 def aao_set_wait_limit(h, cycles: int) -> int:
     return _check(h, load_library().aao_set_wait_limit(h, int(cycles)))
 
@@ -388,6 +397,9 @@ class Solver:
 
     def set_wait_limit(self, cycles):
         return aao_set_wait_limit(self.h, cycles)
+
+    def set_precond_mode(self, mode):
+        return aao_set_precond_mode(self.h, mode)
 
     def profile_enable(self, on=True):
         return aao_profile_enable(self.h, on)

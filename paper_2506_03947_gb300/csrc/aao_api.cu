@@ -64,6 +64,8 @@ struct aao_ctx {
   // CUDA graphs of Arnoldi step j (preconditioner, script-A product, Gram-Schmidt, Givens,
   // read-back of the residual estimate), captured on first use and replayed; dropped when
   // the tables, the step kernel or the wait limit change.
+  int pmode = AAO_PRECOND_NC;     // aao_set_precond_mode
+  aao::DctPlan* dct = nullptr;    // best-case P_alpha (AAO_PRECOND_EXACT_DCT)
   std::vector<cudaGraphExec_t> step_graphs;
   cudaStream_t gstream = nullptr;  // non-blocking stream the graphs are captured on and run on
   cudaEvent_t gevent = nullptr;    // orders gstream after the caller's stream
@@ -417,7 +419,20 @@ int check_tma(aao_ctx* h) {
   return AAO_OK;
 }
 
+// Best-case P_alpha^{-1} (constant diffusivities, FP64): time DFT, then dct_precond.
+int precond_dct(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  AAO_CK(h, aao::launch_dft<double>(h->g, h->dim, h->ell, r, rscale, (double*)h->bhat, h->dft64, h->stream));
+  aao::DctShifts sh{};
+  for (int m = 0; m <= h->ell / 2; ++m) {
+    sh.lam_re[m] = h->steps64[0].lam_re[m];
+    sh.lam_im[m] = h->steps64[0].lam_im[m];
+  }
+  AAO_CK(h, aao::dct_precond(h->dct, h->g, h->ell, (double*)h->bhat, z, sh, h->idft64, h->stream));
+  return AAO_OK;
+}
+
 int precond(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  if (h->pmode == AAO_PRECOND_EXACT_DCT) return precond_dct(h, r, rscale, z);
   if (h->pairs && h->p >= 3) return precond_pairs(h, r, rscale, z);
   if (h->prec == AAO_MIXED)
     return precond_impl<float>(h, r, rscale, z, h->steps32, h->dft32, h->idft32, h->cx32, h->cy32, h->cz32);
@@ -539,7 +554,7 @@ int arnoldi_step_launches(aao_ctx* h, int j) {
 // Run Arnoldi step j (through its CUDA graph unless the event profiler is on) and read back
 // eh = (residual estimate, h_{j+1,j}).
 int arnoldi_step(aao_ctx* h, int j, double* eh) {
-  if (h->prof) {
+  if (h->prof || h->pmode != AAO_PRECOND_NC) {
     const int rc = arnoldi_step_launches(h, j);
     if (rc) return rc;
   } else {
@@ -610,6 +625,7 @@ int solve_impl(aao_ctx* h, const double* b, double* x, double tol, int max_outer
       inner_total += h->palloc[mm];
     }
   }
+  if (h->pmode == AAO_PRECOND_EXACT_DCT) inner_total = 0;  // no products with A inside the exact P_alpha
   const int64_t per_outer = inner_total + h->ell;
 
   // ||b||
@@ -908,6 +924,7 @@ void aao_destroy(aao_handle h) {
   if (h->pinned) cudaFreeHost(h->pinned);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   reset_graphs(h);
+  if (h->dct) aao::dct_plan_destroy(h->dct);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gevent) cudaEventDestroy(h->gevent);
   delete h;
@@ -1223,6 +1240,34 @@ int aao_set_step_kernel(aao_handle h, int kind) {
   if (kind == AAO_STEP_TILE && !h->pairs)
     return fail(h, AAO_EINVAL, "the fused tile kernels need the 2D mixed path with n0 %% 4 == 0");
   h->step_kernel = kind;
+  reset_graphs(h);
+  return AAO_OK;
+}
+
+int aao_set_precond_mode(aao_handle h, int mode) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (mode == AAO_PRECOND_NC) {
+    h->pmode = mode;
+    reset_graphs(h);
+    return AAO_OK;
+  }
+  if (mode != AAO_PRECOND_EXACT_DCT) return fail(h, AAO_EINVAL, "unknown preconditioner mode %d", mode);
+  if (h->prec != AAO_FP64) return fail(h, AAO_EINVAL, "the best-case P_alpha is applied in FP64: create the handle with AAO_FP64");
+  if (!h->dct) {
+    double mm[6] = {0, 0, 0, 0, 0, 0};
+    AAO_CK(h, aao::face_ranges(h->g, h->cx64, h->dim >= 2 ? h->cy64 : nullptr, h->dim == 3 ? h->cz64 : nullptr, mm,
+                               h->stream));
+    double kap[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < h->dim; ++a) {
+      const double lo = mm[2 * a], hi = mm[2 * a + 1];
+      if (hi > 0.0 && !(hi - lo <= 1e-12 * hi))
+        return fail(h, AAO_EINVAL, "the best-case P_alpha needs one diffusivity per axis (axis %d has %.17g .. %.17g)",
+                    a, lo, hi);
+      kap[a] = hi;
+    }
+    AAO_CK(h, aao::dct_plan_create(&h->dct, h->g, h->dim, h->ell, kap));
+  }
+  h->pmode = mode;
   reset_graphs(h);
   return AAO_OK;
 }

@@ -121,6 +121,22 @@ cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap
 // shared-memory base (bit 1); synchronises s.
 cudaError_t quad_tma_fault(unsigned* flag, cudaStream_t s);
 
+// Best-case P_alpha^{-1} for spatially constant diffusivities (dct.cu): spatial DCT-II of the
+// frequency planes, division by (phi - lambda_m), inverse DCT, inverse time DFT (Section 2.2).
+struct DctShifts {
+  double lam_re[kMaxF], lam_im[kMaxF];
+};
+struct DctPlan;
+// kappa[a]: the (constant) face diffusivity of axis a (0 for a missing axis).
+cudaError_t dct_plan_create(DctPlan** out, const GridDesc& g, int dim, int ell, const double kappa[3]);
+void dct_plan_destroy(DctPlan* p);
+// vhat: the ell packed frequency planes of the time DFT (overwritten); z: ell planes of N.
+cudaError_t dct_precond(DctPlan* p, const GridDesc& g, int ell, double* vhat, double* z, const DctShifts& sh,
+                        const IdftArgs<double>& ia, cudaStream_t s);
+// Per-axis (min, max) of the interior faces of cx, cy, cz (cy/cz may be null); synchronises s.
+cudaError_t face_ranges(const GridDesc& g, const double* cx, const double* cy, const double* cz, double out[6],
+                        cudaStream_t s);
+
 // FP64 Krylov kernels (krylov.cu).
 // y = script-A x (mode 0) or y = b - script-A x with per-block partial sums of y^2 (mode 1).
 cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,
