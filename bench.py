@@ -72,11 +72,22 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the headline four-step kernel's source: its translation unit and the shared
+    definitions it compiles against (grid descriptor, step tables, tile constants, TMA map)."""
+    import re
+    csrc = os.path.join(ROOT, "paper_2506_03947_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("cheb_kernels.cuh", "cheb_v4.cuh", "cheb_pair.cuh", "cheb_quad.cuh", "cheb_quad_tma.cu",
-              "aao_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2506_03947_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "cheb_quad_tma.cu"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "aao_internal.cuh")) as fh:
+        hdr = fh.read()
+    pats = [r"struct GridDesc \{.*?\};", r"struct StepArgs \{.*?\};", r"struct QuadSteps \{.*?\};",
+            r"struct alignas\(64\) FieldMap \{.*?\};", r"constexpr int kQuadTmaTY = \d+;",
+            r"constexpr int kQuadTmaR = \d+;", r"constexpr long long kQuadTmaWaitCycles = [^;]*;",
+            r"constexpr int kMaxEll = \d+;"]
+    for pat in pats:
+        m = re.search(pat, hdr, re.S)
+        h.update((m.group(0) if m else pat).encode())
     return h.hexdigest()[:16]
 
 
@@ -299,6 +310,9 @@ def run_ours(args):
     rhs3d = None
     if not args.no_rhs3d:
         rhs3d = run_rhs3d_leg(args, binding, torch, sptr, peak)
+    best = None
+    if not args.no_best_case:
+        best = run_best_case_leg(args, binding, torch, sptr)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -317,7 +331,7 @@ def run_ours(args):
         "a_matvecs": st32["a_matvecs"], "wall_ms_per_step": wall * 1e3 / args.steps,
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * L, "d2h_bytes_per_step": 8 * L},
-        "gpu_launches": launches, "clocks": clocks, "fp64_gpu": fp64, "batch": batch, "rhs3d": rhs3d,
+        "gpu_launches": launches, "clocks": clocks, "fp64_gpu": fp64, "batch": batch, "rhs3d": rhs3d, "best_case": best,
         "step_wall_ms": [round(w * 1e3, 3) for w in walls32],
     }
     if rank == 0:
@@ -415,6 +429,54 @@ def run_rhs3d_leg(args, binding, torch, sptr, peak):
             "sweep_bytes_per_cell": 16 * P.ell + 12,
             "share": {k: round(v["ms"] / total, 3) for k, v in prof.items() if v["ms"] > 0},
             "timing": "CUDA events around 8 device-resident solves after one warm-up solve"}
+
+
+def run_best_case_leg(args, binding, torch, sptr):
+    """Outer iterations of P_NC against the paper's best-case P_alpha (applied exactly through the
+    spatial DCT, FP64) on a constant-diffusivity grid (kappa = 50/ell on every face), 256^2,
+    ell = 10, tol 1e-8, over alpha; plus the time of one best-case solve at 1024^2."""
+    import numpy as np
+    from paper_2506_03947_gb300 import inputs
+    rows = []
+    for alpha in (1e-1, 1e-2, 1e-3, 1e-4):
+        P = inputs.make_problem("const256", 2, (256, 256), 10, alpha, 1, 0.0, (16.0, 16.0), 41, 42)
+        kx = torch.from_numpy(P.kx.ravel()).cuda()
+        ky = torch.from_numpy(P.ky.ravel()).cuda()
+        b = torch.from_numpy(P.b).cuda()
+        row = {"alpha": alpha}
+        for name, prec, p, exact in (("best_case", binding.AAO_FP64, 1, True), ("nc_p40", binding.AAO_MIXED, 40, False),
+                                     ("nc_p10", binding.AAO_MIXED, 10, False)):
+            s = binding.Solver(2, P.n, kx, ky, None, P.ell, alpha, prec=prec, inner_its=p, restart=64, stream=sptr)
+            if exact:
+                s.set_precond_mode(binding.AAO_PRECOND_EXACT_DCT)
+            x = torch.zeros_like(b)
+            s.solve(b, x, 1e-8, 64, allow_notconv=True)
+            row[name] = s.stats()["outer_its"]
+            s.close()
+        rows.append(row)
+    P = inputs.make_problem("const1024", 2, (1024, 1024), 10, 1e-2, 1, 0.0, (16.0, 16.0), 21, 22)
+    kx = torch.from_numpy(P.kx.ravel()).cuda()
+    ky = torch.from_numpy(P.ky.ravel()).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    s = binding.Solver(2, P.n, kx, ky, None, P.ell, P.alpha, prec=binding.AAO_FP64, inner_its=1, restart=64,
+                       stream=sptr)
+    s.set_precond_mode(binding.AAO_PRECOND_EXACT_DCT)
+    x = torch.zeros_like(b)
+    s.solve(b, x, 1e-8, 64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    x.zero_()
+    e0.record(torch.cuda.current_stream())
+    s.solve(b, x, 1e-8, 64)
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    its1024 = s.stats()["outer_its"]
+    s.close()
+    return {"workload": "2d_const_256x256_l10 (kappa 5), tol 1e-8; outer iterations",
+            "alpha_sweep": rows,
+            "best_case_1024": {"alpha": 1e-2, "outer_its": its1024, "ms_per_solve": e0.elapsed_time(e1),
+                               "note": "FP64, spatial DCT as batched cuBLAS DGEMMs"}}
 
 
 def run_ncu_case(args):
@@ -523,6 +585,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance workload")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-rhs3d", action="store_true", help="skip the 3D 128^3 eight-right-hand-side workload")
+    ap.add_argument("--no-best-case", action="store_true", help="skip the best-case (exact P_alpha) comparison")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run only preconditioner applies (small device footprint) for ncu captures")
     ap.add_argument("--ncu-fp64", action="store_true", help="with --ncu-case: FP64 path")
