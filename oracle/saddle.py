@@ -1,0 +1,242 @@
+"""P_SP: the saddle-point reformulation of the shifted solves (Section 4), oracle.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Eq. 5 needs y_j = (A - lambda_j I)^{-1} v_j for every frequency.  Section 4 solves them in
+real arithmetic with a fixed number K of Krylov iterations each:
+  * real shifts (j = 0 and j = ell/2): preconditioned CG on A - lambda_j I;
+  * complex shifts: the real system of twice the size (the saddle-point system of Section 4)
+        S = [[Phi, Psi], [Psi, -Phi]],  Phi = Im(lambda) I,  Psi = A - Re(lambda) I,
+        S [Re x; -Im x] = [-Im b; Re b],
+    by MINRES with the block-diagonal preconditioner P_D = diag(Phi + Psi, Phi + Psi)
+    (Section 4's theorem: the spectrum of P_D^{-1} S lies in [-1, -1/sqrt 2] u [1/sqrt 2, 1]).
+    Phi must be positive definite, so a shift with Im(lambda) < 0 is solved through its
+    conjugate: (A - lambda) x = b  <=>  (A - conj lambda) conj x = conj b.
+The paper applies the SPD blocks approximately with one V-cycle of an algebraic multigrid
+(HSL_MI20).  This build uses its own multigrid for the same operators, defined here and run
+identically on the GPU:
+  * levels: pairwise aggregation of the structured grid (2 x 2 cells, ceil(n/2) per axis), the
+    coarse operator being the Galerkin product R B P with piecewise-constant P and R = P^T.
+    For B = (1 + c) I + K this keeps the form B_H = (1 + c) W_H + K_H: W_H sums the cells of an
+    aggregate and each coarse face sums the fine face diffusivities crossing it;
+  * smoother: weighted Jacobi, omega = 2/3, NU sweeps before and after the coarse correction
+    (a symmetric V-cycle, so it is an SPD preconditioner for CG and MINRES);
+  * coarsest level (both sides <= 4 cells): NU_COARSE Jacobi sweeps from zero.
+Grids are 1D or 2D (n2 = 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List
+
+import numpy as np
+
+from .precond import forward_transform, inverse_transform
+from .spectral import scaled_roots
+
+OMEGA = 2.0 / 3.0
+NU = 2
+NU_COARSE = 16
+COARSEST = 4
+
+
+@dataclass
+class Level:
+    w: np.ndarray    # (n1, n0) cell weights (1 on the finest level)
+    kx: np.ndarray   # (n1, n0 - 1) face diffusivities along x
+    ky: np.ndarray   # (n1 - 1, n0) face diffusivities along y
+
+
+def hierarchy(kx: np.ndarray, ky: np.ndarray, shape) -> List[Level]:
+    """Aggregation levels for a 1D/2D grid; kx, ky in the (n2, n1, n0-1) / (n2, n1-1, n0) layout."""
+    n2, n1, n0 = shape
+    if n2 != 1:
+        raise ValueError("P_SP's multigrid is defined for 1D and 2D grids")
+    lv = [Level(np.ones((n1, n0)), kx[0].astype(float).copy(), ky[0].astype(float).copy())]
+    while lv[-1].w.shape[0] > COARSEST or lv[-1].w.shape[1] > COARSEST:
+        f = lv[-1]
+        m1, m0 = f.w.shape
+        c1, c0 = (m1 + 1) // 2, (m0 + 1) // 2
+        w = np.zeros((c1, c0))
+        for j in range(m1):
+            for i in range(m0):
+                w[j // 2, i // 2] += f.w[j, i]
+        kxc = np.zeros((c1, max(c0 - 1, 0)))
+        for j in range(m1):
+            for ic in range(c0 - 1):
+                kxc[j // 2, ic] += f.kx[j, 2 * ic + 1]    # fine face between 2ic+1 and 2ic+2
+        kyc = np.zeros((max(c1 - 1, 0), c0))
+        for jc in range(c1 - 1):
+            for i in range(m0):
+                kyc[jc, i // 2] += f.ky[2 * jc + 1, i]
+        lv.append(Level(w, kxc, kyc))
+    return lv
+
+
+def level_apply(L: Level, c: float, x: np.ndarray) -> np.ndarray:
+    """B x = (1 + c) W x + K x on one level (x of shape (n1, n0))."""
+    y = (1.0 + c) * L.w * x
+    if L.kx.size:
+        f = L.kx * (x[:, 1:] - x[:, :-1])
+        y[:, :-1] -= f
+        y[:, 1:] += f
+    if L.ky.size:
+        f = L.ky * (x[1:, :] - x[:-1, :])
+        y[:-1, :] -= f
+        y[1:, :] += f
+    return y
+
+
+def level_diag(L: Level, c: float) -> np.ndarray:
+    d = (1.0 + c) * L.w.copy()
+    if L.kx.size:
+        d[:, :-1] += L.kx
+        d[:, 1:] += L.kx
+    if L.ky.size:
+        d[:-1, :] += L.ky
+        d[1:, :] += L.ky
+    return d
+
+
+def jacobi(L: Level, c: float, b: np.ndarray, x: np.ndarray, sweeps: int) -> np.ndarray:
+    d = level_diag(L, c)
+    for _ in range(sweeps):
+        x = x + OMEGA * (b - level_apply(L, c, x)) / d
+    return x
+
+
+def restrict(b: np.ndarray, coarse_shape) -> np.ndarray:
+    r = np.zeros(coarse_shape)
+    m1, m0 = b.shape
+    for j in range(m1):
+        for i in range(m0):
+            r[j // 2, i // 2] += b[j, i]
+    return r
+
+
+def prolong(xc: np.ndarray, fine_shape) -> np.ndarray:
+    m1, m0 = fine_shape
+    return xc[np.arange(m1)[:, None] // 2, np.arange(m0)[None, :] // 2]
+
+
+def vcycle(levels: List[Level], c: float, b: np.ndarray, q: int = 0) -> np.ndarray:
+    """One symmetric V-cycle for B = (1 + c) I + K from level q, zero initial guess."""
+    L = levels[q]
+    x = np.zeros_like(b)
+    if q == len(levels) - 1:
+        return jacobi(L, c, b, x, NU_COARSE)
+    x = jacobi(L, c, b, x, NU)
+    r = b - level_apply(L, c, x)
+    xc = vcycle(levels, c, restrict(r, levels[q + 1].w.shape), q + 1)
+    x = x + prolong(xc, L.w.shape)
+    return jacobi(L, c, b, x, NU)
+
+
+def pcg(levels: List[Level], c: float, b: np.ndarray, iters: int) -> np.ndarray:
+    """iters steps of CG on B = (1 + c) I + K preconditioned by one V-cycle, x_0 = 0."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = vcycle(levels, c, r)
+    p = z.copy()
+    rz = float(np.vdot(r, z))
+    for k in range(iters):
+        if rz == 0.0:
+            break
+        q = level_apply(levels[0], c, p)
+        a = rz / float(np.vdot(p, q))
+        x = x + a * p
+        r = r - a * q
+        if k == iters - 1:
+            break
+        z = vcycle(levels, c, r)
+        rz_new = float(np.vdot(r, z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x
+
+
+def saddle_apply(levels: List[Level], lam: complex, u: np.ndarray, v: np.ndarray):
+    """S [u; v] with Phi = Im(lam) I, Psi = A - Re(lam) I."""
+    phi = lam.imag
+    pu = level_apply(levels[0], -lam.real, u)
+    pv = level_apply(levels[0], -lam.real, v)
+    return phi * u + pv, pu - phi * v
+
+
+def minres(levels: List[Level], lam: complex, fu: np.ndarray, fv: np.ndarray, iters: int):
+    """iters steps of preconditioned MINRES on S [u; v] = [fu; fv] from zero, preconditioner
+    P_D = diag(B, B) applied by one V-cycle per block, B = Phi + Psi = (1 + c) I + K with
+    c = Im(lam) - Re(lam).  Lanczos process in the P_D^{-1} inner product, QR of the
+    tridiagonal by Givens rotations, and the short solution recurrence (Paige and Saunders)."""
+    c_pd = lam.imag - lam.real
+
+    def prec(a, b):
+        return vcycle(levels, c_pd, a), vcycle(levels, c_pd, b)
+
+    xu, xv = np.zeros_like(fu), np.zeros_like(fv)
+    vu_old, vv_old = np.zeros_like(fu), np.zeros_like(fv)
+    vu, vv = fu.copy(), fv.copy()
+    zu, zv = prec(vu, vv)
+    gamma = np.sqrt(float(np.vdot(zu, vu) + np.vdot(zv, vv)))
+    gamma_old = 1.0
+    eta = gamma
+    s_old = s = 0.0
+    c_old = c = 1.0
+    wu_old, wv_old = np.zeros_like(fu), np.zeros_like(fv)
+    wu, wv = np.zeros_like(fu), np.zeros_like(fv)
+    for _ in range(iters):
+        if gamma == 0.0:
+            break
+        zu, zv = zu / gamma, zv / gamma
+        su, sv = saddle_apply(levels, lam, zu, zv)
+        delta = float(np.vdot(su, zu) + np.vdot(sv, zv))
+        nu_ = su - (delta / gamma) * vu - (gamma / gamma_old) * vu_old
+        nv_ = sv - (delta / gamma) * vv - (gamma / gamma_old) * vv_old
+        zu_n, zv_n = prec(nu_, nv_)
+        gamma_n = np.sqrt(max(float(np.vdot(zu_n, nu_) + np.vdot(zv_n, nv_)), 0.0))
+        a0 = c * delta - c_old * s * gamma
+        a1 = np.hypot(a0, gamma_n)
+        a2 = s * delta + c_old * c * gamma
+        a3 = s_old * gamma
+        c_n, s_n = a0 / a1, gamma_n / a1
+        wu_n = (zu - a3 * wu_old - a2 * wu) / a1
+        wv_n = (zv - a3 * wv_old - a2 * wv) / a1
+        xu = xu + c_n * eta * wu_n
+        xv = xv + c_n * eta * wv_n
+        eta = -s_n * eta
+        vu_old, vv_old, vu, vv = vu, vv, nu_, nv_
+        zu, zv = zu_n, zv_n
+        gamma_old, gamma = gamma, gamma_n
+        wu_old, wv_old, wu, wv = wu, wv, wu_n, wv_n
+        c_old, c, s_old, s = c, c_n, s, s_n
+    return xu, xv
+
+
+def shifted_solve(levels: List[Level], lam: complex, b: np.ndarray, iters: int, real: bool) -> np.ndarray:
+    """Approximate (A - lam I)^{-1} b for one frequency (b complex of shape (n1, n0));
+    real: the shift is real (frequencies 0 and ell/2), solved by CG."""
+    if real:
+        xr = pcg(levels, -lam.real, b.real.copy(), iters)
+        xi = pcg(levels, -lam.real, b.imag.copy(), iters) if np.any(b.imag) else np.zeros_like(xr)
+        return xr + 1j * xi
+    conj = lam.imag < 0.0
+    lp = np.conj(lam) if conj else lam
+    bp = np.conj(b) if conj else b
+    u, v = minres(levels, lp, -bp.imag.copy(), bp.real.copy(), iters)   # [Re x; -Im x]
+    x = u - 1j * v
+    return np.conj(x) if conj else x
+
+
+def psp_apply(kx, ky, shape, r: np.ndarray, alpha: float, iters: int) -> np.ndarray:
+    """z = P_SP^{-1} r: Eq. 5 with every shifted solve replaced by iters Krylov steps (Section 4)."""
+    ell = r.shape[0]
+    levels = hierarchy(kx, ky, shape)
+    n2, n1, n0 = shape
+    lam = scaled_roots(ell, alpha)
+    v = forward_transform(r, alpha)
+    y = np.zeros_like(v)
+    for j in range(ell):
+        real = (j == 0) or (2 * j == ell)
+        lj = complex(lam[j].real, 0.0) if real else complex(lam[j])
+        y[j] = shifted_solve(levels, lj, v[j].reshape(n1, n0), iters, real).reshape(-1)
+    return inverse_transform(y, alpha)
