@@ -218,12 +218,22 @@ int aao_set_step_kernel(aao_handle h, int kind);
  *                          orthonormal DCT-II along every axis and
  *                          Phi = 1 + sum_a kappa_a 4 sin^2(pi k_a / (2 n_a)).  The spatial
  *                          transforms run as batched FP64 GEMMs (cuBLAS); FP64 handles only.
- * Returns AAO_EINVAL for an unknown mode, a mixed-precision handle, or face diffusivities
- * that vary along an axis (relative spread > 1e-12).  With the exact mode the statistics count
- * ell A-products per outer iteration (P_alpha^{-1} uses none).
+ *   AAO_PRECOND_SP         P_SP (Section 4): the real shifts (frequencies 0 and ell/2) by
+ *                          p steps of CG on A - lambda I, each complex shift by p steps of
+ *                          MINRES on the saddle-point system of twice the size with the
+ *                          block-diagonal preconditioner P_D (Section 4's theorem); the SPD
+ *                          blocks are applied by one V-cycle of this library's aggregation
+ *                          multigrid (the paper uses an algebraic multigrid, HSL_MI20).
+ *                          p = the handle's inner_its.  FP64 handles, 1D and 2D grids.
+ * Returns AAO_EINVAL for an unknown mode, a mixed-precision handle, face diffusivities that
+ * vary along an axis (exact mode, relative spread > 1e-12) or a 3D grid (P_SP).  With the
+ * exact mode the statistics count ell A-products per outer iteration (P_alpha^{-1} uses none);
+ * with P_SP, ell + ell p (CG: one product per step on two real shifts; MINRES: two per step on
+ * the ell/2 - 1 complex shifts that conjugate symmetry leaves).
  */
 #define AAO_PRECOND_NC 0
 #define AAO_PRECOND_EXACT_DCT 1
+#define AAO_PRECOND_SP 2
 int aao_set_precond_mode(aao_handle h, int mode);
 
 /*

@@ -57,18 +57,16 @@ def hierarchy(kx: np.ndarray, ky: np.ndarray, shape) -> List[Level]:
         f = lv[-1]
         m1, m0 = f.w.shape
         c1, c0 = (m1 + 1) // 2, (m0 + 1) // 2
+        jj, ii = np.meshgrid(np.arange(m1), np.arange(m0), indexing="ij")
         w = np.zeros((c1, c0))
-        for j in range(m1):
-            for i in range(m0):
-                w[j // 2, i // 2] += f.w[j, i]
+        np.add.at(w, (jj // 2, ii // 2), f.w)                       # cells of each aggregate
         kxc = np.zeros((c1, max(c0 - 1, 0)))
-        for j in range(m1):
-            for ic in range(c0 - 1):
-                kxc[j // 2, ic] += f.kx[j, 2 * ic + 1]    # fine face between 2ic+1 and 2ic+2
+        if c0 > 1:
+            # fine faces between columns 2ic+1 and 2ic+2 cross from aggregate ic to ic+1
+            np.add.at(kxc, (np.arange(m1)[:, None] // 2, np.arange(c0 - 1)[None, :]), f.kx[:, 1:2 * c0 - 2:2])
         kyc = np.zeros((max(c1 - 1, 0), c0))
-        for jc in range(c1 - 1):
-            for i in range(m0):
-                kyc[jc, i // 2] += f.ky[2 * jc + 1, i]
+        if c1 > 1:
+            np.add.at(kyc, (np.arange(c1 - 1)[:, None], np.arange(m0)[None, :] // 2), f.ky[1:2 * c1 - 2:2, :])
         lv.append(Level(w, kxc, kyc))
     return lv
 
@@ -106,11 +104,10 @@ def jacobi(L: Level, c: float, b: np.ndarray, x: np.ndarray, sweeps: int) -> np.
 
 
 def restrict(b: np.ndarray, coarse_shape) -> np.ndarray:
+    """Sum of b over each 2 x 2 aggregate (R = P^T)."""
     r = np.zeros(coarse_shape)
     m1, m0 = b.shape
-    for j in range(m1):
-        for i in range(m0):
-            r[j // 2, i // 2] += b[j, i]
+    np.add.at(r, (np.arange(m1)[:, None] // 2, np.arange(m0)[None, :] // 2), b)
     return r
 
 

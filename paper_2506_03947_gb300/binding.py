@@ -31,7 +31,7 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode")
 
 # preconditioner of the outer solve (aao_set_precond_mode)
-AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT = 0, 1
+AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT, AAO_PRECOND_SP = 0, 1, 2
 
 # default bound of the persistent kernel's device-side waits, SM clocks
 DEFAULT_WAIT_CYCLES = 2000000000

@@ -66,6 +66,7 @@ struct aao_ctx {
   // the tables, the step kernel or the wait limit change.
   int pmode = AAO_PRECOND_NC;     // aao_set_precond_mode
   aao::DctPlan* dct = nullptr;    // best-case P_alpha (AAO_PRECOND_EXACT_DCT)
+  aao::SpPlan* sp = nullptr;      // P_SP (AAO_PRECOND_SP)
   std::vector<cudaGraphExec_t> step_graphs;
   cudaStream_t gstream = nullptr;  // non-blocking stream the graphs are captured on and run on
   cudaEvent_t gevent = nullptr;    // orders gstream after the caller's stream
@@ -431,8 +432,22 @@ int precond_dct(aao_ctx* h, const double* r, const double* rscale, double* z) {
   return AAO_OK;
 }
 
+// P_SP^{-1} (Section 4): time DFT, then the fixed-iteration real Krylov solves (sp_precond).
+int precond_sp(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  AAO_CK(h, aao::launch_dft<double>(h->g, h->dim, h->ell, r, rscale, (double*)h->bhat, h->dft64, h->stream));
+  aao::DctShifts sh{};
+  for (int m = 0; m <= h->ell / 2; ++m) {
+    sh.lam_re[m] = h->steps64[0].lam_re[m];
+    sh.lam_im[m] = h->steps64[0].lam_im[m];
+  }
+  AAO_CK(h, aao::sp_precond(h->sp, h->g, h->ell, h->p, (double*)h->bhat, (double*)h->xa, z, sh, h->idft64,
+                            h->stream));
+  return AAO_OK;
+}
+
 int precond(aao_ctx* h, const double* r, const double* rscale, double* z) {
   if (h->pmode == AAO_PRECOND_EXACT_DCT) return precond_dct(h, r, rscale, z);
+  if (h->pmode == AAO_PRECOND_SP) return precond_sp(h, r, rscale, z);
   if (h->pairs && h->p >= 3) return precond_pairs(h, r, rscale, z);
   if (h->prec == AAO_MIXED)
     return precond_impl<float>(h, r, rscale, z, h->steps32, h->dft32, h->idft32, h->cx32, h->cy32, h->cz32);
@@ -925,6 +940,7 @@ void aao_destroy(aao_handle h) {
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   reset_graphs(h);
   if (h->dct) aao::dct_plan_destroy(h->dct);
+  if (h->sp) aao::sp_plan_destroy(h->sp);
   if (h->gstream) cudaStreamDestroy(h->gstream);
   if (h->gevent) cudaEventDestroy(h->gevent);
   delete h;
@@ -1247,6 +1263,14 @@ int aao_set_step_kernel(aao_handle h, int kind) {
 int aao_set_precond_mode(aao_handle h, int mode) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   if (mode == AAO_PRECOND_NC) {
+    h->pmode = mode;
+    reset_graphs(h);
+    return AAO_OK;
+  }
+  if (mode == AAO_PRECOND_SP) {
+    if (h->prec != AAO_FP64) return fail(h, AAO_EINVAL, "P_SP is applied in FP64: create the handle with AAO_FP64");
+    if (h->dim > 2) return fail(h, AAO_EINVAL, "P_SP's multigrid is built for 1D and 2D grids");
+    if (!h->sp) AAO_CK(h, aao::sp_plan_create(&h->sp, h->g, h->dim, h->cx64, h->cy64, h->stream));
     h->pmode = mode;
     reset_graphs(h);
     return AAO_OK;

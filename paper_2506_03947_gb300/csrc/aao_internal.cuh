@@ -137,6 +137,22 @@ cudaError_t dct_precond(DctPlan* p, const GridDesc& g, int ell, double* vhat, do
 cudaError_t face_ranges(const GridDesc& g, const double* cx, const double* cy, const double* cz, double out[6],
                         cudaStream_t s);
 
+// Inverse time DFT of ell packed frequency planes y into z (ell planes), with Gamma^{-1}.
+cudaError_t launch_idft_planes(int64_t N, int ell, const double* y, double* z, const IdftArgs<double>& ia,
+                               cudaStream_t s);
+
+// P_SP (saddle.cu): fixed-iteration PCG on the real shifts and block-diagonally preconditioned
+// MINRES on the saddle-point systems of the complex ones, with one aggregation-multigrid
+// V-cycle per preconditioner block (Section 4).  1D/2D, FP64.
+struct SpPlan;
+cudaError_t sp_plan_create(SpPlan** out, const GridDesc& g, int dim, const double* cx, const double* cy,
+                           cudaStream_t s);
+void sp_plan_destroy(SpPlan* p);
+// vhat: packed frequency planes of the time DFT; y: ell planes of work space; z: result.
+cudaError_t sp_precond(SpPlan* p, const GridDesc& g, int ell, int iters, double* vhat, double* y, double* z,
+                       const DctShifts& sh, const IdftArgs<double>& ia, cudaStream_t s);
+long long sp_last_products(const SpPlan* p);
+
 // FP64 Krylov kernels (krylov.cu).
 // y = script-A x (mode 0) or y = b - script-A x with per-block partial sums of y^2 (mode 1).
 cudaError_t launch_aao_matvec(const GridDesc& g, int dim, int ell, const double* cx, const double* cy,

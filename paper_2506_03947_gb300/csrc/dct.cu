@@ -180,6 +180,13 @@ cudaError_t dct_precond(DctPlan* p, const GridDesc& g, int ell, double* vhat, do
   return cudaGetLastError();
 }
 
+cudaError_t launch_idft_planes(int64_t N, int ell, const double* y, double* z, const IdftArgs<double>& ia,
+                               cudaStream_t s) {
+  k_idft_planes<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, ell, y, z, ia);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Per-axis minimum and maximum of the interior faces (as ordered bit patterns of positive
 // doubles); slots 2a, 2a+1 of mm hold min and max of axis a.
 __global__ void k_face_range(GridDesc g, const double* __restrict__ cx, const double* __restrict__ cy,
