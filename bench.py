@@ -432,9 +432,10 @@ def run_rhs3d_leg(args, binding, torch, sptr, peak):
 
 
 def run_best_case_leg(args, binding, torch, sptr):
-    """Outer iterations of P_NC against the paper's best-case P_alpha (applied exactly through the
-    spatial DCT, FP64) on a constant-diffusivity grid (kappa = 50/ell on every face), 256^2,
-    ell = 10, tol 1e-8, over alpha; plus the time of one best-case solve at 1024^2."""
+    """Outer iterations of P_NC (p = 40, 10) and P_SP (10 Krylov steps per shifted solve) against
+    the paper's best-case P_alpha (applied exactly through the spatial DCT, FP64) on a
+    constant-diffusivity grid (kappa = 50/ell on every face), 256^2, ell = 10, tol 1e-8, over
+    alpha; plus the time of one best-case solve at 1024^2."""
     import numpy as np
     from paper_2506_03947_gb300 import inputs
     rows = []
@@ -444,11 +445,13 @@ def run_best_case_leg(args, binding, torch, sptr):
         ky = torch.from_numpy(P.ky.ravel()).cuda()
         b = torch.from_numpy(P.b).cuda()
         row = {"alpha": alpha}
-        for name, prec, p, exact in (("best_case", binding.AAO_FP64, 1, True), ("nc_p40", binding.AAO_MIXED, 40, False),
-                                     ("nc_p10", binding.AAO_MIXED, 10, False)):
+        for name, prec, p, mode in (("best_case", binding.AAO_FP64, 1, binding.AAO_PRECOND_EXACT_DCT),
+                                    ("nc_p40", binding.AAO_MIXED, 40, binding.AAO_PRECOND_NC),
+                                    ("nc_p10", binding.AAO_MIXED, 10, binding.AAO_PRECOND_NC),
+                                    ("sp_k10", binding.AAO_FP64, 10, binding.AAO_PRECOND_SP)):
             s = binding.Solver(2, P.n, kx, ky, None, P.ell, alpha, prec=prec, inner_its=p, restart=64, stream=sptr)
-            if exact:
-                s.set_precond_mode(binding.AAO_PRECOND_EXACT_DCT)
+            if mode != binding.AAO_PRECOND_NC:
+                s.set_precond_mode(mode)
             x = torch.zeros_like(b)
             s.solve(b, x, 1e-8, 64, allow_notconv=True)
             row[name] = s.stats()["outer_its"]
