@@ -313,6 +313,9 @@ def run_ours(args):
     best = None
     if not args.no_best_case:
         best = run_best_case_leg(args, binding, torch, sptr)
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep_leg(args, binding, torch, sptr)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -332,7 +335,7 @@ def run_ours(args):
         "roofline": roofline, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * L, "d2h_bytes_per_step": 8 * L},
         "gpu_launches": launches, "clocks": clocks, "fp64_gpu": fp64, "batch": batch, "rhs3d": rhs3d, "best_case": best,
-        "step_wall_ms": [round(w * 1e3, 3) for w in walls32],
+        "sweep": sweep, "step_wall_ms": [round(w * 1e3, 3) for w in walls32],
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -482,6 +485,45 @@ def run_best_case_leg(args, binding, torch, sptr):
                                "note": "FP64, spatial DCT as batched cuBLAS DGEMMs"}}
 
 
+def run_sweep_leg(args, binding, torch, sptr):
+    """Outer iterations and time per solve, mixed and FP64, tol 1e-8, restart 64: over alpha in
+    {1e-1, 1e-2, 1e-3} and p in {10, 20, 40} on the lognormal 256^2 grid (sigma 0.5, correlation
+    length 16, seeds 11/12, L2-resident), and at p = 10 on the 1024^2 grid of the main workload.
+    Each solve runs once untimed (graph capture), then once timed by CUDA events."""
+    from paper_2506_03947_gb300 import inputs
+
+    def timed(P, prec, p):
+        kx = torch.from_numpy(P.kx.ravel()).cuda()
+        ky = torch.from_numpy(P.ky.ravel()).cuda()
+        b = torch.from_numpy(P.b).cuda()
+        s = binding.Solver(2, P.n, kx, ky, None, P.ell, P.alpha, prec=prec, inner_its=p, restart=64, stream=sptr)
+        x = torch.zeros_like(b)
+        s.solve(b, x, 1e-8, 64, allow_notconv=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        x.zero_()
+        e0.record(torch.cuda.current_stream())
+        s.solve(b, x, 1e-8, 64, allow_notconv=True)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        st = s.stats()
+        s.close()
+        return {"outer_its": st["outer_its"], "ms_per_solve": round(e0.elapsed_time(e1), 3),
+                "resid_explicit": st["resid_explicit"], "converged": bool(st["converged"])}
+
+    rows = []
+    for alpha in (1e-1, 1e-2, 1e-3):
+        P = inputs.config_2d(n=256, alpha=alpha, seed_field=11, seed_b=12)
+        for p in (10, 20, 40):
+            rows.append({"alpha": alpha, "p": p, "mixed": timed(P, binding.AAO_MIXED, p),
+                         "fp64": timed(P, binding.AAO_FP64, p)})
+    P = inputs.config_2d(n=1024, alpha=1e-2, seed_field=21, seed_b=22)
+    big = {"mixed": timed(P, binding.AAO_MIXED, 10), "fp64": timed(P, binding.AAO_FP64, 10)}
+    return {"workload": "2d_lognormal_256x256_l10 (sigma 0.5, corr 16, seeds 11/12), tol 1e-8",
+            "grid256": rows, "grid1024_a1e-2_p10": big}
+
+
 def run_ncu_case(args):
     """Small launch sequence for ncu captures: preconditioner applies only.
 
@@ -589,6 +631,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-rhs3d", action="store_true", help="skip the 3D 128^3 eight-right-hand-side workload")
     ap.add_argument("--no-best-case", action="store_true", help="skip the best-case (exact P_alpha) comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the alpha / p sweep (256^2) and the 1024^2 p = 10 solves")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run only preconditioner applies (small device footprint) for ncu captures")
     ap.add_argument("--ncu-fp64", action="store_true", help="with --ncu-case: FP64 path")
