@@ -283,8 +283,8 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
  * Batched solve: many independent instances of Eq. 1 (different grids, ell,
  * alpha, diffusivities and right-hand sides) solved together.  All members
  * advance in lockstep through right-preconditioned FGMRES; every phase of an
- * Arnoldi step (transform, each Chebyshev step, matvec, Gram-Schmidt passes,
- * Givens) is one launch over all members (one per distinct ell for the
+ * Arnoldi step (transform, each Chebyshev step, matvec, each modified
+ * Gram-Schmidt step, Givens) is one launch over all members (one per distinct ell for the
  * Chebyshev kernels), each block mapped to an (instance, tile) pair; members
  * that have converged skip their blocks.  With use_graphs != 0 each Arnoldi
  * step is captured once as a CUDA graph and replayed.  The paper solves one
@@ -293,7 +293,9 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
  *   members    count handles created with AAO_MIXED, dim 2, n[0] % 4 == 0, and
  *              the same inner_its (>= 2) and restart; they must outlive the
  *              batch, and the batch uses their workspace (do not use the
- *              members concurrently with a batched solve).
+ *              members concurrently with a batched solve).  The batch
+ *              orthogonalises by modified Gram-Schmidt when every member
+ *              uses AAO_ORTH_MGS (the default), else by CGS2.
  * The batch has its own non-blocking stream.
  */
 int aao_batch_create(aao_batch* hb, int count, const aao_handle* members, int use_graphs);

@@ -797,6 +797,7 @@ int solve_ci_impl(aao_ctx* h, const double* b, double* x, double tol, int max_it
 
 struct aao_batch_ctx {
   int M = 0, p = 0, m = 0;
+  bool mgs = true;  // modified Gram-Schmidt when every member uses it, else CGS2
   std::vector<aao_ctx*> mem;
   cudaStream_t stream = nullptr;
   bool use_graphs = true;
@@ -860,7 +861,8 @@ int batch_step_launches(aao_batch_ctx* B, int j) {
   for (size_t g = 0; g < B->wdft.size(); ++g)
     AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second, B->p, j, s));
   AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 0, j, s));
-  AAO_BCK(B, aao::batch_gram_schmidt(B->dI, B->dact, B->wred, B->wone, j, s));
+  if (B->mgs) AAO_BCK(B, aao::batch_mgs(B->dI, B->dact, B->wred, j, s));
+  else AAO_BCK(B, aao::batch_gram_schmidt(B->dI, B->dact, B->wred, B->wone, j, s));
   AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 0, j, B->dkvec, B->dout, s));
   AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 3, j, B->dkvec, B->dout, s));
   return AAO_OK;
@@ -1455,6 +1457,8 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     bi.Z = h->Z;
     bi.sc = h->sc;
     bi.partials = h->partials;
+    bi.counter = h->counter;
+    if (h->orth != AAO_ORTH_MGS) B->mgs = false;
     void* dsteps = nullptr;
     AAO_BCK_CREATE(cudaMalloc(&dsteps, sizeof(aao::StepArgs<float>) * h->steps32.size()));
     B->owned.push_back(dsteps);

@@ -107,6 +107,21 @@ __global__ void __launch_bounds__(kRedThreads) kb_orth_update(const BInst* __res
                    second ? b.partials + (int64_t)(b.m + 1) * b.nbred : nullptr);
 }
 
+// Step i of modified Gram-Schmidt on w = V_{j+1} (MODE as in mgs_step_body).
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) kb_mgs_step(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                            WorkList wl, int j, int iprev, int inext) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  double* hnext = (MODE == kMgsUpdNrm) ? b.sc + L.nrm2() : b.sc + L.h1(inext);
+  const double* hprev = (MODE == kMgsDot) ? nullptr : b.sc + L.h1(iprev);
+  mgs_step_body<MODE>(blockIdx.x - wl.start[li], b.nbred, b.V, b.L, iprev, inext, b.sc + L.vscale(0), hprev, hnext,
+                      b.V + (int64_t)(j + 1) * b.L, b.L, b.partials, b.counter);
+}
+
 __global__ void __launch_bounds__(kRedThreads) kb_norm2(const BInst* __restrict__ I, const int* __restrict__ act,
                                                          WorkList wl) {
   const int li = wl_find(wl, blockIdx.x);
@@ -261,6 +276,18 @@ cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& w
     AAO_BCHECK();
   }
   kb_reduce<<<dim3(1, wone.cnt, 1), kRedThreads, 0, s>>>(I, act, wone, 2);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_mgs(const BInst* I, const int* act, const WorkList& wred, int j, cudaStream_t s) {
+  kb_mgs_step<kMgsDot><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, -1, 0);
+  AAO_BCHECK();
+  for (int i = 1; i <= j; ++i) {
+    kb_mgs_step<kMgsUpdDot><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, i - 1, i);
+    AAO_BCHECK();
+  }
+  kb_mgs_step<kMgsUpdNrm><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, j, -1);
   AAO_BCHECK();
   return cudaSuccess;
 }

@@ -23,6 +23,7 @@ struct BInst {
   const double *cx64, *cy64;
   float *bhat, *xa, *xb;
   double *V, *Z, *sc, *partials;
+  unsigned* counter;             // the member's last-block ticket (modified Gram-Schmidt)
   const StepArgs<float>* steps;  // p entries
   const DftArgs<float>* da;
   const IdftArgs<float>* ia;
@@ -35,6 +36,9 @@ cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkLis
 cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, cudaStream_t s);
 cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& wred, const WorkList& wone, int j,
                                cudaStream_t s);
+// Modified Gram-Schmidt of Arnoldi step j: j + 2 fused launches over the list (one per basis
+// vector, as in the single-instance solver), each writing h_i (or ||w||^2) from its last block.
+cudaError_t batch_mgs(const BInst* I, const int* act, const WorkList& wred, int j, cudaStream_t s);
 cudaError_t batch_reduce(const BInst* I, const int* act, const WorkList& wone, int what, cudaStream_t s);
 cudaError_t batch_small(const BInst* I, const int* act, const WorkList& wone, int op, int j, const int* kvec,
                         double* out, cudaStream_t s);

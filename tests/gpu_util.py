@@ -29,7 +29,7 @@ def faces_or_none(a):
     return a.ravel() if a.size else None
 
 
-def make_solver(P, prec, p, restart=64, mu_max_override=0.0, device_faces=True):
+def make_solver(P, prec, p, restart=64, mu_max_override=0.0, device_faces=True, orth=None):
     torch = torch_cuda()
     binding = ensure_lib()
     fk = []
@@ -41,7 +41,7 @@ def make_solver(P, prec, p, restart=64, mu_max_override=0.0, device_faces=True):
         else:
             fk.append(np.ascontiguousarray(a.ravel()))
     s = binding.Solver(P.dim, P.n, fk[0], fk[1], fk[2], P.ell, P.alpha, prec=prec, inner_its=p,
-                       restart=restart, mu_max_override=mu_max_override,
+                       restart=restart, mu_max_override=mu_max_override, orth=orth,
                        stream=torch.cuda.current_stream().cuda_stream)
     s._faces = fk   # keep device copies alive
     return s

@@ -65,6 +65,39 @@ def test_batch_matches_oracle_and_single_solves():
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
+def test_batch_orthogonalisation_follows_members(orth):
+    # Members on modified Gram-Schmidt (the default): the batch runs one fused MGS launch per
+    # basis vector over all members.  Members on CGS2: the batch runs the classical passes.
+    # Either way each member converges, certified, within the tolerance of the exact solution,
+    # in the iterations it takes alone (+-1: the batch sweeps one Chebyshev step per launch and
+    # the single solver four, so their FP32 rounding differs).
+    torch = torch_cuda()
+    binding = ensure_lib()
+    code = binding.AAO_ORTH_MGS if orth == "mgs" else binding.AAO_ORTH_CGS2
+    probs = _members()[:4]
+    bs = [to_dev(P.b) for P in probs]
+    solvers = [make_solver(P, 1, 12, restart=32, orth=code) for P in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = binding.Batch(solvers, use_graphs=True)
+    batch.solve(bs, xs, 1e-8, 200)
+    for i, P in enumerate(probs):
+        st = batch.stats(i)
+        s1 = make_solver(P, 1, 12, restart=32, orth=code)
+        x1 = torch.zeros_like(bs[i])
+        s1.solve(bs[i], x1, 1e-8, 200)
+        its1 = s1.stats()["outer_its"]
+        A = solve.make_block_op(P.kx, P.ky, P.kz, P.shape)
+        xg = xs[i].cpu().numpy()
+        res = np.linalg.norm(P.b - allatonce.aao_apply(A, xg)) / np.linalg.norm(P.b)
+        xe = _exact(P)
+        err = np.linalg.norm(xg - xe) / np.linalg.norm(xe)
+        log_record({"test": "batch_orth", "orth": orth, "i": i, "its": st["outer_its"], "its_single": its1,
+                    "resid": res, "err": err})
+        assert st["converged"] and res <= 1e-8 and err <= 1e-7
+        assert abs(st["outer_its"] - its1) <= 1
+
+
 def test_batch_argument_checks():
     torch_cuda()
     binding = ensure_lib()
