@@ -559,6 +559,32 @@ def run_ncu_case(args):
                       "z_norm": float(torch.linalg.norm(z))}))
 
 
+def run_ncu_batch(args):
+    """One batched solve of the 64-instance workload with direct launches (no CUDA graphs), for
+    an ncu launch list of the batch's kernels.  The device holds about 65 GB (Krylov spaces of
+    restart 64); every launch is short."""
+    import torch
+
+    from paper_2506_03947_gb300 import binding
+    from paper_2506_03947_gb300 import build as pkg_build
+    from paper_2506_03947_gb300 import inputs
+    pkg_build.build()
+    probs = inputs.config_batch(count=args.batch_count)
+    sptr = torch.cuda.current_stream().cuda_stream
+    solvers = [binding.Solver(P.dim, P.n, P.kx.ravel(), P.ky.ravel(), None, P.ell, P.alpha,
+                              prec=binding.AAO_MIXED, inner_its=P.inner_its, restart=64, stream=sptr)
+               for P in probs]
+    bs = [torch.from_numpy(P.b).cuda() for P in probs]
+    xs = [torch.zeros_like(v) for v in bs]
+    bat = binding.Batch(solvers, use_graphs=False)
+    n0 = binding.aao_kernel_launch_count()
+    bat.solve(bs, xs, 1e-8, 200)
+    torch.cuda.synchronize()
+    its = [bat.stats(i)["outer_its"] for i in range(len(probs))]
+    print(json.dumps({"ncu_batch": len(probs), "launches": binding.aao_kernel_launch_count() - n0,
+                      "outer_its_max": max(its), "outer_its_mean": sum(its) / len(its)}))
+
+
 def cpu_baseline_sample(P, p, outer_its):
     """Oracle (numpy FP64) on a bounded sample: one outer FGMRES iteration on the full grid.
 
@@ -637,9 +663,14 @@ def main():
     ap.add_argument("--ncu-fp64", action="store_true", help="with --ncu-case: FP64 path")
     ap.add_argument("--ncu-solve", action="store_true",
                     help="with --ncu-case: also one solve with a 16-vector Krylov space (about 3 GB)")
+    ap.add_argument("--ncu-batch", action="store_true",
+                    help="run only one batched solve of the 64-instance workload without graphs (ncu launch list)")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)
+        return
+    if args.ncu_batch:
+        run_ncu_batch(args)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

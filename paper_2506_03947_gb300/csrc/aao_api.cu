@@ -808,8 +808,8 @@ struct aao_batch_ctx {
   double* dout = nullptr;
   double* hout = nullptr;  // pinned, 2M
   std::vector<void*> owned;
-  std::vector<std::pair<int, aao::WorkList>> wdft, wstep;  // per ell
-  aao::WorkList wmv{}, wred{}, wone{};
+  std::vector<std::pair<int, aao::WorkList>> wdft, wstep, wquad;  // per ell
+  aao::WorkList wmv{}, wred{}, wone{}, wmgs{};
   std::vector<cudaGraphExec_t> graphs;
   std::vector<long long> graph_launches;
   std::vector<aao_stats> stats;
@@ -859,9 +859,10 @@ int make_worklist(aao_batch_ctx* B, const std::vector<int>& inst, const std::vec
 int batch_step_launches(aao_batch_ctx* B, int j) {
   cudaStream_t s = B->stream;
   for (size_t g = 0; g < B->wdft.size(); ++g)
-    AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second, B->p, j, s));
+    AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second,
+                                  B->wquad[g].second, B->p, j, s));
   AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 0, j, s));
-  if (B->mgs) AAO_BCK(B, aao::batch_mgs(B->dI, B->dact, B->wred, j, s));
+  if (B->mgs) AAO_BCK(B, aao::batch_mgs(B->dI, B->dact, B->wmgs, j, s));
   else AAO_BCK(B, aao::batch_gram_schmidt(B->dI, B->dact, B->wred, B->wone, j, s));
   AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 0, j, B->dkvec, B->dout, s));
   AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 3, j, B->dkvec, B->dout, s));
@@ -1434,7 +1435,8 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
   } while (0)
   AAO_BCK_CREATE(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
   B->hI.resize(count);
-  std::vector<int> all(count), bdft(count), bstep(count), bmv(count), bred(count), bone(count, 1);
+  std::vector<int> all(count), bdft(count), bstep(count), bquad(count), bmv(count), bred(count), bmgs(count),
+      bone(count, 1);
   std::vector<int> ells;
   for (int i = 0; i < count; ++i) {
     aao_ctx* h = members[i];
@@ -1445,6 +1447,7 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     bi.m = h->m;
     bi.L = h->L;
     bi.nbred = aao::reduction_blocks(h->L);
+    bi.nbmgs = aao::batch_mgs_blocks(h->L);
     bi.nbmv = (int)(((h->n[0] + 31) / 32) * ((h->n[1] + 7) / 8));
     bi.cx32 = h->cx32;
     bi.cy32 = h->cy32;
@@ -1453,6 +1456,8 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     bi.bhat = (float*)h->bhat;
     bi.xa = (float*)h->xa;
     bi.xb = (float*)h->xb;
+    bi.xc = (float*)h->xc;
+    bi.xd = (float*)h->xd;
     bi.V = h->V;
     bi.Z = h->Z;
     bi.sc = h->sc;
@@ -1480,25 +1485,30 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     all[i] = i;
     bdft[i] = (int)((h->N + 255) / 256);
     bstep[i] = (int)(((h->n[0] + 127) / 128) * ((h->n[1] + 7) / 8));
+    bquad[i] = aao::batch_quad_tiles(h->g);
     bmv[i] = bi.nbmv;
     bred[i] = bi.nbred;
+    bmgs[i] = bi.nbmgs;
     if (std::find(ells.begin(), ells.end(), h->ell) == ells.end()) ells.push_back(h->ell);
   }
   for (int ell : ells) {
-    std::vector<int> inst, nd, ns;
+    std::vector<int> inst, nd, ns, nq;
     for (int i = 0; i < count; ++i)
       if (members[i]->ell == ell) {
         inst.push_back(i);
         nd.push_back(bdft[i]);
         ns.push_back(bstep[i]);
+        nq.push_back(bquad[i]);
       }
-    aao::WorkList wd, ws;
-    if (make_worklist(B, inst, nd, &wd) || make_worklist(B, inst, ns, &ws)) return bail(AAO_ECUDA);
+    aao::WorkList wd, ws, wq;
+    if (make_worklist(B, inst, nd, &wd) || make_worklist(B, inst, ns, &ws) || make_worklist(B, inst, nq, &wq))
+      return bail(AAO_ECUDA);
     B->wdft.push_back({ell, wd});
     B->wstep.push_back({ell, ws});
+    B->wquad.push_back({ell, wq});
   }
   if (make_worklist(B, all, bmv, &B->wmv) || make_worklist(B, all, bred, &B->wred) ||
-      make_worklist(B, all, bone, &B->wone))
+      make_worklist(B, all, bmgs, &B->wmgs) || make_worklist(B, all, bone, &B->wone))
     return bail(AAO_ECUDA);
   AAO_BCK_CREATE(cudaMalloc(&B->dI, sizeof(aao::BInst) * count));
   AAO_BCK_CREATE(cudaMalloc(&B->dact, sizeof(int) * count));

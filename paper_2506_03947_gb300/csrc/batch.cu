@@ -10,6 +10,7 @@
 // split by ell; the FP64 kernels take ell at run time.
 #include "batch.cuh"
 #include "cheb_kernels.cuh"
+#include "cheb_quad.cuh"
 #include "krylov_bodies.cuh"
 
 namespace aao {
@@ -62,6 +63,42 @@ __global__ void __launch_bounds__(256) kb_step(const BInst* __restrict__ I, cons
   }
   cheb_step_v4_body<ELL, 2, KSRC, PSRC, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, xk, xio,
                                               b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
+}
+
+__device__ __forceinline__ float* field(const BInst& b, int i) {
+  return i == 0 ? b.xa : i == 1 ? b.xb : i == 2 ? b.xc : b.xd;
+}
+
+// Steps k .. k+3 from x_k = field cur and x_{k-1} = field prev (PSRC 2) or bhat/theta (PSRC 1),
+// writing x_{k+3} to field o3 and x_{k+4} to field o4; one block per (instance, tile).
+template <int ELL, int PSRC>
+__global__ void __launch_bounds__(kQuadTileNT) kb_quad(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                        WorkList wl, int k, int cur, int prev, int o3, int o4) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const int lb = blockIdx.x - wl.start[li];
+  const int tx = (b.g.n0 + kQuadInnerX - 1) / kQuadInnerX;
+  static_assert(sizeof(QuadArgs) == 4 * sizeof(StepArgs<float>), "four consecutive step tables");
+  cheb_quad_body<ELL, kQuadTileTY, PSRC, kQuadTileNT>(b.g, lb % tx, lb / tx, b.cx32, b.cy32, b.bhat, field(b, cur),
+                                                      PSRC == 2 ? field(b, prev) : nullptr, field(b, o3),
+                                                      field(b, o4), *reinterpret_cast<const QuadArgs*>(b.steps + k));
+}
+
+// One step k from x_k = field cur; x_{k-1} = field io (PSRC 2, overwritten by x_{k+1}) or
+// bhat/theta (PSRC 1, x_{k+1} into field io); LAST: inverse transform into Z_j instead.
+template <int ELL, int PSRC, bool LAST>
+__global__ void __launch_bounds__(256) kb_step_f(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                  WorkList wl, int k, int j, int cur, int io) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const int lb = blockIdx.x - wl.start[li];
+  const int gx = (b.g.n0 + 127) / 128;
+  cheb_step_v4_body<ELL, 2, 1, PSRC, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, field(b, cur),
+                                           field(b, io), b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
 }
 
 // ---- FP64 outer solve ----------------------------------------------------------
@@ -118,7 +155,7 @@ __global__ void __launch_bounds__(kRedThreads) kb_mgs_step(const BInst* __restri
   const ScLayout L{b.m};
   double* hnext = (MODE == kMgsUpdNrm) ? b.sc + L.nrm2() : b.sc + L.h1(inext);
   const double* hprev = (MODE == kMgsDot) ? nullptr : b.sc + L.h1(iprev);
-  mgs_step_body<MODE>(blockIdx.x - wl.start[li], b.nbred, b.V, b.L, iprev, inext, b.sc + L.vscale(0), hprev, hnext,
+  mgs_step_body<MODE>(blockIdx.x - wl.start[li], b.nbmgs, b.V, b.L, iprev, inext, b.sc + L.vscale(0), hprev, hnext,
                       b.V + (int64_t)(j + 1) * b.L, b.L, b.partials, b.counter);
 }
 
@@ -195,47 +232,73 @@ __global__ void __launch_bounds__(kRedThreads) kb_xupdate(const BInst* __restric
     if (e_ != cudaSuccess) return e_; \
   } while (0)
 
+int batch_quad_tiles(const GridDesc& g) {
+  return ((g.n0 + kQuadInnerX - 1) / kQuadInnerX) * ((g.n1 + kQuadTileTY - 1) / kQuadTileTY);
+}
+
 template <int ELL>
-cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wdft, const WorkList& wstep, int p, int j,
-                              cudaStream_t s) {
+cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wdft, const WorkList& wstep,
+                              const WorkList& wquad, int p, int j, cudaStream_t s) {
   if (wdft.cnt == 0) return cudaSuccess;
   if (p < 2) return cudaErrorInvalidValue;  // the batch runs p >= 2
   kb_dft<ELL><<<wdft.total, 256, 0, s>>>(I, act, wdft, j);
   AAO_BCHECK();
   const dim3 blk(32, 8, 1);
+  // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in field 0 (or Z_j if p == 2)
   if (p == 2) {
-    // step 1 is the last one: transform straight to Z_j
     kb_step<ELL, 0, 0, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, 1, j);
     AAO_BCHECK();
     return cudaSuccess;
   }
   kb_step<ELL, 0, 0, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, 1, j);
   AAO_BCHECK();
-  if (p == 3) {
-    kb_step<ELL, 1, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, 2, j);
+  // Four-step launches while steps k .. k+3 all come before the last step; the four fields
+  // rotate so that a launch never writes a field it reads (same schedule as the single solver).
+  const size_t qsmem = quad_smem_bytes<kQuadTileTY>();
+  int cur = 0, prev = -1, k = 2;
+  while (k + 3 <= p - 2) {
+    int o[2], n = 0;
+    for (int f = 0; f < 4 && n < 2; ++f)
+      if (f != cur && f != prev) o[n++] = f;
+    if (prev < 0) {
+      cudaFuncSetAttribute(kb_quad<ELL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+      kb_quad<ELL, 1><<<wquad.total, kQuadTileNT, qsmem, s>>>(I, act, wquad, k, cur, 0, o[0], o[1]);
+    } else {
+      cudaFuncSetAttribute(kb_quad<ELL, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+      kb_quad<ELL, 2><<<wquad.total, kQuadTileNT, qsmem, s>>>(I, act, wquad, k, cur, prev, o[0], o[1]);
+    }
     AAO_BCHECK();
-    return cudaSuccess;
+    prev = o[0];
+    cur = o[1];
+    k += 4;
   }
-  kb_step<ELL, 1, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, 2, j);
+  // single steps up to p - 2, x_{k+1} over x_{k-1}
+  for (; k <= p - 2; ++k) {
+    int dst = prev;
+    if (dst < 0) dst = (cur == 0) ? 1 : 0;
+    if (prev < 0) kb_step_f<ELL, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    else kb_step_f<ELL, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    AAO_BCHECK();
+    prev = cur;
+    cur = dst;
+  }
+  // the last step k = p - 1, fused with the inverse transform into Z_j
+  if (prev < 0) kb_step_f<ELL, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
+  else kb_step_f<ELL, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
   AAO_BCHECK();
-  for (int k = 3; k <= p - 1; ++k) {
-    if (k == p - 1) kb_step<ELL, 1, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j);
-    else kb_step<ELL, 1, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j);
-    AAO_BCHECK();
-  }
   return cudaSuccess;
 }
 
-cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep, int p,
-                          int j, cudaStream_t s) {
+cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
+                          const WorkList& wquad, int p, int j, cudaStream_t s) {
   switch (ell) {
-    case 4: return batch_precond_ell<4>(I, act, wdft, wstep, p, j, s);
-    case 6: return batch_precond_ell<6>(I, act, wdft, wstep, p, j, s);
-    case 8: return batch_precond_ell<8>(I, act, wdft, wstep, p, j, s);
-    case 10: return batch_precond_ell<10>(I, act, wdft, wstep, p, j, s);
-    case 12: return batch_precond_ell<12>(I, act, wdft, wstep, p, j, s);
-    case 14: return batch_precond_ell<14>(I, act, wdft, wstep, p, j, s);
-    case 16: return batch_precond_ell<16>(I, act, wdft, wstep, p, j, s);
+    case 4: return batch_precond_ell<4>(I, act, wdft, wstep, wquad, p, j, s);
+    case 6: return batch_precond_ell<6>(I, act, wdft, wstep, wquad, p, j, s);
+    case 8: return batch_precond_ell<8>(I, act, wdft, wstep, wquad, p, j, s);
+    case 10: return batch_precond_ell<10>(I, act, wdft, wstep, wquad, p, j, s);
+    case 12: return batch_precond_ell<12>(I, act, wdft, wstep, wquad, p, j, s);
+    case 14: return batch_precond_ell<14>(I, act, wdft, wstep, wquad, p, j, s);
+    case 16: return batch_precond_ell<16>(I, act, wdft, wstep, wquad, p, j, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -280,14 +343,24 @@ cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& w
   return cudaSuccess;
 }
 
-cudaError_t batch_mgs(const BInst* I, const int* act, const WorkList& wred, int j, cudaStream_t s) {
-  kb_mgs_step<kMgsDot><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, -1, 0);
+// At least 16 K elements (64 per thread) per block: with the reduction lists' ~2 K the fixed
+// cost of a block (last-block ticket, block sums) rivalled its streaming work.
+int batch_mgs_blocks(int64_t L) {
+  const int64_t per_block = (int64_t)kRedThreads * 64;
+  int64_t nb = (L + per_block - 1) / per_block;
+  const int64_t cap = reduction_blocks(L);
+  if (nb > cap) nb = cap;
+  return nb < 1 ? 1 : (int)nb;
+}
+
+cudaError_t batch_mgs(const BInst* I, const int* act, const WorkList& wmgs, int j, cudaStream_t s) {
+  kb_mgs_step<kMgsDot><<<wmgs.total, kRedThreads, 0, s>>>(I, act, wmgs, j, -1, 0);
   AAO_BCHECK();
   for (int i = 1; i <= j; ++i) {
-    kb_mgs_step<kMgsUpdDot><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, i - 1, i);
+    kb_mgs_step<kMgsUpdDot><<<wmgs.total, kRedThreads, 0, s>>>(I, act, wmgs, j, i - 1, i);
     AAO_BCHECK();
   }
-  kb_mgs_step<kMgsUpdNrm><<<wred.total, kRedThreads, 0, s>>>(I, act, wred, j, j, -1);
+  kb_mgs_step<kMgsUpdNrm><<<wmgs.total, kRedThreads, 0, s>>>(I, act, wmgs, j, j, -1);
   AAO_BCHECK();
   return cudaSuccess;
 }

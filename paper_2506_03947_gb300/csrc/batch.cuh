@@ -17,11 +17,11 @@ struct WorkList {
 // Everything a batched kernel needs about one instance (device array, one entry per member).
 struct BInst {
   GridDesc g;
-  int ell, m, nbred, nbmv;
+  int ell, m, nbred, nbmv, nbmgs;  // reduction, matvec and modified Gram-Schmidt blocks
   int64_t L;
   const float *cx32, *cy32;
   const double *cx64, *cy64;
-  float *bhat, *xa, *xb;
+  float *bhat, *xa, *xb, *xc, *xd;  // transformed rhs and the four rotating Chebyshev fields
   double *V, *Z, *sc, *partials;
   unsigned* counter;             // the member's last-block ticket (modified Gram-Schmidt)
   const StepArgs<float>* steps;  // p entries
@@ -31,14 +31,21 @@ struct BInst {
   double* x;
 };
 
-cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep, int p,
-                          int j, cudaStream_t s);
+// Tiles (blocks) of the four-step kernel for one grid.
+int batch_quad_tiles(const GridDesc& g);
+// P_NC^{-1} of Arnoldi step j for the members of one ell: transform, step 1, four-step
+// launches (shared-memory tile kernel; list wquad) while they fit before the last step, single
+// steps for the rest (list wstep), the last step fused with the inverse transform into Z_j.
+cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
+                          const WorkList& wquad, int p, int j, cudaStream_t s);
 cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, cudaStream_t s);
 cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& wred, const WorkList& wone, int j,
                                cudaStream_t s);
 // Modified Gram-Schmidt of Arnoldi step j: j + 2 fused launches over the list (one per basis
 // vector, as in the single-instance solver), each writing h_i (or ||w||^2) from its last block.
-cudaError_t batch_mgs(const BInst* I, const int* act, const WorkList& wred, int j, cudaStream_t s);
+// List wmgs gives instance i batch_mgs_blocks(L_i) blocks.
+int batch_mgs_blocks(int64_t L);
+cudaError_t batch_mgs(const BInst* I, const int* act, const WorkList& wmgs, int j, cudaStream_t s);
 cudaError_t batch_reduce(const BInst* I, const int* act, const WorkList& wone, int what, cudaStream_t s);
 cudaError_t batch_small(const BInst* I, const int* act, const WorkList& wone, int op, int j, const int* kvec,
                         double* out, cudaStream_t s);

@@ -31,6 +31,8 @@ constexpr int kQuadCols = 128;                 // staged cells per row (32 lanes
 constexpr int kQuadPad = 4;                    // zero padding each side of a staged row
 constexpr int kQuadStride = kQuadCols + 2 * kQuadPad;
 constexpr int kQuadInnerX = kQuadCols - 2 * kQuadS;  // 120
+constexpr int kQuadTileTY = 16;                // interior rows of a tile
+constexpr int kQuadTileNT = 384;               // threads of a tile block
 
 template <int TY>
 __host__ __device__ constexpr int quad_rows() {
@@ -47,11 +49,14 @@ using QuadArgs = QuadSteps;
 // PSRC: x_{k-1} = bhat/theta (1, first fused step is k = 2) or read from xkm1 (2).
 // NT threads: NT/32 warps, each owning the staged rows warp, warp + NT/32, ...
 // (RPW of them) for the whole launch, so bhat of those rows stays in registers.
+// The body runs tile (bx, by); it is shared by the single-instance kernel below and the batched
+// one, which maps its blocks to (instance, tile) pairs.
 template <int ELL, int TY, int PSRC, int NT>
-__global__ void __launch_bounds__(NT)
-    k_cheb_quad(GridDesc g, const float* __restrict__ cx, const float* __restrict__ cy,
-                const float* __restrict__ bhat, const float* __restrict__ xk, const float* __restrict__ xkm1,
-                float* __restrict__ out3, float* __restrict__ out4, QuadArgs qa) {
+__device__ __forceinline__ void cheb_quad_body(const GridDesc& g, int bx, int by, const float* __restrict__ cx,
+                                               const float* __restrict__ cy, const float* __restrict__ bhat,
+                                               const float* __restrict__ xk, const float* __restrict__ xkm1,
+                                               float* __restrict__ out3, float* __restrict__ out4,
+                                               const QuadArgs& qa) {
   constexpr int ROWS = quad_rows<TY>();
   constexpr int PLANE = ROWS * kQuadStride;      // floats per staged plane
   extern __shared__ float sm[];
@@ -65,8 +70,8 @@ __global__ void __launch_bounds__(NT)
   constexpr int NW = NT / 32;
   constexpr int RPW = (ROWS + NW - 1) / NW;   // staged rows per warp
   F4 hreg[RPW][2];                             // bhat of this thread's rows, current pass
-  const int gx0 = blockIdx.x * kQuadInnerX - kQuadS;   // global x of staged column 0
-  const int gy0 = blockIdx.y * TY - kQuadS;            // global y of staged row 0
+  const int gx0 = bx * kQuadInnerX - kQuadS;   // global x of staged column 0
+  const int gy0 = by * TY - kQuadS;            // global y of staged row 0
   const int gx = gx0 + 4 * lane;
   const bool colok = gx >= 0 && gx < g.n0;             // four cells all in or all out (n0 % 4 == 0)
   const int64_t N = g.N;
@@ -243,6 +248,14 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
+template <int ELL, int TY, int PSRC, int NT>
+__global__ void __launch_bounds__(NT)
+    k_cheb_quad(GridDesc g, const float* __restrict__ cx, const float* __restrict__ cy,
+                const float* __restrict__ bhat, const float* __restrict__ xk, const float* __restrict__ xkm1,
+                float* __restrict__ out3, float* __restrict__ out4, const __grid_constant__ QuadArgs qa) {
+  cheb_quad_body<ELL, TY, PSRC, NT>(g, blockIdx.x, blockIdx.y, cx, cy, bhat, xk, xkm1, out3, out4, qa);
+}
+
 template <int ELL, int TY, int NT>
 cudaError_t launch_quad_cfg(const GridDesc& g, int psrc, const float* cx, const float* cy, const float* bhat,
                             const float* xk, const float* xkm1, float* out3, float* out4, const QuadArgs& qa,
@@ -265,7 +278,7 @@ template <int ELL>
 cudaError_t launch_quad_ell(const GridDesc& g, int psrc, const float* cx, const float* cy, const float* bhat,
                             const float* xk, const float* xkm1, float* out3, float* out4, const QuadArgs& qa,
                             cudaStream_t s) {
-  return launch_quad_cfg<ELL, 16, 384>(g, psrc, cx, cy, bhat, xk, xkm1, out3, out4, qa, s);
+  return launch_quad_cfg<ELL, kQuadTileTY, kQuadTileNT>(g, psrc, cx, cy, bhat, xk, xkm1, out3, out4, qa, s);
 }
 
 }  // namespace aao
