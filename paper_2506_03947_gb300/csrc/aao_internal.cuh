@@ -100,8 +100,11 @@ cudaError_t launch_quad(const GridDesc& g, int ell, int psrc, const float* cx, c
 // Persistent TMA-fed variant of the four-step kernel (cheb_quad_tma.cu):
 // tiles of 120 x kQuadTmaTY interior cells, kQuadTmaR staged rows per warp.
 // Its x_k, x_{k-1} and bhat arrive through TMA descriptors of the ell-plane
-// FP32 fields (3D: n0, n1, ell; box 128 x (kQuadTmaTY + 8) x 2).
-constexpr int kQuadTmaTY = 16;
+// FP32 fields (3D: n0, n1, ell; box 128 x (kQuadTmaTY + 8) x 2).  22 rows give
+// 15 warps per CTA (123 registers, 216 KB of shared memory) and, on a 1024^2 grid,
+// 423 tiles, i.e. three rounds over 152 SMs; 16 rows gave 12 warps and 576 tiles
+// in four rounds (7 % slower), 24 rows 16 warps at the shared-memory limit (12 % slower).
+constexpr int kQuadTmaTY = 22;
 constexpr int kQuadTmaR = 2;
 constexpr long long kQuadTmaWaitCycles = 2000000000ll;  // bound of one TMA wait (~1 s at 2 GHz)
 struct alignas(64) FieldMap {

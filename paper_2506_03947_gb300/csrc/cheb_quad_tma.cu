@@ -8,13 +8,13 @@
 // (d = 1 + sum of the four face coefficients).
 //
 // Organisation (one CTA per SM, persistent over tiles):
-//  * A tile is 120 x 16 interior cells plus a four-cell halo: 128 x 24 staged
+//  * A tile is 120 x 22 interior cells plus a four-cell halo: 128 x 30 staged
 //    cells.  Warp w owns staged rows R*w .. R*w+R-1 and lane l owns columns
 //    4l .. 4l+3 of them for the whole tile; the face coefficients and the
 //    diagonal of those cells live in registers across all ell/2 passes.
 //  * A pass handles one plane pair (the two real frequencies, then each
 //    complex one).  Its x_k, x_{k-1} and bhat tiles (three boxes of
-//    128 x 24 x 2 floats) arrive by TMA into one of two shared-memory stages;
+//    128 x 30 x 2 floats) arrive by TMA into one of two shared-memory stages;
 //    the copy of the next pass (or the next tile's first pass) is issued as
 //    soon as the current one has landed, so loads overlap a whole pass of
 //    arithmetic.
@@ -23,7 +23,7 @@
 //    (into the consumed x_{k-1} / bhat boxes of the current stage), so a
 //    level costs one barrier and, per warp row pair, two stores and two
 //    loads per plane; east/west neighbours come from warp shuffles.
-//  * After four levels the interior (lanes 1..30, rows 4..19) holds x_{k+3}
+//  * After four levels the interior (lanes 1..30, rows 4..25) holds x_{k+3}
 //    and x_{k+4}; both are stored straight from registers.
 // Every wait on a TMA transaction is bounded (wait_limit SM clocks, about a
 // second by default); on expiry the block records the fault in a device flag,
