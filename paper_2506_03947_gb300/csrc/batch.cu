@@ -72,16 +72,17 @@ __device__ __forceinline__ float* field(const BInst& b, int i) {
 // Steps k .. k+3 from x_k = field cur and x_{k-1} = field prev (PSRC 2) or bhat/theta (PSRC 1),
 // writing x_{k+3} to field o3 and x_{k+4} to field o4; one block per (instance, tile).
 template <int ELL, int PSRC>
-__global__ void __launch_bounds__(kQuadTileNT) kb_quad(const BInst* __restrict__ I, const int* __restrict__ act,
+__global__ void __launch_bounds__(kQuadTileNT, 2) kb_quad(const BInst* __restrict__ I, const int* __restrict__ act,
                                                         WorkList wl, int k, int cur, int prev, int o3, int o4) {
   const int li = wl_find(wl, blockIdx.x);
   const int inst = wl.inst[li];
   if (!act[inst]) return;
   const BInst& b = I[inst];
   const int lb = blockIdx.x - wl.start[li];
-  const int tx = (b.g.n0 + kQuadInnerX - 1) / kQuadInnerX;
+  const GridDesc g = b.g;
+  const int tx = (g.n0 + kQuadInnerX - 1) / kQuadInnerX;
   static_assert(sizeof(QuadArgs) == 4 * sizeof(StepArgs<float>), "four consecutive step tables");
-  cheb_quad_body<ELL, kQuadTileTY, PSRC, kQuadTileNT>(b.g, lb % tx, lb / tx, b.cx32, b.cy32, b.bhat, field(b, cur),
+  cheb_quad_body<ELL, kQuadTileTY, PSRC, kQuadTileNT>(g, lb % tx, lb / tx, b.cx32, b.cy32, b.bhat, field(b, cur),
                                                       PSRC == 2 ? field(b, prev) : nullptr, field(b, o3),
                                                       field(b, o4), *reinterpret_cast<const QuadArgs*>(b.steps + k));
 }

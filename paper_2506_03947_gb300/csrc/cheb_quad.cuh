@@ -21,6 +21,8 @@
 // multiplied by g ~ 2/mu_max, i.e. a few units of roundoff of |x| per step.
 #pragma once
 
+#include <type_traits>
+
 #include "aao_internal.cuh"
 #include "cheb_v4.cuh"
 
@@ -105,146 +107,152 @@ __device__ __forceinline__ void cheb_quad_body(const GridDesc& g, int bx, int by
 
   const int npass = ELL / 2;
   for (int pass = 0; pass < npass; ++pass) {
-    // planes of this pass: (0, 1) = the two real frequencies, else (2m, 2m+1) for complex m = pass
-    const int p0 = (pass == 0) ? 0 : 2 * pass;
-    const int p1 = p0 + 1;
-    const bool cplx = pass > 0;
-    const int m0 = (pass == 0) ? 0 : pass;      // frequency of plane p0
-    const int m1 = (pass == 0) ? ELL / 2 : pass;  // frequency of plane p1
-    __syncthreads();  // previous pass finished reading the buffers
-    // ---- stage x_k (bufA) and x_{k-1} (bufB) on the staged region; bhat into registers
-#pragma unroll
-    for (int rr = 0; rr < RPW; ++rr) {
-      const int ly = warp + rr * NW;
-      if (ly >= ROWS) break;
-      const int gy = gy0 + ly;
-      const bool ok = colok && gy >= 0 && gy < g.n1;
-      const int64_t c = (int64_t)g.n0 * gy + gx;
-      const size_t o = (size_t)ly * kQuadStride + kQuadPad + 4 * lane;
-      const F4 x0 = ok ? ld4(xk + p0 * N + c) : zero4();
-      const F4 x1 = ok ? ld4(xk + p1 * N + c) : zero4();
-      const F4 h0 = ok ? ld4(bhat + p0 * N + c) : zero4();
-      const F4 h1 = ok ? ld4(bhat + p1 * N + c) : zero4();
-      F4 m0v, m1v;
-      if (PSRC == 2) {
-        m0v = ok ? ld4(xkm1 + p0 * N + c) : zero4();
-        m1v = ok ? ld4(xkm1 + p1 * N + c) : zero4();
-      } else {
-        // x_1 = bhat / theta
-        const StepArgs<float>& s0 = qa.s[0];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (cplx) {
-            m0v.v[e] = h0.v[e] * s0.it_re[m0] - h1.v[e] * s0.it_im[m0];
-            m1v.v[e] = h0.v[e] * s0.it_im[m0] + h1.v[e] * s0.it_re[m0];
-          } else {
-            m0v.v[e] = h0.v[e] * s0.it_re[m0];
-            m1v.v[e] = h1.v[e] * s0.it_re[m1];
-          }
-        }
-      }
-      st4(bufA + o, x0);
-      st4(bufA + PLANE + o, x1);
-      st4(bufB + o, m0v);
-      st4(bufB + PLANE + o, m1v);
-      hreg[rr][0] = h0;
-      hreg[rr][1] = h1;
-    }
-    // ---- four levels; level q+1 lives where level q-1 was
-    float* cur = bufA;   // level q
-    float* oth = bufB;   // level q-1, overwritten by level q+1
-#pragma unroll
-    for (int lv = 0; lv < kQuadS; ++lv) {
-      __syncthreads();
-      const StepArgs<float>& st = qa.s[lv];
-      const int lo = lv + 1;  // valid region of the new level: rows/cols [lo, extent - lo)
+    // The pass body is instantiated for the real pair (pass 0) and for a complex frequency, so
+    // the level loop carries no run-time branch on the pass type.
+    auto run = [&](auto cplx_c) {
+      constexpr bool cplx = decltype(cplx_c)::value;
+      // planes of this pass: (0, 1) = the two real frequencies, else (2m, 2m+1) for complex m = pass
+      const int p0 = (pass == 0) ? 0 : 2 * pass;
+      const int p1 = p0 + 1;
+      const int m0 = (pass == 0) ? 0 : pass;      // frequency of plane p0
+      const int m1 = (pass == 0) ? ELL / 2 : pass;  // frequency of plane p1
+      __syncthreads();  // previous pass finished reading the buffers
+      // ---- stage x_k (bufA) and x_{k-1} (bufB) on the staged region; bhat into registers
 #pragma unroll
       for (int rr = 0; rr < RPW; ++rr) {
         const int ly = warp + rr * NW;
         if (ly >= ROWS) break;
-        if (ly < lo || ly >= ROWS - lo) continue;
-        const size_t o = (size_t)ly * kQuadStride + kQuadPad + 4 * lane;
-        // coefficients of the four cells (E: own cx, W: cx of the left cell, N: own cy, S: cy of the row below)
-        const float4 kxe = *reinterpret_cast<const float4*>(kxs + o);
-        const float kxw = kxs[o - 1];
-        const float4 kyn = *reinterpret_cast<const float4*>(kys + o);
-        const float4 kys_ = *reinterpret_cast<const float4*>(kys + o - kQuadStride);
-        const float4 kdd = *reinterpret_cast<const float4*>(kds + o);
-        const float kE[4] = {kxe.x, kxe.y, kxe.z, kxe.w};
-        const float kW[4] = {kxw, kxe.x, kxe.y, kxe.z};
-        const float kN[4] = {kyn.x, kyn.y, kyn.z, kyn.w};
-        const float kS[4] = {kys_.x, kys_.y, kys_.z, kys_.w};
-        const float kD[4] = {kdd.x, kdd.y, kdd.z, kdd.w};
-        // nb[pl][e] = bhat + sum of kappa * neighbour values; xc = centre; xm = level q-1
-        float nb[2][4], xc[2][4], xm[2][4];
-#pragma unroll
-        for (int pl = 0; pl < 2; ++pl) {
-          const float* rp = cur + (size_t)pl * PLANE + o;
-          const float4 cc = *reinterpret_cast<const float4*>(rp);
-          const float4 nn = *reinterpret_cast<const float4*>(rp + kQuadStride);
-          const float4 ss = *reinterpret_cast<const float4*>(rp - kQuadStride);
-          const float left = rp[-1], right = rp[4];
-          const float c4[4] = {cc.x, cc.y, cc.z, cc.w};
-          const float n4[4] = {nn.x, nn.y, nn.z, nn.w};
-          const float s4[4] = {ss.x, ss.y, ss.z, ss.w};
-          const float4 mm = *reinterpret_cast<const float4*>(oth + (size_t)pl * PLANE + o);
-          const float m4[4] = {mm.x, mm.y, mm.z, mm.w};
-          const F4& h4v = hreg[rr][pl];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float xe = (e < 3) ? c4[e + 1] : right;
-            const float xw = (e > 0) ? c4[e - 1] : left;
-            float acc = fmaf(kE[e], xe, h4v.v[e]);
-            acc = fmaf(kW[e], xw, acc);
-            acc = fmaf(kN[e], n4[e], acc);
-            acc = fmaf(kS[e], s4[e], acc);
-            nb[pl][e] = acc;
-            xc[pl][e] = c4[e];
-            xm[pl][e] = m4[e];
-          }
-        }
-        float n0v[4], n1v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (cplx) {
-            const float lr = st.lam_re[m0], li = st.lam_im[m0];
-            const float ar = st.a_re[m0], ai = st.a_im[m0], gr = st.g_re[m0], gi = st.g_im[m0];
-            const float xr = xc[0][e], xi = xc[1][e];
-            const float dl = kD[e] - lr;
-            // b - (A - lambda) x, real and imaginary parts
-            const float rr_ = fmaf(-li, xi, fmaf(-dl, xr, nb[0][e]));
-            const float ri = fmaf(li, xr, fmaf(-dl, xi, nb[1][e]));
-            const float dr = xr - xm[0][e], di = xi - xm[1][e];
-            n0v[e] = fmaf(-gi, ri, fmaf(gr, rr_, fmaf(-ai, di, fmaf(ar, dr, xr))));
-            n1v[e] = fmaf(gi, rr_, fmaf(gr, ri, fmaf(ai, dr, fmaf(ar, di, xi))));
-          } else {
-            const float r0 = fmaf(-(kD[e] - st.lam_re[m0]), xc[0][e], nb[0][e]);
-            const float r1 = fmaf(-(kD[e] - st.lam_re[m1]), xc[1][e], nb[1][e]);
-            n0v[e] = fmaf(st.g_re[m0], r0, fmaf(st.a_re[m0], xc[0][e] - xm[0][e], xc[0][e]));
-            n1v[e] = fmaf(st.g_re[m1], r1, fmaf(st.a_re[m1], xc[1][e] - xm[1][e], xc[1][e]));
-          }
-        }
-        *reinterpret_cast<float4*>(oth + o) = make_float4(n0v[0], n0v[1], n0v[2], n0v[3]);
-        *reinterpret_cast<float4*>(oth + PLANE + o) = make_float4(n1v[0], n1v[1], n1v[2], n1v[3]);
-      }
-      float* t = cur;
-      cur = oth;
-      oth = t;
-    }
-    __syncthreads();
-    // ---- write the interior: level 4 (cur) -> out4, level 3 (oth) -> out3
-    if (lane >= 1 && lane <= 30 && colok) {
-      for (int ly = kQuadS + warp; ly < kQuadS + TY; ly += NW) {
         const int gy = gy0 + ly;
-        if (gy >= g.n1) break;
+        const bool ok = colok && gy >= 0 && gy < g.n1;
         const int64_t c = (int64_t)g.n0 * gy + gx;
         const size_t o = (size_t)ly * kQuadStride + kQuadPad + 4 * lane;
-        *reinterpret_cast<float4*>(out4 + p0 * N + c) = *reinterpret_cast<const float4*>(cur + o);
-        *reinterpret_cast<float4*>(out4 + p1 * N + c) = *reinterpret_cast<const float4*>(cur + PLANE + o);
-        *reinterpret_cast<float4*>(out3 + p0 * N + c) = *reinterpret_cast<const float4*>(oth + o);
-        *reinterpret_cast<float4*>(out3 + p1 * N + c) = *reinterpret_cast<const float4*>(oth + PLANE + o);
+        const F4 x0 = ok ? ld4(xk + p0 * N + c) : zero4();
+        const F4 x1 = ok ? ld4(xk + p1 * N + c) : zero4();
+        const F4 h0 = ok ? ld4(bhat + p0 * N + c) : zero4();
+        const F4 h1 = ok ? ld4(bhat + p1 * N + c) : zero4();
+        F4 m0v, m1v;
+        if (PSRC == 2) {
+          m0v = ok ? ld4(xkm1 + p0 * N + c) : zero4();
+          m1v = ok ? ld4(xkm1 + p1 * N + c) : zero4();
+        } else {
+          // x_1 = bhat / theta
+          const StepArgs<float>& s0 = qa.s[0];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (cplx) {
+              m0v.v[e] = h0.v[e] * s0.it_re[m0] - h1.v[e] * s0.it_im[m0];
+              m1v.v[e] = h0.v[e] * s0.it_im[m0] + h1.v[e] * s0.it_re[m0];
+            } else {
+              m0v.v[e] = h0.v[e] * s0.it_re[m0];
+              m1v.v[e] = h1.v[e] * s0.it_re[m1];
+            }
+          }
+        }
+        st4(bufA + o, x0);
+        st4(bufA + PLANE + o, x1);
+        st4(bufB + o, m0v);
+        st4(bufB + PLANE + o, m1v);
+        hreg[rr][0] = h0;
+        hreg[rr][1] = h1;
       }
-    }
+      // ---- four levels; level q+1 lives where level q-1 was
+      float* cur = bufA;   // level q
+      float* oth = bufB;   // level q-1, overwritten by level q+1
+#pragma unroll
+      for (int lv = 0; lv < kQuadS; ++lv) {
+        __syncthreads();
+        const StepArgs<float>& st = qa.s[lv];
+        const int lo = lv + 1;  // valid region of the new level: rows/cols [lo, extent - lo)
+#pragma unroll
+        for (int rr = 0; rr < RPW; ++rr) {
+          const int ly = warp + rr * NW;
+          if (ly >= ROWS) break;
+          if (ly < lo || ly >= ROWS - lo) continue;
+          const size_t o = (size_t)ly * kQuadStride + kQuadPad + 4 * lane;
+          // coefficients of the four cells (E: own cx, W: cx of the left cell, N: own cy, S: cy of the row below)
+          const float4 kxe = *reinterpret_cast<const float4*>(kxs + o);
+          const float kxw = kxs[o - 1];
+          const float4 kyn = *reinterpret_cast<const float4*>(kys + o);
+          const float4 kys_ = *reinterpret_cast<const float4*>(kys + o - kQuadStride);
+          const float4 kdd = *reinterpret_cast<const float4*>(kds + o);
+          const float kE[4] = {kxe.x, kxe.y, kxe.z, kxe.w};
+          const float kW[4] = {kxw, kxe.x, kxe.y, kxe.z};
+          const float kN[4] = {kyn.x, kyn.y, kyn.z, kyn.w};
+          const float kS[4] = {kys_.x, kys_.y, kys_.z, kys_.w};
+          const float kD[4] = {kdd.x, kdd.y, kdd.z, kdd.w};
+          // nb[pl][e] = bhat + sum of kappa * neighbour values; xc = centre; xm = level q-1
+          float nb[2][4], xc[2][4], xm[2][4];
+#pragma unroll
+          for (int pl = 0; pl < 2; ++pl) {
+            const float* rp = cur + (size_t)pl * PLANE + o;
+            const float4 cc = *reinterpret_cast<const float4*>(rp);
+            const float4 nn = *reinterpret_cast<const float4*>(rp + kQuadStride);
+            const float4 ss = *reinterpret_cast<const float4*>(rp - kQuadStride);
+            const float left = rp[-1], right = rp[4];
+            const float c4[4] = {cc.x, cc.y, cc.z, cc.w};
+            const float n4[4] = {nn.x, nn.y, nn.z, nn.w};
+            const float s4[4] = {ss.x, ss.y, ss.z, ss.w};
+            const float4 mm = *reinterpret_cast<const float4*>(oth + (size_t)pl * PLANE + o);
+            const float m4[4] = {mm.x, mm.y, mm.z, mm.w};
+            const F4& h4v = hreg[rr][pl];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float xe = (e < 3) ? c4[e + 1] : right;
+              const float xw = (e > 0) ? c4[e - 1] : left;
+              float acc = fmaf(kE[e], xe, h4v.v[e]);
+              acc = fmaf(kW[e], xw, acc);
+              acc = fmaf(kN[e], n4[e], acc);
+              acc = fmaf(kS[e], s4[e], acc);
+              nb[pl][e] = acc;
+              xc[pl][e] = c4[e];
+              xm[pl][e] = m4[e];
+            }
+          }
+          float n0v[4], n1v[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (cplx) {
+              const float lr = st.lam_re[m0], li = st.lam_im[m0];
+              const float ar = st.a_re[m0], ai = st.a_im[m0], gr = st.g_re[m0], gi = st.g_im[m0];
+              const float xr = xc[0][e], xi = xc[1][e];
+              const float dl = kD[e] - lr;
+              // b - (A - lambda) x, real and imaginary parts
+              const float rr_ = fmaf(-li, xi, fmaf(-dl, xr, nb[0][e]));
+              const float ri = fmaf(li, xr, fmaf(-dl, xi, nb[1][e]));
+              const float dr = xr - xm[0][e], di = xi - xm[1][e];
+              n0v[e] = fmaf(-gi, ri, fmaf(gr, rr_, fmaf(-ai, di, fmaf(ar, dr, xr))));
+              n1v[e] = fmaf(gi, rr_, fmaf(gr, ri, fmaf(ai, dr, fmaf(ar, di, xi))));
+            } else {
+              const float r0 = fmaf(-(kD[e] - st.lam_re[m0]), xc[0][e], nb[0][e]);
+              const float r1 = fmaf(-(kD[e] - st.lam_re[m1]), xc[1][e], nb[1][e]);
+              n0v[e] = fmaf(st.g_re[m0], r0, fmaf(st.a_re[m0], xc[0][e] - xm[0][e], xc[0][e]));
+              n1v[e] = fmaf(st.g_re[m1], r1, fmaf(st.a_re[m1], xc[1][e] - xm[1][e], xc[1][e]));
+            }
+          }
+          *reinterpret_cast<float4*>(oth + o) = make_float4(n0v[0], n0v[1], n0v[2], n0v[3]);
+          *reinterpret_cast<float4*>(oth + PLANE + o) = make_float4(n1v[0], n1v[1], n1v[2], n1v[3]);
+        }
+        float* t = cur;
+        cur = oth;
+        oth = t;
+      }
+      __syncthreads();
+      // ---- write the interior: level 4 (cur) -> out4, level 3 (oth) -> out3
+      if (lane >= 1 && lane <= 30 && colok) {
+        for (int ly = kQuadS + warp; ly < kQuadS + TY; ly += NW) {
+          const int gy = gy0 + ly;
+          if (gy >= g.n1) break;
+          const int64_t c = (int64_t)g.n0 * gy + gx;
+          const size_t o = (size_t)ly * kQuadStride + kQuadPad + 4 * lane;
+          *reinterpret_cast<float4*>(out4 + p0 * N + c) = *reinterpret_cast<const float4*>(cur + o);
+          *reinterpret_cast<float4*>(out4 + p1 * N + c) = *reinterpret_cast<const float4*>(cur + PLANE + o);
+          *reinterpret_cast<float4*>(out3 + p0 * N + c) = *reinterpret_cast<const float4*>(oth + o);
+          *reinterpret_cast<float4*>(out3 + p1 * N + c) = *reinterpret_cast<const float4*>(oth + PLANE + o);
+        }
+      }
+    };
+    if (pass == 0) run(std::false_type{});
+    else run(std::true_type{});
   }
 }
 
