@@ -98,6 +98,41 @@ def test_batch_orthogonalisation_follows_members(orth):
         assert abs(st["outer_its"] - its1) <= 1
 
 
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 11])
+def test_batch_schedules_over_p(p):
+    # The batch's preconditioner schedule depends on p:
+    #   p = 2: the last step at k = 1;
+    #   p = 3: the last step from x_1 = bhat/theta;
+    #   p = 5: single steps only;
+    #   p = 7: one four-step launch from x_1;
+    #   p = 11: two four-step launches and a single step.
+    # Each member must reach the oracle's exact solution, certified, in about the iterations it
+    # takes alone: within 5 %, or +-1. Small p needs 45-115 iterations with restarts, and the
+    # single solver runs fused pairs or four-step launches where the batch runs single steps,
+    # so FP32 rounding differs.
+    torch = torch_cuda()
+    binding = ensure_lib()
+    probs = _members()[:3]
+    bs = [to_dev(P.b) for P in probs]
+    solvers = [make_solver(P, 1, p, restart=64) for P in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = binding.Batch(solvers, use_graphs=True)
+    batch.solve(bs, xs, 1e-8, 200)
+    for i, P in enumerate(probs):
+        st = batch.stats(i)
+        s1 = make_solver(P, 1, p, restart=64)
+        x1 = torch.zeros_like(bs[i])
+        s1.solve(bs[i], x1, 1e-8, 200)
+        xe = _exact(P)
+        err = np.linalg.norm(xs[i].cpu().numpy() - xe) / np.linalg.norm(xe)
+        log_record({"test": "batch_p", "p": p, "i": i, "its": st["outer_its"],
+                    "its_single": s1.stats()["outer_its"], "err": err})
+        assert st["converged"] and err <= 1e-7
+        its1 = s1.stats()["outer_its"]
+        assert abs(st["outer_its"] - its1) <= max(1, its1 // 20)
+        assert st["a_matvecs"] == st["outer_its"] * P.ell * (p + 1) + (st["cycles"] + 1) * P.ell
+
+
 def test_batch_argument_checks():
     torch_cuda()
     binding = ensure_lib()
