@@ -61,6 +61,43 @@ def dist_env():
     return rank, world, local
 
 
+class Replicas:
+    """The N > 1 path: one process per GPU, each solving its own replica of the workload.  The
+    method has no exchange between instances, so the only collectives are a barrier around each
+    timed region and the maximum of the timed durations; rank 0 alone prints."""
+
+    def __init__(self, backend: str):
+        self.rank, self.world, self.local = dist_env()
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v: float, device: str = "cpu") -> float:
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_rate(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -167,24 +204,16 @@ def run_ours(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    rep = Replicas("nccl")
     pkg_build.build()
     binding.load_library()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        rep.barrier()
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rep.max(v, device="cuda")
 
     P = make_problem(args.workload)
     p = WORKLOADS[args.workload]["p"]
@@ -239,7 +268,7 @@ def run_ours(args):
                                                        sampler=sampler)
     walls32 = list(timed_solves.walls)
     ms_max = max_over_ranks(ms)
-    value = world * args.steps / (ms_max / 1e3)
+    value = job_rate(world, args.steps, ms_max / 1e3)
     x32 = x.clone()
     prof_steps = max(3, args.steps // 2)
     ms_prof, _, _, prof, _, _ = timed_solves(s32, prof_steps, 1, profile=True)
@@ -256,7 +285,7 @@ def run_ours(args):
         s32.solve(bh, xh, P.tol, 64)           # H2D b, solve, D2H x, stream synchronised
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * args.steps / e2e_s
+    e2e_value = job_rate(world, args.steps, e2e_s)
 
     # --- all-FP64 GPU path on the same workload ---
     fp64 = None
@@ -268,7 +297,7 @@ def run_ours(args):
         ms64, _, _, prof64, _, st64 = timed_solves(s64, k64, 1, profile=True)
         ms64 = max_over_ranks(ms64)
         rel = float(torch.linalg.norm(x - x32) / torch.linalg.norm(x))
-        fp64 = {"value": world * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64,
+        fp64 = {"value": job_rate(world, k64, ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64,
                 "outer_its": st64["outer_its"], "resid_explicit": st64["resid_explicit"],
                 "mixed_vs_fp64_rel_diff": rel,
                 "step_mid_gbs": (prof64["step_mid"]["bytes"] / (prof64["step_mid"]["ms"] * 1e-3) / 1e9
@@ -339,9 +368,7 @@ def run_ours(args):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    rep.close()
 
 
 def run_batch_leg(args, binding, torch, sptr):
