@@ -40,29 +40,19 @@ __global__ void __launch_bounds__(256) kb_dft(const BInst* __restrict__ I, const
                        gs);
 }
 
-template <int ELL, int KSRC, int PSRC, bool LAST>
-__global__ void __launch_bounds__(256) kb_step(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl,
-                                                int k, int j) {
+// Step k = 1 from x_1 = bhat/theta (x_0 = 0): x_2 into field 0, or (LAST, p = 2) the inverse
+// transform into Z_j.
+template <int ELL, bool LAST>
+__global__ void __launch_bounds__(256) kb_step_first(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                      WorkList wl, int j) {
   const int li = wl_find(wl, blockIdx.x);
   const int inst = wl.inst[li];
   if (!act[inst]) return;
   const BInst& b = I[inst];
   const int lb = blockIdx.x - wl.start[li];
   const int gx = (b.g.n0 + 127) / 128;
-  const float* xk;
-  float* xio;
-  if (k == 1) {
-    xk = nullptr;
-    xio = b.xa;
-  } else if (k == 2) {
-    xk = b.xa;
-    xio = b.xb;
-  } else {
-    xk = (k % 2 == 1) ? b.xb : b.xa;
-    xio = (k % 2 == 1) ? b.xa : b.xb;
-  }
-  cheb_step_v4_body<ELL, 2, KSRC, PSRC, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, xk, xio,
-                                              b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
+  cheb_step_v4_body<ELL, 2, 0, 0, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, nullptr, b.xa,
+                                        b.Z + (int64_t)j * b.L, b.steps[1], *b.ia);
 }
 
 __device__ __forceinline__ float* field(const BInst& b, int i) {
@@ -247,11 +237,11 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
   const dim3 blk(32, 8, 1);
   // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in field 0 (or Z_j if p == 2)
   if (p == 2) {
-    kb_step<ELL, 0, 0, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, 1, j);
+    kb_step_first<ELL, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
     AAO_BCHECK();
     return cudaSuccess;
   }
-  kb_step<ELL, 0, 0, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, 1, j);
+  kb_step_first<ELL, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
   AAO_BCHECK();
   // Four-step launches while steps k .. k+3 all come before the last step; the four fields
   // rotate so that a launch never writes a field it reads (same schedule as the single solver).
@@ -262,10 +252,14 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
     for (int f = 0; f < 4 && n < 2; ++f)
       if (f != cur && f != prev) o[n++] = f;
     if (prev < 0) {
-      cudaFuncSetAttribute(kb_quad<ELL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+      const cudaError_t ea = cudaFuncSetAttribute(kb_quad<ELL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)qsmem);
+      if (ea != cudaSuccess) return ea;
       kb_quad<ELL, 1><<<wquad.total, kQuadTileNT, qsmem, s>>>(I, act, wquad, k, cur, 0, o[0], o[1]);
     } else {
-      cudaFuncSetAttribute(kb_quad<ELL, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+      const cudaError_t ea = cudaFuncSetAttribute(kb_quad<ELL, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)qsmem);
+      if (ea != cudaSuccess) return ea;
       kb_quad<ELL, 2><<<wquad.total, kQuadTileNT, qsmem, s>>>(I, act, wquad, k, cur, prev, o[0], o[1]);
     }
     AAO_BCHECK();

@@ -271,11 +271,14 @@ cudaError_t launch_quad_cfg(const GridDesc& g, int psrc, const float* cx, const 
   const dim3 block(NT, 1, 1);
   const dim3 grid((unsigned)((g.n0 + kQuadInnerX - 1) / kQuadInnerX), (unsigned)((g.n1 + TY - 1) / TY), 1);
   const size_t smem = quad_smem_bytes<TY>();
+  cudaError_t e;
   if (psrc == 1) {
-    cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_cheb_quad<ELL, TY, 1, NT><<<grid, block, smem, s>>>(g, cx, cy, bhat, xk, xkm1, out3, out4, qa);
   } else {
-    cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_cheb_quad<ELL, TY, 2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     k_cheb_quad<ELL, TY, 2, NT><<<grid, block, smem, s>>>(g, cx, cy, bhat, xk, xkm1, out3, out4, qa);
   }
   count_launch();
