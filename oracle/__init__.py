@@ -35,7 +35,15 @@ Modules:
                 convergence results (Theorems 1, 3, 4; Proposition 1;
                 Corollary 1; Algorithm 1).
   chebyshev  -- textbook Chebyshev semi-iteration on B_j = A - lambda_j I.
-  precond    -- P_NC^{-1} (Eq. 5 with inner CI) and exact P_alpha^{-1}.
+  precond    -- P_NC^{-1} (Eq. 5 with inner CI), exact P_alpha^{-1}, and the
+                best-case P_alpha^{-1} through the spatial DCT (constant
+                diffusivities, Section 2.2).
+  saddle     -- P_SP (Section 4): CG on the real shifts, block-diagonally
+                preconditioned MINRES on the saddle-point systems, and the
+                aggregation multigrid V-cycle that applies the SPD blocks.
   gmres      -- right-preconditioned flexible GMRES (MGS, Givens).
+  outer_ci   -- the paper's outer Chebyshev semi-iteration over Corollary 1's
+                interval (Section 5).
+  solve      -- FGMRES on Eq. 1 with P_NC^{-1}, assembled from the above.
   exact      -- the solution of Eq. 1 by sequential solves; plain CG.
 """
