@@ -144,19 +144,37 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     return lib
 
 
-def _ptr(a) -> int:
-    """Address of a contiguous float64 torch tensor or numpy array (None -> 0)."""
+def _ptr(a, n: Optional[int] = None, what: str = "array") -> int:
+    """Address of a contiguous float64 torch tensor or numpy array (None -> 0).
+
+    n: the number of float64 values the library will access through the pointer.  The C ABI
+    takes plain pointers and cannot check sizes, so a shorter array is refused here, before
+    any device work."""
     if a is None:
         return 0
     if hasattr(a, "data_ptr"):                       # torch.Tensor
         import torch
         if a.dtype != torch.float64 or not a.is_contiguous():
             raise ValueError("tensors passed to libaao must be contiguous float64")
-        return int(a.data_ptr())
-    import numpy as np
-    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-        raise ValueError("arrays passed to libaao must be C-contiguous float64 numpy arrays")
-    return int(a.ctypes.data)
+        size, addr = int(a.numel()), int(a.data_ptr())
+    else:
+        import numpy as np
+        if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to libaao must be C-contiguous float64 numpy arrays")
+        size, addr = int(a.size), int(a.ctypes.data)
+    if n is not None and size != n:
+        raise ValueError("%s: expected %d float64 values, got %d" % (what, n, size))
+    return addr
+
+
+def _grid(n: Sequence[int]):
+    return tuple(int(v) for v in (list(n) + [1, 1, 1])[:3])
+
+
+def _face_counts(dim: int, n: Sequence[int]):
+    """Interior faces per axis (include/aao.h): kx n2*n1*(n0-1), ky n2*(n1-1)*n0, kz (n2-1)*n1*n0."""
+    n0, n1, n2 = _grid(n)
+    return (n2 * n1 * (n0 - 1), n2 * (n1 - 1) * n0 if dim >= 2 else 0, (n2 - 1) * n1 * n0 if dim == 3 else 0)
 
 
 def _check(h, rc: int, ok=(AAO_OK,)) -> int:
@@ -177,38 +195,45 @@ def aao_create(dim: int, n: Sequence[int], kx, ky, kz, ell: int, alpha: float,
                opt: Optional[aao_options] = None):
     lib = load_library()
     h = C.c_void_p()
-    n3 = (C.c_int64 * 3)(*[int(v) for v in (list(n) + [1, 1, 1])[:3]])
-    rc = lib.aao_create(C.byref(h), int(dim), n3, _ptr(kx) or None, _ptr(ky) or None,
-                        _ptr(kz) or None, int(ell), float(alpha),
+    n3 = (C.c_int64 * 3)(*_grid(n))
+    fx, fy, fz = _face_counts(int(dim), n)
+    px = _ptr(kx, fx if kx is not None else None, "kx")
+    py = _ptr(ky, fy if ky is not None else None, "ky")
+    pz = _ptr(kz, fz if kz is not None else None, "kz")
+    rc = lib.aao_create(C.byref(h), int(dim), n3, px or None, py or None, pz or None, int(ell), float(alpha),
                         C.byref(opt) if opt is not None else None)
     _check(None, rc)
     return h
 
 
-def aao_matvec(h, x, y) -> int:
-    return _check(h, load_library().aao_matvec(h, _ptr(x), _ptr(y)))
+# L: ell * N, the float64 values of one block vector; None skips the size check.
+
+def aao_matvec(h, x, y, L: Optional[int] = None) -> int:
+    return _check(h, load_library().aao_matvec(h, _ptr(x, L, "x"), _ptr(y, L, "y")))
 
 
-def aao_precond_apply(h, r, z) -> int:
-    return _check(h, load_library().aao_precond_apply(h, _ptr(r), _ptr(z)))
+def aao_precond_apply(h, r, z, L: Optional[int] = None) -> int:
+    return _check(h, load_library().aao_precond_apply(h, _ptr(r, L, "r"), _ptr(z, L, "z")))
 
 
 def aao_solve(h, b, x, tol: float, max_outer: int, inner_its: int = 0, use_x0: bool = False,
-              allow_notconv: bool = False) -> int:
+              allow_notconv: bool = False, L: Optional[int] = None) -> int:
     ok = (AAO_OK, AAO_ENOTCONV) if allow_notconv else (AAO_OK,)
-    return _check(h, load_library().aao_solve(h, _ptr(b), _ptr(x), float(tol), int(max_outer),
+    return _check(h, load_library().aao_solve(h, _ptr(b, L, "b"), _ptr(x, L, "x"), float(tol), int(max_outer),
                                               int(inner_its), 1 if use_x0 else 0), ok)
 
 
-def aao_solve_fixed(h, b, x, k: int, inner_its: int = 0) -> int:
-    return _check(h, load_library().aao_solve_fixed(h, _ptr(b), _ptr(x), int(k), int(inner_its)))
+def aao_solve_fixed(h, b, x, k: int, inner_its: int = 0, L: Optional[int] = None) -> int:
+    return _check(h, load_library().aao_solve_fixed(h, _ptr(b, L, "b"), _ptr(x, L, "x"), int(k), int(inner_its)))
 
 
 def aao_solve_ci(h, b, x, tol: float, max_outer: int, inner_its: int = 0, use_x0: bool = False,
-                 l_min: float = 0.0, l_max: float = 0.0, fixed_its: int = 0, allow_notconv: bool = False) -> int:
+                 l_min: float = 0.0, l_max: float = 0.0, fixed_its: int = 0, allow_notconv: bool = False,
+                 L: Optional[int] = None) -> int:
     ok = (AAO_OK, AAO_ENOTCONV) if allow_notconv else (AAO_OK,)
-    return _check(h, load_library().aao_solve_ci(h, _ptr(b), _ptr(x), float(tol), int(max_outer), int(inner_its),
-                                                 1 if use_x0 else 0, float(l_min), float(l_max), int(fixed_its)),
+    return _check(h, load_library().aao_solve_ci(h, _ptr(b, L, "b"), _ptr(x, L, "x"), float(tol), int(max_outer),
+                                                 int(inner_its), 1 if use_x0 else 0, float(l_min), float(l_max),
+                                                 int(fixed_its)),
                   ok)
 
 
@@ -249,11 +274,17 @@ def aao_profile_get(h) -> dict:
 def aao_precond_apply_noalloc(dim: int, n: Sequence[int], kx, ky, kz, ell: int, alpha: float,
                               prec: int, inner_its: int, mu_max: float, r, z, stream=None) -> int:
     """Allocation-free, handle-free preconditioner apply (device pointers only)."""
-    n3 = (C.c_int64 * 3)(*[int(v) for v in (list(n) + [1, 1, 1])[:3]])
+    g = _grid(n)
+    n3 = (C.c_int64 * 3)(*g)
+    L = int(ell) * g[0] * g[1] * g[2]
+    fx, fy, fz = _face_counts(int(dim), n)
+    px = _ptr(kx, fx if kx is not None else None, "kx")
+    py = _ptr(ky, fy if ky is not None else None, "ky")
+    pz = _ptr(kz, fz if kz is not None else None, "kz")
     buf = C.create_string_buffer(512)
     rc = load_library().aao_precond_apply_noalloc(
-        int(dim), n3, _ptr(kx) or None, _ptr(ky) or None, _ptr(kz) or None, int(ell), float(alpha),
-        int(prec), int(inner_its), float(mu_max), _ptr(r), _ptr(z), stream, buf, len(buf))
+        int(dim), n3, px or None, py or None, pz or None, int(ell), float(alpha),
+        int(prec), int(inner_its), float(mu_max), _ptr(r, L, "r"), _ptr(z, L, "z"), stream, buf, len(buf))
     if rc != AAO_OK:
         raise AaoError(rc, buf.value.decode(errors="replace"))
     return rc
@@ -318,8 +349,12 @@ class Batch:
     def solve(self, bs, xs, tol, max_outer, allow_notconv=False):
         lib = load_library()
         n = len(self.solvers)
-        pb = (C.c_void_p * n)(*[_ptr(v) for v in bs])
-        px = (C.c_void_p * n)(*[_ptr(v) for v in xs])
+        if len(bs) != n or len(xs) != n:
+            raise ValueError("Batch.solve: need one b and one x per member (%d), got %d and %d"
+                             % (n, len(bs), len(xs)))
+        Ls = [s.ell * s.N for s in self.solvers]
+        pb = (C.c_void_p * n)(*[_ptr(v, L, "b[%d]" % i) for i, (v, L) in enumerate(zip(bs, Ls))])
+        px = (C.c_void_p * n)(*[_ptr(v, L, "x[%d]" % i) for i, (v, L) in enumerate(zip(xs, Ls))])
         rc = lib.aao_batch_solve(self.hb, pb, px, float(tol), int(max_outer))
         ok = (AAO_OK, AAO_ENOTCONV) if allow_notconv else (AAO_OK,)
         if rc not in ok:
@@ -363,22 +398,27 @@ class Solver:
         self.N = self.n[0] * self.n[1] * self.n[2]
         self.h = aao_create(dim, n, kx, ky, kz, ell, alpha, opt)
 
+    @property
+    def L(self) -> int:
+        """Float64 values of one block vector (ell * N)."""
+        return self.ell * self.N
+
     def matvec(self, x, y):
-        return aao_matvec(self.h, x, y)
+        return aao_matvec(self.h, x, y, self.L)
 
     def precond_apply(self, r, z):
-        return aao_precond_apply(self.h, r, z)
+        return aao_precond_apply(self.h, r, z, self.L)
 
     def solve(self, b, x, tol, max_outer, inner_its=0, use_x0=False, allow_notconv=False):
-        return aao_solve(self.h, b, x, tol, max_outer, inner_its, use_x0, allow_notconv)
+        return aao_solve(self.h, b, x, tol, max_outer, inner_its, use_x0, allow_notconv, self.L)
 
     def solve_ci(self, b, x, tol, max_outer, inner_its=0, use_x0=False, l_min=0.0, l_max=0.0, fixed_its=0,
                  allow_notconv=False):
         return aao_solve_ci(self.h, b, x, tol, max_outer, inner_its, use_x0, l_min, l_max, fixed_its,
-                            allow_notconv)
+                            allow_notconv, self.L)
 
     def solve_fixed(self, b, x, k, inner_its=0):
-        return aao_solve_fixed(self.h, b, x, k, inner_its)
+        return aao_solve_fixed(self.h, b, x, k, inner_its, self.L)
 
     def stats(self):
         return aao_get_stats(self.h)

@@ -91,3 +91,36 @@ def test_assign_iterations_matches_oracle_and_tables(lib):
     assert sum(binding.aao_assign_iterations(10, 100, mx, mn, 1.0, 0.2)) == 193   # Table 3: 3248 = 16 x (10 + 193)
     with pytest.raises(binding.AaoError):
         binding.aao_assign_iterations(9, 100, mx, mn, 1.0, 0.2)
+
+
+def test_binding_refuses_arrays_of_the_wrong_size_before_any_library_call(lib):
+    # The C ABI takes plain pointers and cannot see sizes; the binding knows ell * N and the face
+    # counts, and refuses a shorter (or longer) array before the call, so no kernel ever reads
+    # past a caller's buffer.
+    from paper_2506_03947_gb300 import binding
+    with pytest.raises(ValueError, match="kx: expected 7"):
+        binding.aao_create(1, (8, 1, 1), np.ones(6), None, None, 10, 1e-2)
+    with pytest.raises(ValueError, match="ky: expected 12"):
+        binding.aao_create(2, (4, 4, 1), np.ones(12), np.ones(11), None, 10, 1e-2)
+    with pytest.raises(ValueError, match="kz: expected 32"):
+        binding.aao_create(3, (4, 4, 3), np.ones(36), np.ones(36), np.ones(31), 10, 1e-2)
+    s = object.__new__(binding.Solver)           # a handle-less solver: only the checks run
+    s.ell, s.n, s.N, s.h = 10, (8, 1, 1), 8, None
+    assert s.L == 80
+    for call in (lambda: s.solve(np.zeros(79), np.zeros(80), 1e-8, 10),
+                 lambda: s.solve(np.zeros(80), np.zeros(81), 1e-8, 10),
+                 lambda: s.matvec(np.zeros((10, 7)), np.zeros((10, 8))),
+                 lambda: s.precond_apply(np.zeros((10, 8)), np.zeros((9, 8))),
+                 lambda: s.solve_fixed(np.zeros(40), np.zeros(80), 3),
+                 lambda: s.solve_ci(np.zeros(80), np.zeros(8), 1e-8, 10)):
+        with pytest.raises(ValueError, match="expected 80 float64 values"):
+            call()
+    with pytest.raises(ValueError, match="r: expected 80"):
+        binding.aao_precond_apply_noalloc(1, (8, 1, 1), np.ones(7), None, None, 10, 1e-2, 1, 5, 0.0,
+                                          np.zeros(8), np.zeros(80))
+    b = object.__new__(binding.Batch)
+    b.solvers, b.hb = [s, s], None
+    with pytest.raises(ValueError, match="one b and one x per member"):
+        b.solve([np.zeros(80)], [np.zeros(80), np.zeros(80)], 1e-8, 10)
+    with pytest.raises(ValueError, match=r"x\[1\]: expected 80"):
+        b.solve([np.zeros(80)] * 2, [np.zeros(80), np.zeros(70)], 1e-8, 10)
