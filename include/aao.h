@@ -283,9 +283,10 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
  * Batched solve: many independent instances of Eq. 1 (different grids, ell,
  * alpha, diffusivities and right-hand sides) solved together.  All members
  * advance in lockstep through right-preconditioned FGMRES; every phase of an
- * Arnoldi step (transform, each Chebyshev step, matvec, each modified
- * Gram-Schmidt step, Givens) is one launch over all members (one per distinct ell for the
- * Chebyshev kernels), each block mapped to an (instance, tile) pair; members
+ * Arnoldi step (transform, the Chebyshev steps - four per launch while they
+ * fit before the last one -, matvec, each modified Gram-Schmidt step, Givens)
+ * is one launch over all members (one per distinct ell for the Chebyshev
+ * kernels), each block mapped to an (instance, tile) pair; members
  * that have converged skip their blocks.  With use_graphs != 0 each Arnoldi
  * step is captured once as a CUDA graph and replayed.  The paper solves one
  * instance at a time; batching is this library's addition for covariance
