@@ -77,3 +77,23 @@ def test_reference_arm_other_ranks_exit_without_work():
                        env=_env(1, 2, _free_port()), cwd=ROOT, capture_output=True, text=True, timeout=180)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_prints_one_complete_line():
+    # The reference arm times the oracle on the host cores (a bounded sample: one FGMRES
+    # iteration, scaled by the oracle's iteration count). Its JSON line carries the contract
+    # keys, with a cpu_baseline describing the run and an e2e that moves no bytes.
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "2d256_p20",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["config"]["workload"] == "2d_lognormal_256x256_l10_a1e-2_p20"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
