@@ -1557,8 +1557,6 @@ int aao_batch_solve(aao_batch B, const double* const* b, double* const* x, doubl
       B->stats[i].converged = 1;
     }
   }
-  const int64_t per_outer_base = 0;
-  (void)per_outer_base;
   while (true) {
     // explicit residuals of the instances still running
     for (int i = 0; i < M; ++i) act[i] = !done[i];
