@@ -1,6 +1,6 @@
 """Right-preconditioned flexible GMRES (oracle).
 
-The paper's outer solver is Chebyshev semi-iteration on Eq. 3; this build
+The paper's outer solver is Chebyshev semi-iteration on Eq. 3; this library
 solves the same preconditioned system with right-preconditioned FGMRES (the
 preconditioned vectors Z_j are kept), modified Gram-Schmidt Arnoldi and Givens
 rotations.  The convergence measure is the paper's relative residual

@@ -13,7 +13,7 @@ real arithmetic with a fixed number K of Krylov iterations each:
     Phi must be positive definite, so a shift with Im(lambda) < 0 is solved through its
     conjugate: (A - lambda) x = b  <=>  (A - conj lambda) conj x = conj b.
 The paper applies the SPD blocks approximately with one V-cycle of an algebraic multigrid
-(HSL_MI20).  This build uses its own multigrid for the same operators, defined here and run
+(HSL_MI20).  This library uses its own multigrid for the same operators, defined here and run
 identically on the GPU:
   * levels: pairwise aggregation of the structured grid (2 x 2 cells, ceil(n/2) per axis), the
     coarse operator being the Galerkin product R B P with piecewise-constant P and R = P^T.

@@ -44,7 +44,7 @@ def test_corollary1_interval_with_exact_preconditioner():
 def test_table3_nc_counts_at_small_alpha():
     # Paper's operator (Eq. 17), n_x = 50, ell = 10, alpha = 0.01: outer CI iterations with P_NC1 and
     # P_NC2 (Table 3).  The paper's random b_1 is not reproducible, so counts are compared to within
-    # 35% (the survey's independent runs gave 42/14/8 and 32/10/6 for 38/13/7 and 27/10/7).
+    # 35% (independent draws of b_1 gave 42/14/8 and 32/10/6 against the table's 38/13/7 and 27/10/7).
     import scipy.sparse as sp
     nx, ell, alpha = 50, 10, 0.01
     A = operator.dirichlet_sparse(nx, ell)
