@@ -355,10 +355,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 inner / f64 outer",
         "data": "synthetic (seeded lognormal diffusivity, b_1 ~ N(0,1))",
-        "config": {"workload": workload_name(args.workload), "grid": [P.n[0], P.n[1]], "N": P.N,
-                   "ell": P.ell, "alpha": P.alpha, "inner_its": p, "tol": P.tol, "restart": 64,
-                   "precision": "mixed", "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": bench_config(args.workload, P, p, world), "precision": "mixed",
         "outer_its": st32["outer_its"], "resid_explicit": st32["resid_explicit"],
         "a_matvecs": st32["a_matvecs"], "wall_ms_per_step": wall * 1e3 / args.steps,
         "roofline": roofline, "cpu_baseline": cpu,
@@ -614,21 +611,53 @@ def run_ncu_batch(args):
                       "outer_its_max": max(its), "outer_its_mean": sum(its) / len(its)}))
 
 
-def cpu_baseline_sample(P, p, outer_its):
-    """Oracle (numpy FP64) on a bounded sample: one outer FGMRES iteration on the full grid.
+def oracle_iterations(P, p, steps, warmup):
+    """Time the oracle (numpy FP64) iteration by iteration on the full workload.
 
-    The sample is one Arnoldi step of the oracle (initial residual, one P_NC
-    apply with all ell frequencies, one script-A product, MGS, Givens, solution
-    update and explicit residual); a full solve is that times the number of
-    outer iterations the solve needs.
+    The oracle solves the workload's system (FGMRES with P_NC, tol 1e-8, x_0 = 0) back to back,
+    as many solves as it takes; every outer FGMRES iteration of that stream is one unit.  The
+    first ``warmup`` iterations are untimed, the next ``steps`` are timed with the host clock
+    (the work between two iterations - the solution update, the explicit residual and the next
+    solve's first residual - falls into the next iteration's interval).  Returns the per-iteration
+    durations and the outer iteration counts of the solves that finished.
     """
     from oracle import solve
-    t = time.perf_counter()
-    solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, 1, fixed_its=1)
-    dt = time.perf_counter() - t
-    return {"value": 1.0 / (dt * outer_its), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one oracle FGMRES iteration on the full %dx%d grid (%.2f s), scaled by %d outer "
-                      "iterations per solve" % (P.n[0], P.n[1], dt, outer_its)}
+
+    stamps = []
+    finished = []
+
+    class Enough(Exception):
+        pass
+
+    def tick(_):
+        stamps.append(time.perf_counter())
+        if len(stamps) > warmup + steps:
+            raise Enough()
+
+    stamps.append(time.perf_counter())
+    try:
+        while True:
+            res = solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, P.tol, 64, callback=tick)
+            finished.append(res.outer_its)
+    except Enough:
+        pass
+    t = stamps[warmup:warmup + steps + 1]
+    return [b - a for a, b in zip(t[:-1], t[1:])], finished
+
+
+def oracle_rate(durations, its_per_solve):
+    """Solve-equivalents per second: timed iterations / (iterations per solve x their time)."""
+    return len(durations) / (its_per_solve * sum(durations))
+
+
+def cpu_baseline_sample(P, p, outer_its):
+    """Oracle (numpy FP64, one thread) on a bounded sample: three consecutive outer FGMRES
+    iterations of a real oracle solve of the full workload, converted to solves/s with the
+    outer iteration count the solve needs."""
+    d, _ = oracle_iterations(P, p, 3, 0)
+    return {"value": oracle_rate(d, outer_its), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "the first 3 outer FGMRES iterations of an oracle solve on the full %dx%d grid "
+                      "(%.2f s), over %d outer iterations per solve" % (P.n[0], P.n[1], sum(d), outer_its)}
 
 
 def oracle_outer_its(workload):
@@ -641,34 +670,47 @@ def oracle_outer_its(workload):
     raise RuntimeError("no oracle iteration count for %s in %s" % (workload, path))
 
 
+def bench_config(workload, P, p, world):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": workload_name(workload),
+            "grid": [P.n[0], P.n[1]], "N": P.N, "ell": P.ell, "alpha": P.alpha, "inner_its": p,
+            "tol": P.tol, "restart": 64,
+            "l2": "working set above the 129 MB L2; the GPU arm also flushes L2 (256 MiB write) "
+                  "between timed steps",
+            "parallelism": "replicas" if world > 1 else "single device"}
+
+
 def run_reference(args):
+    """The oracle on the host cores, one thread (BLAS threads pinned to 1 before numpy loads).
+
+    One step = one outer FGMRES iteration of back-to-back oracle solves of the full workload
+    (measured, not extrapolated); value = solve-equivalents per second = steps / (outer
+    iterations per solve x timed seconds), with the iteration count the oracle's own solves took
+    in this run (from the golden file if no solve finished inside the run)."""
     rank, world, local = dist_env()
     if rank != 0:
         return
-    from oracle import solve
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     P = make_problem(args.workload)
     p = WORKLOADS[args.workload]["p"]
-    its = oracle_outer_its(args.workload)
-    for _ in range(args.warmup):
-        solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, 1, fixed_its=1)
-    times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        solve.solve(P.kx, P.ky, P.kz, P.shape, P.ell, P.alpha, P.b, p, 1e-30, 1, fixed_its=1)
-        times.append(time.perf_counter() - t)
-    dt = sum(times) / len(times)
-    value = 1.0 / (dt * its)
-    sample = ("each step: one oracle FGMRES iteration on the full %dx%d grid (mean %.2f s), "
-              "scaled by the oracle's %d outer iterations per solve (tests/golden/oracle_outer_its.txt)"
-              % (P.n[0], P.n[1], dt, its))
+    d, finished = oracle_iterations(P, p, args.steps, args.warmup)
+    its = finished[0] if finished else oracle_outer_its(args.workload)
+    value = oracle_rate(d, its)
+    T = sum(d)
+    sample = ("each step: one outer FGMRES iteration of back-to-back oracle solves of the full %dx%d grid "
+              "(%d timed, mean %.2f s, after %d untimed); %d outer iterations per oracle solve (%s); "
+              "solves finished in the run: %d" % (P.n[0], P.n[1], len(d), T / len(d), args.warmup, its,
+                                                  "measured in this run" if finished else "golden file",
+                                                  len(finished)))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * its * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": T * 1e3 / len(d),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded lognormal diffusivity, b_1 ~ N(0,1))",
-           "config": {"workload": workload_name(args.workload), "grid": [P.n[0], P.n[1]], "N": P.N,
-                      "ell": P.ell, "alpha": P.alpha, "inner_its": p, "tol": P.tol},
+           "config": bench_config(args.workload, P, p, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "oracle_ms_per_iteration": [round(v * 1e3, 1) for v in d]}
     print(json.dumps(out), flush=True)
 
 

@@ -355,17 +355,21 @@ int64_t aao_kernel_launch_count(void);
  * handle.)
  *
  * Computes the same z = P_NC^{-1} r as aao_precond_apply on a handle created
- * with the same arguments, with the same kernels.  Every temporary (face
- * coefficients, three Chebyshev field buffers, reduction partials) lives in
- * one fixed 16 MiB array in the library's device memory, which every GPU that
- * loads the library holds until the process exits.  Sizes: roughly
- * 36 N + 3 ell N sizeof(T) bytes must fit (T = 4 mixed, 8 FP64), e.g.
- * ell = 10 and N <= 107,000 cells mixed or N <= 60,000 FP64; larger problems
+ * with the same arguments: the same method steps, one Chebyshev step per
+ * launch.  (On 2D mixed-precision grids a handle fuses several steps per
+ * launch, so the two agree to rounding, not bit for bit.)  Every temporary
+ * (face coefficients, three Chebyshev field buffers, reduction partials)
+ * lives in one fixed 16 MiB array in the library's device memory, which every
+ * GPU that loads the library holds until the process exits.  Sizes: about
+ * 3 N sizeof(T) + 3 ell N sizeof(T) bytes must fit (T = 4 mixed, 8 FP64), e.g.
+ * ell = 10 and N <= 127,000 cells mixed or N <= 63,000 FP64; larger problems
  * are rejected with AAO_EINVAL and a message giving the bytes needed.
  *
  *   dim, n, kx, ky, kz, ell, alpha   as aao_create; face arrays, r and z must
- *                  be DEVICE pointers (host pointers would need staging
- *                  buffers and are rejected).
+ *                  be DEVICE pointers of the current device (or managed
+ *                  memory); host pointers would need staging buffers, and
+ *                  another GPU's memory is not reachable from the kernels:
+ *                  both are rejected.
  *   prec, inner_its                  as aao_options.
  *   mu_max         > 1: upper spectral bound to use; 0: the Gershgorin bound.
  *   r, z           ell*N doubles each, block-major, distinct.

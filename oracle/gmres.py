@@ -31,11 +31,14 @@ class GmresResult:
 
 def fgmres(Aop: Op, Mop: Op, b: np.ndarray, tol: float, max_outer: int,
            restart: Optional[int] = None, x0: Optional[np.ndarray] = None,
-           fixed_its: Optional[int] = None) -> GmresResult:
+           fixed_its: Optional[int] = None,
+           callback: Optional[Callable[[int], None]] = None) -> GmresResult:
     """Solve Aop(x) = b with right preconditioner Mop (x = Mop-preconditioned Krylov).
 
     ``fixed_its``: run exactly that many Arnoldi steps in one cycle (no early
     stop, no restart) and return the iterate; used for step-by-step parity.
+    ``callback``: called with the running Arnoldi step count after every step
+    (a timing hook; it sees no vectors and changes nothing).
     """
     shape = b.shape
     bnorm = np.linalg.norm(b)
@@ -86,6 +89,8 @@ def fgmres(Aop: Op, Mop: Op, b: np.ndarray, tol: float, max_outer: int,
             k += 1
             total += 1
             history.append(abs(g[k]) / bnorm)
+            if callback is not None:
+                callback(total)
             # happy breakdown: the Krylov space is invariant, the iterate is exact
             breakdown = hnext <= 1e-14 * beta
             if k < m and not breakdown:

@@ -32,9 +32,9 @@ def precond_op(kx, ky, kz, shape, alpha: float, p: Union[int, Sequence[int]],
 
 def solve(kx, ky, kz, shape, ell: int, alpha: float, b: np.ndarray, p, tol: float,
           max_outer: int, restart: Optional[int] = None, mu_max: Optional[float] = None,
-          fixed_its: Optional[int] = None) -> GmresResult:
+          fixed_its: Optional[int] = None, callback=None) -> GmresResult:
     """FGMRES on script-A x = b (Eq. 1) right-preconditioned by P_NC^{-1}."""
     A = make_block_op(kx, ky, kz, shape)
     M = precond_op(kx, ky, kz, shape, alpha, p, mu_max)
     return fgmres(lambda x: aao_apply(A, x), M, b, tol, max_outer, restart=restart,
-                  fixed_its=fixed_its)
+                  fixed_its=fixed_its, callback=callback)

@@ -9,6 +9,7 @@
 #include "aao.h"
 #include "aao_internal.cuh"
 #include "batch.cuh"
+#include "host_tables.h"
 
 #include <algorithm>
 #include <cmath>
@@ -126,15 +127,31 @@ int fail(aao_ctx* h, int code, const char* fmt, ...) {
                   #call, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
   } while (0)
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
+// Pointer kinds at the boundary: device memory of the current device (or managed memory) is
+// used in place; host memory is staged.  Another GPU's memory is neither: the kernels run on the
+// current device and cannot reach it without peer access, so it is refused.
+enum PtrKind { kPtrHost = 0, kPtrDevice = 1, kPtrOtherDevice = 2 };
+
+PtrKind ptr_kind(const void* p) {
+  if (!p) return kPtrHost;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kPtrHost;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return kPtrDevice;
+  if (a.type != cudaMemoryTypeDevice) return kPtrHost;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return kPtrOtherDevice;
+  }
+  return a.device == dev ? kPtrDevice : kPtrOtherDevice;
 }
+
+bool is_device_ptr(const void* p) { return ptr_kind(p) == kPtrDevice; }
+
+bool is_other_device_ptr(const void* p) { return ptr_kind(p) == kPtrOtherDevice; }
 
 // ---- profiling: events around timed launches -------------------------------
 
@@ -171,104 +188,22 @@ void prof_resolve(aao_ctx* h) {
 }
 
 // Chebyshev and transform tables for the current p (host FP64, Section 2.2 and
-// Lemma 2): lambda_m = alpha^{1/ell} exp(-2 pi i m/ell) paired with the forward
-// transform exp(-2 pi i t m/ell); theta_m = (mu_max+mu_min)/2 - lambda_m,
-// delta = (mu_max-mu_min)/2; rho_0 = delta/theta, rho_k = 1/(2 theta/delta - rho_{k-1}).
+// Lemma 2; host_tables.h), with their FP32 copies.
 void reset_graphs(aao_ctx* h);
 
 void build_tables(aao_ctx* h) {
   reset_graphs(h);
-  using cd = std::complex<double>;
-  const int ell = h->ell, F = ell / 2 + 1, p = h->p;
-  const double pi = 3.14159265358979323846;
-  const double delta = 0.5 * (h->mu_max - h->mu_min);
-  const double root = std::pow(h->alpha, 1.0 / ell);
-  std::vector<cd> lam(F), theta(F);
-  for (int m = 0; m < F; ++m) {
-    lam[m] = root * std::exp(cd(0.0, -2.0 * pi * m / ell));
-    if (m == 0 || 2 * m == ell) lam[m] = cd(lam[m].real(), 0.0);
-    theta[m] = 0.5 * (h->mu_max + h->mu_min) - lam[m];
+  const int p = std::max(h->p, 1);
+  aao::ChebTables tb;
+  aao::cheb_tables_init(tb, h->ell, h->alpha, h->mu_min, h->mu_max);
+  h->steps32.assign(p, StepArgs<float>{});
+  h->steps64.assign(p, StepArgs<double>{});
+  for (int k = 0; k < p; ++k) {
+    aao::cheb_tables_step(tb, k, h->nc2 ? h->palloc : nullptr, h->steps64[k]);
+    h->steps32[k] = aao::narrow_step(h->steps64[k]);
   }
-  h->steps32.assign(std::max(p, 1), StepArgs<float>{});
-  h->steps64.assign(std::max(p, 1), StepArgs<double>{});
-  std::vector<cd> rho_prev(F);
-  for (int m = 0; m < F; ++m) rho_prev[m] = delta / theta[m];
-  for (int k = 0; k < std::max(p, 1); ++k) {
-    StepArgs<double>& s = h->steps64[k];
-    for (int m = 0; m < F; ++m) {
-      cd a(0.0, 0.0), gk(0.0, 0.0);
-      const int pm = h->nc2 ? h->palloc[m] : p;
-      if (k >= 1 && k >= pm) {
-        // frequency m has used its budget (Algorithm 1): a = g = 0 keeps x_{k+1} = x_k
-      } else if (k >= 1 && delta == 0.0) {
-        // single-point segment (one cell, A = I): the delta -> 0 limit is the
-        // exact solve, a = 0 and g = 1/theta
-        gk = 1.0 / theta[m];
-      } else if (k >= 1) {
-        const cd rho = 1.0 / (2.0 * theta[m] / delta - rho_prev[m]);
-        a = rho * rho_prev[m];
-        gk = 2.0 * rho / delta;
-        rho_prev[m] = rho;
-      }
-      // a zero budget means y_m = 0: x_1 = bhat * 0
-      const cd it = (h->nc2 && h->palloc[m] == 0) ? cd(0.0, 0.0) : 1.0 / theta[m];
-      s.lam_re[m] = lam[m].real();
-      s.lam_im[m] = lam[m].imag();
-      s.a_re[m] = a.real();
-      s.a_im[m] = a.imag();
-      s.g_re[m] = gk.real();
-      s.g_im[m] = gk.imag();
-      s.it_re[m] = it.real();
-      s.it_im[m] = it.imag();
-    }
-    StepArgs<float>& f = h->steps32[k];
-    for (int m = 0; m < aao::kMaxF; ++m) {
-      f.lam_re[m] = (float)s.lam_re[m];
-      f.lam_im[m] = (float)s.lam_im[m];
-      f.a_re[m] = (float)s.a_re[m];
-      f.a_im[m] = (float)s.a_im[m];
-      f.g_re[m] = (float)s.g_re[m];
-      f.g_im[m] = (float)s.g_im[m];
-      f.it_re[m] = (float)s.it_re[m];
-      f.it_im[m] = (float)s.it_im[m];
-    }
-  }
-  const double isq = 1.0 / std::sqrt((double)ell);
-  h->dft64 = DftArgs<double>{};
-  h->idft64 = IdftArgs<double>{};
-  for (int t = 0; t < ell; ++t) {
-    h->dft64.gamma[t] = std::pow(h->alpha, (double)t / ell);
-    h->idft64.igamma[t] = std::pow(h->alpha, -(double)t / ell);
-    for (int m = 0; m < F; ++m) {
-      const double ang = 2.0 * pi * (double)((t * m) % ell) / ell;
-      h->dft64.cf[t][m] = std::cos(ang) * isq;
-      h->dft64.sf[t][m] = std::sin(ang) * isq;
-      if (m == 0) {
-        h->idft64.ci[t][m] = isq;
-        h->idft64.si[t][m] = 0.0;
-      } else if (2 * m == ell) {
-        h->idft64.ci[t][m] = (t % 2 == 0) ? isq : -isq;
-        h->idft64.si[t][m] = 0.0;
-      } else {
-        h->idft64.ci[t][m] = 2.0 * std::cos(ang) * isq;
-        h->idft64.si[t][m] = 2.0 * std::sin(ang) * isq;
-      }
-    }
-  }
-  h->dft32 = DftArgs<float>{};
-  h->idft32 = IdftArgs<float>{};
-  for (int t = 0; t < aao::kMaxEll; ++t) {
-    h->dft32.gamma[t] = h->dft64.gamma[t];
-    h->idft32.igamma[t] = h->idft64.igamma[t];
-    h->idft32.igamma_T[t] = (float)h->idft64.igamma[t];
-    h->idft64.igamma_T[t] = h->idft64.igamma[t];
-    for (int m = 0; m < aao::kMaxF; ++m) {
-      h->dft32.cf[t][m] = (float)h->dft64.cf[t][m];
-      h->dft32.sf[t][m] = (float)h->dft64.sf[t][m];
-      h->idft32.ci[t][m] = (float)h->idft64.ci[t][m];
-      h->idft32.si[t][m] = (float)h->idft64.si[t][m];
-    }
-  }
+  aao::transform_tables(h->ell, h->alpha, h->dft64, h->idft64);
+  aao::narrow_transforms(h->dft64, h->idft64, h->dft32, h->idft32);
 }
 
 template <typename T>
@@ -964,6 +899,12 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   }
   if (n[0] > 2000000000LL || n[1] > 8LL * 65535 || n[2] > 65535)
     return fail(nullptr, AAO_EINVAL, "grid too large (n0 <= 2e9, n1 <= 524280, n2 <= 65535)");
+  {
+    // N, ell N and the Krylov bases' byte counts must not wrap: N <= 2^36 cells
+    int64_t nn = 0;
+    if (__builtin_mul_overflow(n[0], n[1], &nn) || __builtin_mul_overflow(nn, n[2], &nn) || nn > (1LL << 36))
+      return fail(nullptr, AAO_EINVAL, "grid too large: n0 * n1 * n2 must be at most 2^36 cells");
+  }
   if (n[0] > 1 && !kx) return fail(nullptr, AAO_EINVAL, "kx is NULL but n0 > 1");
   if (n[1] > 1 && !ky) return fail(nullptr, AAO_EINVAL, "ky is NULL but n1 > 1");
   if (n[2] > 1 && !kz) return fail(nullptr, AAO_EINVAL, "kz is NULL but n2 > 1");
@@ -1046,6 +987,12 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   const double* dk[3] = {nullptr, nullptr, nullptr};
   for (int d = 0; d < 3; ++d) {
     if (fn[d] == 0) continue;
+    if (is_other_device_ptr(fk[d])) {
+      for (double* t : tmp)
+        if (t) cudaFree(t);
+      fail(h, AAO_EINVAL, "face array %d must be host memory or memory of the current device", d);
+      return bail(AAO_EINVAL);
+    }
     if (is_device_ptr(fk[d])) {
       dk[d] = fk[d];
     } else {
@@ -1124,6 +1071,8 @@ int aao_matvec(aao_handle h, const double* x, double* y) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   if (!x || !y || x == y) return fail(h, AAO_EINVAL, "aao_matvec: x and y must be distinct non-NULL pointers");
   h->err.clear();
+  if (is_other_device_ptr(x) || is_other_device_ptr(y))
+    return fail(h, AAO_EINVAL, "aao_matvec: x and y must be host memory or memory of the current device");
   const bool hx = !is_device_ptr(x), hy = !is_device_ptr(y);
   int rc = (hx || hy) ? ensure_stage(h) : AAO_OK;
   if (rc) return rc;
@@ -1145,6 +1094,8 @@ int aao_precond_apply(aao_handle h, const double* r, double* z) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   if (!r || !z || r == z) return fail(h, AAO_EINVAL, "aao_precond_apply: r and z must be distinct non-NULL pointers");
   h->err.clear();
+  if (is_other_device_ptr(r) || is_other_device_ptr(z))
+    return fail(h, AAO_EINVAL, "aao_precond_apply: r and z must be host memory or memory of the current device");
   const bool hr = !is_device_ptr(r), hz = !is_device_ptr(z);
   int rc = (hr || hz) ? ensure_stage(h) : AAO_OK;
   if (rc) return rc;
@@ -1177,6 +1128,8 @@ static int solve_entry(aao_handle h, const double* b, double* x, double tol, int
     h->nc2 = false;
     build_tables(h);
   }
+  if (is_other_device_ptr(b) || is_other_device_ptr(x))
+    return fail(h, AAO_EINVAL, "b and x must be host memory or memory of the current device");
   const bool hb = !is_device_ptr(b), hx = !is_device_ptr(x);
   int rc = (hb || hx) ? ensure_stage(h) : AAO_OK;
   if (rc) return rc;
@@ -1358,6 +1311,8 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
     h->nc2 = false;
     build_tables(h);
   }
+  if (is_other_device_ptr(b) || is_other_device_ptr(x))
+    return fail(h, AAO_EINVAL, "b and x must be host memory or memory of the current device");
   const bool hb = !is_device_ptr(b), hx = !is_device_ptr(x);
   int rc = (hb || hx) ? ensure_stage(h) : AAO_OK;
   if (rc) return rc;

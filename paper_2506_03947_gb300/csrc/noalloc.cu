@@ -13,13 +13,15 @@
 // declared below, which every GPU that loads the library keeps until the
 // process exits.
 //
-// The kernels are the same ones the handle path launches; only where their
-// temporaries live differs.
+// It runs the method's steps one Chebyshev step per launch (the transform, the
+// single-step sweep kernels and the sweep fused with the inverse transform).  A
+// handle fuses several steps per launch on 2D grids in mixed precision, so the
+// two results agree to rounding, not bit for bit.
 #include "aao.h"
 #include "aao_internal.cuh"
+#include "host_tables.h"
 
 #include <cmath>
-#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -56,6 +58,9 @@ int say(char* buf, int len, int code, const char* fmt, ...) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Device memory of the current device, or managed memory.  Memory of another GPU is refused:
+// the kernels run on the current device, and without peer access its addresses are not
+// reachable from there.
 bool on_device(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -63,7 +68,13 @@ bool on_device(const void* p) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Device address of the scratch on the current device; looked up once per
@@ -84,107 +95,59 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-// Same shift, scaling and transform tables as the handle path, for one step at
-// a time (no heap use): lambda_m = alpha^{1/ell} exp(-2 pi i m/ell),
-// theta_m = (mu_max + mu_min)/2 - lambda_m, delta = (mu_max - mu_min)/2.
-struct Tables {
-  int ell, F;
-  double delta;
-  std::complex<double> lam[aao::kMaxF], theta[aao::kMaxF], rho_prev[aao::kMaxF];
+// The shift, scaling and transform tables come from the same host builder as the handle
+// path's (host_tables.h), one step at a time.
+template <typename T>
+struct Narrow;
+template <>
+struct Narrow<double> {
+  static const aao::StepArgs<double>& step(const aao::StepArgs<double>& s) { return s; }
+  static void transforms(const aao::DftArgs<double>& da, const aao::IdftArgs<double>& ia, aao::DftArgs<double>& oa,
+                         aao::IdftArgs<double>& oi) {
+    oa = da;
+    oi = ia;
+  }
 };
-
-void tables_init(Tables& tb, int ell, double alpha, double mu_min, double mu_max) {
-  using cd = std::complex<double>;
-  const double pi = 3.14159265358979323846;
-  tb.ell = ell;
-  tb.F = ell / 2 + 1;
-  tb.delta = 0.5 * (mu_max - mu_min);
-  const double root = std::pow(alpha, 1.0 / ell);
-  for (int m = 0; m < tb.F; ++m) {
-    tb.lam[m] = root * std::exp(cd(0.0, -2.0 * pi * m / ell));
-    if (m == 0 || 2 * m == ell) tb.lam[m] = cd(tb.lam[m].real(), 0.0);
-    tb.theta[m] = 0.5 * (mu_max + mu_min) - tb.lam[m];
-    tb.rho_prev[m] = tb.delta / tb.theta[m];
+template <>
+struct Narrow<float> {
+  static aao::StepArgs<float> step(const aao::StepArgs<double>& s) { return aao::narrow_step(s); }
+  static void transforms(const aao::DftArgs<double>& da, const aao::IdftArgs<double>& ia, aao::DftArgs<float>& oa,
+                         aao::IdftArgs<float>& oi) {
+    aao::narrow_transforms(da, ia, oa, oi);
   }
-}
-
-// Coefficients of step k; must be called for k = 0, 1, 2, ... in order.
-template <typename T>
-void tables_step(Tables& tb, int k, aao::StepArgs<T>& s) {
-  using cd = std::complex<double>;
-  s = aao::StepArgs<T>{};
-  for (int m = 0; m < tb.F; ++m) {
-    cd a(0.0, 0.0), gk(0.0, 0.0);
-    if (k >= 1 && tb.delta == 0.0) {
-      gk = 1.0 / tb.theta[m];
-    } else if (k >= 1) {
-      const cd rho = 1.0 / (2.0 * tb.theta[m] / tb.delta - tb.rho_prev[m]);
-      a = rho * tb.rho_prev[m];
-      gk = 2.0 * rho / tb.delta;
-      tb.rho_prev[m] = rho;
-    }
-    const cd it = 1.0 / tb.theta[m];
-    s.lam_re[m] = (T)tb.lam[m].real();
-    s.lam_im[m] = (T)tb.lam[m].imag();
-    s.a_re[m] = (T)a.real();
-    s.a_im[m] = (T)a.imag();
-    s.g_re[m] = (T)gk.real();
-    s.g_im[m] = (T)gk.imag();
-    s.it_re[m] = (T)it.real();
-    s.it_im[m] = (T)it.imag();
-  }
-}
-
-template <typename T>
-void transform_tables(int ell, double alpha, aao::DftArgs<T>& da, aao::IdftArgs<T>& ia) {
-  const double pi = 3.14159265358979323846;
-  const double isq = 1.0 / std::sqrt((double)ell);
-  da = aao::DftArgs<T>{};
-  ia = aao::IdftArgs<T>{};
-  for (int t = 0; t < ell; ++t) {
-    da.gamma[t] = std::pow(alpha, (double)t / ell);
-    ia.igamma[t] = std::pow(alpha, -(double)t / ell);
-    ia.igamma_T[t] = (T)ia.igamma[t];
-    for (int m = 0; m <= ell / 2; ++m) {
-      const double ang = 2.0 * pi * (double)((t * m) % ell) / ell;
-      da.cf[t][m] = (T)(std::cos(ang) * isq);
-      da.sf[t][m] = (T)(std::sin(ang) * isq);
-      if (m == 0) {
-        ia.ci[t][m] = (T)isq;
-      } else if (2 * m == ell) {
-        ia.ci[t][m] = (T)((t % 2 == 0) ? isq : -isq);
-      } else {
-        ia.ci[t][m] = (T)(2.0 * std::cos(ang) * isq);
-        ia.si[t][m] = (T)(2.0 * std::sin(ang) * isq);
-      }
-    }
-  }
-}
+};
 
 template <typename T>
 cudaError_t run_apply(const aao::GridDesc& g, int dim, int ell, double alpha, int p, double mu_min, double mu_max,
                       const T* cx, const T* cy, const T* cz, T* bhat, T* xa, T* xb, const double* r, double* z,
                       cudaStream_t s) {
-  Tables tb;
-  tables_init(tb, ell, alpha, mu_min, mu_max);
+  aao::ChebTables tb;
+  aao::cheb_tables_init(tb, ell, alpha, mu_min, mu_max);
+  aao::DftArgs<double> da64;
+  aao::IdftArgs<double> ia64;
+  aao::transform_tables(ell, alpha, da64, ia64);
   aao::DftArgs<T> da;
   aao::IdftArgs<T> ia;
-  transform_tables<T>(ell, alpha, da, ia);
-  aao::StepArgs<T> st;
-  tables_step<T>(tb, 0, st);
+  Narrow<T>::transforms(da64, ia64, da, ia);
+  aao::StepArgs<double> s64;
+  auto step = [&](int k) {
+    aao::cheb_tables_step(tb, k, nullptr, s64);
+    return Narrow<T>::step(s64);
+  };
   cudaError_t e;
+  aao::StepArgs<T> st = step(0);
   if (p == 1) return aao::launch_direct<T>(g, dim, ell, r, nullptr, z, da, st, ia, s);
   if ((e = aao::launch_dft<T>(g, dim, ell, r, nullptr, bhat, da, s)) != cudaSuccess) return e;
-  tables_step<T>(tb, 1, st);
+  st = step(1);
   if ((e = aao::launch_step<T>(g, dim, ell, 0, 0, p == 2, cx, cy, cz, bhat, nullptr, xa, z, st, ia, s)) != cudaSuccess)
     return e;
   if (p >= 3) {
-    tables_step<T>(tb, 2, st);
+    st = step(2);
     if ((e = aao::launch_step<T>(g, dim, ell, 1, 1, p == 3, cx, cy, cz, bhat, xa, xb, z, st, ia, s)) != cudaSuccess)
       return e;
   }
   for (int k = 3; k <= p - 1; ++k) {
-    tables_step<T>(tb, k, st);
+    st = step(k);
     T* cur = (k % 2 == 1) ? xb : xa;
     T* prev = (k % 2 == 1) ? xa : xb;
     if ((e = aao::launch_step<T>(g, dim, ell, 1, 2, k == p - 1, cx, cy, cz, bhat, cur, prev, z, st, ia, s)) !=
@@ -215,24 +178,35 @@ extern "C" int aao_precond_apply_noalloc(int dim, const int64_t n[3], const doub
   if (inner_its < 1 || inner_its > 100000) return say(err, err_len, AAO_EINVAL, "inner_its must be in [1, 100000]");
   if (!(mu_max >= 0.0) || !std::isfinite(mu_max) || (mu_max > 0.0 && mu_max <= 1.0))
     return say(err, err_len, AAO_EINVAL, "mu_max must be 0 (Gershgorin bound) or > 1");
+  // N within the array before any size arithmetic (no product below can wrap)
+  int64_t N = 0;
+  if (__builtin_mul_overflow(n[0], n[1], &N) || __builtin_mul_overflow(N, n[2], &N) ||
+      N > (int64_t)(kNoallocScratchBytes / sizeof(float)))
+    return say(err, err_len, AAO_EINVAL,
+               "problem needs more scratch than the %zu bytes the allocation-free entry point holds "
+               "(n = %lld x %lld x %lld)",
+               kNoallocScratchBytes, (long long)n[0], (long long)n[1], (long long)n[2]);
   const double* fk[3] = {kx, ky, kz};
   for (int d = 0; d < 3; ++d)
     if (n[d] > 1 && !on_device(fk[d]))
-      return say(err, err_len, AAO_EINVAL, "face array %d must be a device pointer", d);
+      return say(err, err_len, AAO_EINVAL, "face array %d must be a device pointer on the current device", d);
   if (!on_device(r) || !on_device(z) || r == z)
-    return say(err, err_len, AAO_EINVAL, "r and z must be distinct device pointers");
+    return say(err, err_len, AAO_EINVAL, "r and z must be distinct device pointers on the current device");
 
-  const int64_t N = n[0] * n[1] * n[2];
   const int64_t L = (int64_t)ell * N;
   const size_t Ts = (prec == AAO_MIXED) ? sizeof(float) : sizeof(double);
+  const size_t To = (prec == AAO_MIXED) ? sizeof(double) : sizeof(float);
   const int nb = aao::build_coeff_blocks(N);
-  // layout of the scratch: FP64 coefficients, FP32 coefficients, partials, flag, fields
-  const size_t off_c64 = 0;
-  const size_t off_c32 = off_c64 + 3 * align256(sizeof(double) * (size_t)N);
-  const size_t off_part = off_c32 + 3 * align256(sizeof(float) * (size_t)N);
+  // layout of the scratch: the coefficients of the path's precision, partials, flag, fields.
+  // The set-up kernel also writes the other precision's copy; that copy is dead before the
+  // first field is written, so it sits at the start of the field region.
+  const size_t off_cu = 0;
+  const size_t off_part = off_cu + 3 * align256(Ts * (size_t)N);
   const size_t off_flag = off_part + align256(sizeof(double) * ((size_t)nb + 1));
   const size_t off_field = off_flag + 256;
-  const size_t need = off_field + 3 * align256(Ts * (size_t)L);
+  const size_t field_bytes = 3 * align256(Ts * (size_t)L);
+  const size_t other_bytes = 3 * align256(To * (size_t)N);
+  const size_t need = off_field + (field_bytes > other_bytes ? field_bytes : other_bytes);
   if (need > kNoallocScratchBytes)
     return say(err, err_len, AAO_EINVAL,
                "problem needs %zu bytes of scratch (ell*N = %lld, %s); the allocation-free entry point holds "
@@ -246,6 +220,8 @@ extern "C" int aao_precond_apply_noalloc(int dim, const int64_t n[3], const doub
   cudaStream_t s = (cudaStream_t)stream;
   double* c64[3];
   float* c32[3];
+  const size_t off_c64 = (prec == AAO_MIXED) ? off_field : off_cu;
+  const size_t off_c32 = (prec == AAO_MIXED) ? off_cu : off_field;
   for (int d = 0; d < 3; ++d) {
     c64[d] = (double*)(base + off_c64 + d * align256(sizeof(double) * (size_t)N));
     c32[d] = (float*)(base + off_c32 + d * align256(sizeof(float) * (size_t)N));

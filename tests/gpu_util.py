@@ -60,21 +60,41 @@ def oracle_ops(P):
     return A, mu_max
 
 
-def precond_tol(prec, p, ell, alpha):
-    """Bound on max|z_gpu - z_oracle| / max|z| for one preconditioner apply.
+def precond_tol(prec, p, ell=None, alpha=None):
+    """Bound on the error of one preconditioner apply as measured by precond_err.
 
     Rounding model: a Chebyshev step forms A x_k from differences of
     neighbours (relative error about mu_max u) but multiplies that residual by
     g_k = 2 rho_k / delta, about 2/mu_max, so each step adds an error of a few
     units of roundoff relative to |x|; Chebyshev semi-iteration propagates
-    such errors with at most linear growth in the step count.  The inverse
-    transform mixes all frequencies and the unscaling Gamma^{-1} multiplies
-    block t by alpha^{-t/ell}, at most alpha^{-(ell-1)/ell}.  With c = 16 for
-    the operations per step and the transforms:
-        tol = 16 (p + 2) u alpha^{-(ell-1)/ell}.
+    such errors with at most linear growth in the step count.  The forward
+    and inverse transforms add a few more units.  Everything up to the
+    unscaling Gamma^{-1} happens on zhat_t = gamma_t z_t, so the error is
+    measured there (precond_err); Gamma^{-1} itself is one rounded product
+    per value.  With c = 16 for the operations per step and the transforms:
+        tol = 16 (p + 2) u.
+    ``ell`` and ``alpha`` are accepted for call-site symmetry and unused.
     """
     u = U32 if prec == 1 else U64
-    return 16.0 * (max(p, 1) + 2) * u * alpha ** (-(ell - 1) / ell)
+    return 16.0 * (max(p, 1) + 2) * u
+
+
+def precond_err(z, ref, ell, alpha):
+    """Error of z against the oracle's ref (both (ell, ...)) in the transformed
+    domain: max_t max|z_t - ref_t| gamma_t / max_t max|ref_t| gamma_t, with
+    gamma_t = alpha^(t/ell) the scaling of Section 2.2 (Eq. 5's Gamma).
+
+    Block t of z is zhat_t / gamma_t, and every rounding error of the apply
+    enters zhat; measuring block t after multiplying back by gamma_t gives
+    each block its own Gamma^{-1} factor instead of the worst block's.
+    """
+    import numpy as np
+    z = np.asarray(z).reshape(ell, -1)
+    ref = np.asarray(ref).reshape(ell, -1)
+    g = float(alpha) ** (np.arange(ell) / ell)
+    num = (np.abs(z - ref).max(axis=1) * g).max()
+    den = (np.abs(ref).max(axis=1) * g).max()
+    return float(num / den) if den > 0 else float(num)
 
 
 def log_record(rec):

@@ -8,7 +8,7 @@ degenerate one-cell grid, 1D/2D/3D stencils and every supported ell.
 import numpy as np
 import pytest
 
-from gpu_util import (U64, ensure_lib, log_record, make_solver, oracle_ops, precond_tol, to_dev,
+from gpu_util import (U64, ensure_lib, log_record, make_solver, oracle_ops, precond_err, precond_tol, to_dev,
                       torch_cuda)
 from oracle import allatonce, operator, precond
 from paper_2506_03947_gb300 import inputs
@@ -77,9 +77,10 @@ def test_precond_parity(name, mk, p, prec):
     zd = torch.empty_like(rd)
     s.precond_apply(rd, zd)
     z = zd.cpu().numpy()
-    err = np.abs(z - ref).max() / np.abs(ref).max()
-    tol = precond_tol(prec, p, P.ell, P.alpha)
-    log_record({"test": "precond", "case": name, "p": p, "prec": prec, "err": err, "tol": tol})
+    err = precond_err(z, ref, P.ell, P.alpha)
+    tol = precond_tol(prec, p)
+    log_record({"test": "precond", "case": name, "p": p, "prec": prec, "err": err, "tol": tol,
+                "ratio": err / tol})
     assert err <= tol, (err, tol)
 
 

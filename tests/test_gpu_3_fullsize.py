@@ -12,7 +12,7 @@ radius p around each sample.
 import numpy as np
 import pytest
 
-from gpu_util import log_record, make_solver, precond_tol, to_dev, torch_cuda
+from gpu_util import log_record, make_solver, precond_err, precond_tol, to_dev, torch_cuda
 from oracle import allatonce, exact, operator, precond, solve
 from paper_2506_03947_gb300 import inputs
 
@@ -70,7 +70,7 @@ def test_precond_sampled_full_size(problem, p, prec):
     rng = np.random.default_rng(3)
     samples = [(0, 0), (n - 1, n - 1), (0, n // 2), (n // 2, n - 1)] + \
         [tuple(int(v) for v in rng.integers(0, n, 2)) for _ in range(4)]
-    tol = precond_tol(prec, p, P.ell, P.alpha)
+    tol = precond_tol(prec, p)
     r3 = r.reshape(P.ell, P.n[1], P.n[0])
     worst = 0.0
     for cy, cx in samples:
@@ -81,9 +81,9 @@ def test_precond_sampled_full_size(problem, p, prec):
         zw = precond.pnc_apply(Aw, rw, P.alpha, 1.0, mu_max, p).reshape(P.ell, y1 - y0, x1 - x0)
         ref = zw[:, cy - y0, cx - x0]
         got = z[:, cy, cx]
-        err = np.abs(got - ref).max() / np.abs(ref).max()
+        err = precond_err(got, ref, P.ell, P.alpha)
         worst = max(worst, err)
-    log_record({"test": "precond_fullsize", "p": p, "prec": prec, "err": worst, "tol": tol})
+    log_record({"test": "precond_fullsize", "p": p, "prec": prec, "err": worst, "tol": tol, "ratio": worst / tol})
     assert worst <= tol, (worst, tol)
 
 

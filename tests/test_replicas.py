@@ -80,11 +80,13 @@ def test_reference_arm_other_ranks_exit_without_work():
 
 
 def test_reference_arm_prints_one_complete_line():
-    # The reference arm times the oracle on the host cores (a bounded sample: one FGMRES
-    # iteration, scaled by the oracle's iteration count). Its JSON line carries the contract
-    # keys, with a cpu_baseline describing the run and an e2e that moves no bytes.
+    # The reference arm times the oracle on the host cores: every step is one measured outer
+    # FGMRES iteration of back-to-back oracle solves (here 16 steps after 2 untimed ones, so the
+    # first solve of 14 iterations finishes inside the run).  Its JSON line carries the contract
+    # keys, a cpu_baseline describing the run, an e2e that moves no bytes, and the same config
+    # object as the GPU arm.
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "2d256_p20",
-                        "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+                        "--steps", "16", "--warmup", "2"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -95,5 +97,22 @@ def test_reference_arm_prints_one_complete_line():
     assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["config"]["workload"] == "2d_lognormal_256x256_l10_a1e-2_p20"
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 1 and cb["sample"]
+    assert "measured in this run" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    per = d["oracle_ms_per_iteration"]
+    assert len(per) == 16
+    assert abs(sum(per) / 16 - d["ms_per_step"]) <= 0.1 + 1e-6 * d["ms_per_step"]
+    # value = 16 iterations / (14 iterations per solve x the timed seconds)
+    assert abs(d["value"] - 16 / (14 * sum(per) / 1e3)) <= 1e-3 * d["value"]
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2506_03947_gb300 import inputs
+    P = inputs.config_2d(n=256, ell=10, alpha=1e-2, inner_its=20, seed_field=11, seed_b=12)
+    assert d["config"] == json.loads(json.dumps(bench.bench_config("2d256_p20", P, 20, 1)))
+
+
+def test_oracle_rate_counts_solve_equivalents():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.oracle_rate([1.0, 1.0, 2.0], 2) == 3 / (2 * 4.0)

@@ -16,7 +16,7 @@ the other tests.
 import numpy as np
 import pytest
 
-from gpu_util import ensure_lib, make_solver, precond_tol, to_dev, torch_cuda
+from gpu_util import ensure_lib, make_solver, precond_err, precond_tol, to_dev, torch_cuda
 from paper_2506_03947_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -36,7 +36,7 @@ def test_noalloc_matches_handle_path_twice(prec, p):
     stream = torch.cuda.current_stream().cuda_stream
     kx, ky, kz = _faces_dev(P)
     ref_solver = make_solver(P, prec, p)
-    tol = precond_tol(prec, p, P.ell, P.alpha)
+    tol = precond_tol(prec, p)
     for call in range(2):
         r = to_dev(np.random.default_rng(10 + call).standard_normal((P.ell, P.N)))
         z_ref = torch.empty_like(r)
@@ -44,7 +44,7 @@ def test_noalloc_matches_handle_path_twice(prec, p):
         z = torch.full_like(r, float("nan"))
         binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, prec, p, 0.0, r, z, stream)
         torch.cuda.synchronize()
-        err = float((z - z_ref).abs().max() / z_ref.abs().max())
+        err = precond_err(z.cpu().numpy(), z_ref.cpu().numpy(), P.ell, P.alpha)
         assert err <= tol, (call, err, tol)
 
 
@@ -61,8 +61,8 @@ def test_noalloc_3d_and_1d_shapes():
         s.precond_apply(r, z_ref)
         z = torch.empty_like(r)
         binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, 1, 9, 0.0, r, z, stream)
-        err = float((z - z_ref).abs().max() / z_ref.abs().max())
-        assert err <= precond_tol(1, 9, P.ell, P.alpha)
+        err = precond_err(z.cpu().numpy(), z_ref.cpu().numpy(), P.ell, P.alpha)
+        assert err <= precond_tol(1, 9)
 
 
 def test_noalloc_refuses_problems_larger_than_its_array():
@@ -77,7 +77,29 @@ def test_noalloc_refuses_problems_larger_than_its_array():
                                           torch.cuda.current_stream().cuda_stream)
     assert ei.value.status == binding.AAO_EINVAL
     assert "scratch" in str(ei.value) and "bytes" in str(ei.value)
-    # host pointers would need staging buffers: refused, not allocated
-    with pytest.raises(binding.AaoError):
-        binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, 1, 5, 0.0,
-                                          np.zeros((P.ell, P.N)), np.zeros((P.ell, P.N)), None)
+    # host pointers would need staging buffers: refused, not allocated.  The problem is small
+    # enough for the array, so the refusal must come from the pointer check.
+    Q = inputs.config_2d(n=32, ell=10, alpha=1e-2)
+    qx, qy, qz = _faces_dev(Q)
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_precond_apply_noalloc(Q.dim, Q.n, qx, qy, qz, Q.ell, Q.alpha, 1, 5, 0.0,
+                                          np.zeros((Q.ell, Q.N)), np.zeros((Q.ell, Q.N)), None)
+    assert ei.value.status == binding.AAO_EINVAL
+    assert "device pointers" in str(ei.value), str(ei.value)
+
+
+def test_noalloc_refuses_memory_of_another_device():
+    # the kernels run on the current device; another GPU's memory is refused before any launch
+    torch = torch_cuda()
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    binding = ensure_lib()
+    Q = inputs.config_2d(n=32, ell=10, alpha=1e-2)
+    kx, ky, kz = _faces_dev(Q)
+    r = torch.zeros((Q.ell, Q.N), dtype=torch.float64, device="cuda:1")
+    z = torch.zeros((Q.ell, Q.N), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_precond_apply_noalloc(Q.dim, Q.n, kx, ky, kz, Q.ell, Q.alpha, 1, 5, 0.0, r, z,
+                                          torch.cuda.current_stream().cuda_stream)
+    assert ei.value.status == binding.AAO_EINVAL
+    assert "current device" in str(ei.value)
