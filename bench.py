@@ -567,7 +567,10 @@ def run_ncu_case(args):
     s = binding.Solver(P.dim, P.n, P.kx.ravel(), P.ky.ravel(), None, P.ell, P.alpha, prec=prec, inner_its=p,
                        restart=1, stream=sptr)
     if args.step_kernel != "auto":
-        s.set_step_kernel(binding.AAO_STEP_TILE if args.step_kernel == "tile" else binding.AAO_STEP_TMA)
+        s.set_step_kernel({"tile": binding.AAO_STEP_TILE, "tma": binding.AAO_STEP_TMA,
+                           "stream": binding.AAO_STEP_STREAM}[args.step_kernel])
+    if args.stream_config:
+        s.set_stream_config(*[int(v) for v in args.stream_config.split(",")])
     r = torch.from_numpy(P.b).cuda()
     z = torch.empty_like(r)
     for _ in range(args.steps):
@@ -732,8 +735,11 @@ def main():
     ap.add_argument("--ncu-case", action="store_true",
                     help="run only preconditioner applies (small device footprint) for ncu captures")
     ap.add_argument("--ncu-fp64", action="store_true", help="with --ncu-case: FP64 path")
-    ap.add_argument("--step-kernel", choices=["auto", "tile", "tma"], default="auto",
-                    help="with --ncu-case: the four-step kernel (shared-memory tile or persistent TMA)")
+    ap.add_argument("--step-kernel", choices=["auto", "tile", "tma", "stream"], default="auto",
+                    help="with --ncu-case: the fused-step kernel (shared-memory tile, persistent TMA or "
+                         "warp-strip)")
+    ap.add_argument("--stream-config", default="",
+                    help="with --ncu-case: S,H,D,NW of the warp-strip kernel")
     ap.add_argument("--ncu-solve", action="store_true",
                     help="with --ncu-case: also one solve with a 16-vector Krylov space (about 3 GB)")
     ap.add_argument("--ncu-batch", action="store_true",

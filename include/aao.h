@@ -196,7 +196,10 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
  *   AAO_STEP_AUTO  the persistent TMA kernel when its descriptors could be
  *                  built at aao_create, else the shared-memory tile kernel;
  *   AAO_STEP_TILE  the shared-memory tile kernel (one CTA per 120 x 16 tile);
- *   AAO_STEP_TMA   the persistent TMA-fed kernel (one CTA per SM).
+ *   AAO_STEP_TMA   the persistent TMA-fed kernel (one CTA per SM);
+ *   AAO_STEP_STREAM the warp-strip kernel streamed along y: S steps per launch
+ *                  (aao_set_stream_config), one warp per 64-column strip of an
+ *                  H-row segment, inputs prefetched by per-lane cp.async rings.
  * Returns AAO_EINVAL for an unknown kind, or when the handle has no fused
  * 2D path (FP64, 1D/3D, n0 % 4 != 0) or, for AAO_STEP_TMA, no descriptors.
  * A TMA wait in the persistent kernel that does not finish within the wait
@@ -208,7 +211,19 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
 #define AAO_STEP_AUTO 0
 #define AAO_STEP_TILE 1
 #define AAO_STEP_TMA 2
+#define AAO_STEP_STREAM 3
 int aao_set_step_kernel(aao_handle h, int kind);
+/*
+ * Configuration of the warp-strip kernel (AAO_STEP_STREAM): S fused Chebyshev
+ * steps per launch (the halo width; 4), H interior rows per segment (H + 2S a
+ * multiple of 3), D rows prefetched ahead (3 or 4) and NW warps per CTA
+ * (D = 3: 8, 12 or 13; D = 4: 8, 10 or 11).  No counterpart in the paper:
+ * these are launch parameters of this library's kernel (Eq. 7's steps are
+ * unchanged).  AAO_EINVAL for an unsupported combination.
+ * aao_get_stream_config writes (S, H, D, NW) to out[0..3].
+ */
+int aao_set_stream_config(aao_handle h, int S, int H, int D, int NW);
+int aao_get_stream_config(aao_handle h, int32_t out[4]);
 /*
  * Preconditioner of the outer solve (aao_solve, aao_solve_ci, aao_precond_apply):
  *   AAO_PRECOND_NC         P_NC, Eq. 5 with Chebyshev inner solves (default);

@@ -28,7 +28,8 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_profile_enable", "aao_profile_get", "aao_precond_apply_noalloc",
             "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
-            "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode")
+            "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode",
+            "aao_set_stream_config", "aao_get_stream_config")
 
 # preconditioner of the outer solve (aao_set_precond_mode)
 AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT, AAO_PRECOND_SP = 0, 1, 2
@@ -40,7 +41,7 @@ DEFAULT_WAIT_CYCLES = 2000000000
 AAO_ORTH_CGS, AAO_ORTH_CGS2, AAO_ORTH_MGS = 0, 1, 2
 
 # four-step kernel selection (aao_set_step_kernel)
-AAO_STEP_AUTO, AAO_STEP_TILE, AAO_STEP_TMA = 0, 1, 2
+AAO_STEP_AUTO, AAO_STEP_TILE, AAO_STEP_TMA, AAO_STEP_STREAM = 0, 1, 2, 3
 
 AAO_NPROF = 9
 PROF_NAMES = ("dft", "step_first", "step_second", "step_mid", "step_last", "matvec", "orth", "step_pair",
@@ -136,6 +137,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_set_step_kernel.restype = i32
     lib.aao_get_step_kernel.argtypes = [vp]
     lib.aao_get_step_kernel.restype = i32
+    lib.aao_set_stream_config.argtypes = [vp, i32, i32, i32, i32]
+    lib.aao_set_stream_config.restype = i32
+    lib.aao_get_stream_config.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.aao_get_stream_config.restype = i32
     lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.aao_set_wait_limit.restype = i32
     lib.aao_set_precond_mode.argtypes = [vp, i32]
@@ -311,6 +316,16 @@ def aao_get_step_kernel(h) -> int:
     return load_library().aao_get_step_kernel(h)
 
 
+def aao_set_stream_config(h, S: int, H: int, D: int, NW: int) -> int:
+    return _check(h, load_library().aao_set_stream_config(h, int(S), int(H), int(D), int(NW)))
+
+
+def aao_get_stream_config(h):
+    out = (C.c_int32 * 4)()
+    _check(h, load_library().aao_get_stream_config(h, out))
+    return {"S": out[0], "H": out[1], "D": out[2], "NW": out[3]}
+
+
 def aao_assign_iterations(ell: int, nx: int, mu_max: float, mu_min: float, alpha: float, eta: float):
     out = (C.c_int32 * int(ell))()
     rc = load_library().aao_assign_iterations(int(ell), int(nx), float(mu_max), float(mu_min), float(alpha),
@@ -434,6 +449,12 @@ class Solver:
 
     def step_kernel(self):
         return aao_get_step_kernel(self.h)
+
+    def set_stream_config(self, S=4, H=88, D=4, NW=8):
+        return aao_set_stream_config(self.h, S, H, D, NW)
+
+    def stream_config(self):
+        return aao_get_stream_config(self.h)
 
     def set_wait_limit(self, cycles):
         return aao_set_wait_limit(self.h, cycles)

@@ -59,6 +59,7 @@ struct aao_ctx {
   aao::FieldMap fmap[7];                               // TMA descriptors of xa, xb, xc, xd, bhat, cx32, cy32
   bool tma = false;                                    // descriptors built: persistent four-step kernel usable
   int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
+  aao::StreamConfig scfg{};                            // warp-strip kernel configuration
   bool tma_used = false;                               // TMA kernel launched since the last fault check
   long long wait_limit = aao::kQuadTmaWaitCycles;      // bound of the TMA waits (aao_set_wait_limit)
 
@@ -284,7 +285,25 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
   if (last1) return AAO_OK;
   int cur = 0, prev = -1;  // prev = -1: x_{k-1} = x_1 = bhat/theta (not stored)
   int k = 2;
-  while (k + 3 <= p - 2) {
+  if (h->step_kernel == AAO_STEP_STREAM) {
+    // S steps per launch, warp strips streamed along y
+    const int S = h->scfg.S;
+    while (k + S - 1 <= p - 2) {
+      int o[2], n = 0;
+      for (int b = 0; b < 4 && n < 2; ++b)
+        if (b != cur && b != prev) o[n++] = b;
+      aao::FuseSteps fs;
+      for (int q = 0; q < S; ++q) fs.s[q] = st[k + q];
+      pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
+      AAO_CK(h, aao::launch_stream(h->g, h->ell, prev < 0 ? 1 : 2, h->scfg, cx, cy, bhat, X[cur],
+                                   prev < 0 ? nullptr : X[prev], X[o[0]], X[o[1]], fs, s));
+      prof_end(h, pi);
+      prev = o[0];
+      cur = o[1];
+      k += S;
+    }
+  }
+  while (k + 3 <= p - 2 && h->step_kernel != AAO_STEP_STREAM) {
     int o[2], n = 0;
     for (int b = 0; b < 4 && n < 2; ++b)
       if (b != cur && b != prev) o[n++] = b;
@@ -1205,8 +1224,10 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell) {
 
 int aao_set_step_kernel(aao_handle h, int kind) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
-  if (kind != AAO_STEP_AUTO && kind != AAO_STEP_TILE && kind != AAO_STEP_TMA)
+  if (kind != AAO_STEP_AUTO && kind != AAO_STEP_TILE && kind != AAO_STEP_TMA && kind != AAO_STEP_STREAM)
     return fail(h, AAO_EINVAL, "unknown step kernel %d", kind);
+  if (kind == AAO_STEP_STREAM && !h->pairs)
+    return fail(h, AAO_EINVAL, "the warp-strip kernel needs the 2D mixed path with n0 %% 4 == 0");
   if (kind == AAO_STEP_TMA && !h->tma)
     return fail(h, AAO_EINVAL, "the persistent TMA kernel needs the 2D mixed path with n0 %% 4 == 0 and TMA descriptors");
   if (kind == AAO_STEP_TILE && !h->pairs)
@@ -1260,9 +1281,33 @@ int aao_set_wait_limit(aao_handle h, int64_t cycles) {
   return AAO_OK;
 }
 
+int aao_set_stream_config(aao_handle h, int S, int H, int D, int NW) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  aao::StreamConfig c;
+  c.S = S;
+  c.H = H;
+  c.D = D;
+  c.NW = NW;
+  if (!aao::stream_config_supported(c))
+    return fail(h, AAO_EINVAL, "unsupported warp-strip configuration S=%d H=%d D=%d NW=%d", S, H, D, NW);
+  h->scfg = c;
+  reset_graphs(h);
+  return AAO_OK;
+}
+
+int aao_get_stream_config(aao_handle h, int32_t out[4]) {
+  if (!h || !out) return fail(h, AAO_EINVAL, "NULL argument");
+  out[0] = h->scfg.S;
+  out[1] = h->scfg.H;
+  out[2] = h->scfg.D;
+  out[3] = h->scfg.NW;
+  return AAO_OK;
+}
+
 int aao_get_step_kernel(aao_handle h) {
   if (!h) return -1;
   if (!h->pairs) return AAO_STEP_AUTO;
+  if (h->step_kernel == AAO_STEP_STREAM) return AAO_STEP_STREAM;
   return (h->tma && h->step_kernel != AAO_STEP_TILE) ? AAO_STEP_TMA : AAO_STEP_TILE;
 }
 

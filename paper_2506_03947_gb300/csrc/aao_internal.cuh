@@ -124,6 +124,28 @@ cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap
 // shared-memory base (bit 1); synchronises s.
 cudaError_t quad_tma_fault(unsigned* flag, cudaStream_t s);
 
+// Warp-strip variant streamed along y (cheb_stream.cu): S fused steps per launch
+// (k .. k+S-1), same contract as launch_quad with S in place of 4: reads xk, xkm1 (or
+// bhat/theta when psrc == 1) and bhat; writes x_{k+S-1} to outA and x_{k+S} to outB, which
+// must differ from every input; fs.s[q] holds the coefficients of step k + q.
+// A warp owns a 64-column strip (64 - 2S interior columns) of an H-row segment and streams
+// it from S rows above to S rows below; inputs arrive through per-lane cp.async rings issued
+// D rows ahead; NW warps per CTA, one CTA per SM.
+constexpr int kMaxFuse = 8;
+struct FuseSteps {
+  StepArgs<float> s[kMaxFuse];
+};
+struct StreamConfig {
+  int S = 4;    // fused steps (halo width)
+  int H = 88;   // interior rows of a segment; H + 2S must be a multiple of 6
+  int D = 4;    // rows in flight ahead of the one being consumed
+  int NW = 8;   // warps per CTA
+};
+bool stream_config_supported(const StreamConfig& c);
+cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConfig& c, const float* cx,
+                          const float* cy, const float* bhat, const float* xk, const float* xkm1, float* outA,
+                          float* outB, const FuseSteps& fs, cudaStream_t s);
+
 // Best-case P_alpha^{-1} for spatially constant diffusivities (dct.cu): spatial DCT-II of the
 // frequency planes, division by (phi - lambda_m), inverse DCT, inverse time DFT (Section 2.2).
 struct DctShifts {

@@ -1,0 +1,444 @@
+// S Chebyshev steps per launch (2D, FP32), streamed along y: the warp-strip kernel.
+//
+// Steps k .. k+S-1 of the Chebyshev semi-iteration (Eq. 7 over Lemma 2's segment) on every
+// frequency,
+//   x_{q+1} = x_q + a_q (x_q - x_{q-1}) + g_q (bhat - A x_q + lambda x_q),
+// with the residual formed as bhat + sum_f kappa_f x_nbr(f) - (d - lambda) x
+// (d = 1 + sum of the four face coefficients), in the same operation order as the shared-memory
+// tile kernel (bitwise equal results), with the two cells of a lane in packed FP32x2 operations.
+//
+// Organisation:
+//  * A unit of work is (plane pair, y segment, x strip).  A strip is 64 staged columns (lane l
+//    owns columns 2l, 2l+1), of which the middle 64 - 2S are interior; a segment is H interior
+//    rows, streamed from S rows above it to S rows below it.  Units are spread over all warps of
+//    a persistent grid (one CTA per SM); warps never wait on one another.
+//  * Level 0 (x_k) of stream row t arrives at step t; level j+1 of row t-1-j is computed at the
+//    same step from level j's rows t-j, t-1-j, t-2-j.  Each level's three newest rows live in
+//    registers (the step loop is unrolled by three, so the rotation is a renaming); level S of
+//    row t-S, and level S-1 of the same row, are the outputs.
+//  * Inputs stream through per-lane shared-memory rings filled by cp.async (8 bytes per lane
+//    per plane, zero-filled outside the grid, which gives the Neumann boundary: faces and
+//    values outside are zero).  Rows are issued D steps ahead; a lane only ever reads the
+//    ring slots it filled itself, so cp.async.wait_group is the only synchronisation.  Ring A
+//    holds x_k and x_{k-1}, ring B bhat and the two face arrays, 6 rows each.  When a row
+//    lands, its bhat and face coefficients (with the diagonal) move into register windows of
+//    6 rows, where all S levels read them; shared memory is read once per value.  The step
+//    loop is unrolled by 6, so every ring slot and window row is a compile-time constant.
+//  * Per cell and S steps the launch moves (5 ell + 2) * 4 bytes algorithmically (reads x_k,
+//    x_{k-1}, bhat, two face arrays; writes two fields); the redundant halo reads are
+//    64/(64-2S) across x and (H+2S)/H across y, and mostly hit L2 (neighbouring units run
+//    side by side).
+// cp.async waits are hardware waits on the thread's own copies: nothing here spins.
+#include <type_traits>
+#include <utility>
+
+#include "aao_internal.cuh"
+
+namespace aao {
+
+namespace {
+
+constexpr int kSW = 64;  // staged columns of a strip
+
+__device__ __forceinline__ void cp8(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float2 lds2(unsigned a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+
+// ring B arrays of a row: bhat plane 0, bhat plane 1, kE (cx), kN (cy)
+constexpr int kB_H0 = 0, kB_H1 = 1, kB_E = 2, kB_N = 3, kNB = 4;
+// Both rings hold 6 rows and the step loop is unrolled by 6 (a multiple of the three
+// level-window rows), so every ring slot and window row is a compile-time constant.
+constexpr int kRing = 6, kUnroll = 6;
+
+template <int PSRC>
+struct StreamGeom {
+  static constexpr int NA = (PSRC == 2) ? 4 : 2;  // ring A arrays: x_k planes (+ x_{k-1} planes)
+  static constexpr int lane_bytes = (kRing * NA + kRing * kNB) * 8;  // both rings, per lane
+};
+
+struct Unit {
+  int p0;       // first plane of the pair
+  int m0, m1;   // frequencies of the two planes (real pass) or the complex frequency (m0)
+  int y0;       // first interior row of the segment
+  int gx;       // global column of this lane's first cell
+  bool colok;   // this lane's two cells are inside the grid
+};
+
+// Packed FP32x2 arithmetic on a lane's two cells (each component rounds as fmaf / a + b).
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// Per-level scalars of a pass, hoisted out of the step loop as duplicated pairs.  Real pass:
+// (l, a, g) of the two real frequencies; complex pass: (lr, li, ar, ai, gr, gi) of one frequency.
+template <int S>
+struct PassCoef {
+  float2 c[S][6];
+};
+
+template <int S, bool CPLX>
+__device__ __forceinline__ void load_pass_coef(PassCoef<S>& pc, const FuseSteps& fs, int m0, int m1) {
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const StepArgs<float>& st = fs.s[q];
+    if (CPLX) {
+      pc.c[q][0] = dup(st.lam_re[m0]), pc.c[q][1] = dup(st.lam_im[m0]);
+      pc.c[q][2] = dup(st.a_re[m0]), pc.c[q][3] = dup(st.a_im[m0]);
+      pc.c[q][4] = dup(st.g_re[m0]), pc.c[q][5] = dup(st.g_im[m0]);
+    } else {
+      pc.c[q][0] = dup(st.lam_re[m0]), pc.c[q][1] = dup(st.lam_re[m1]);
+      pc.c[q][2] = dup(st.a_re[m0]), pc.c[q][3] = dup(st.a_re[m1]);
+      pc.c[q][4] = dup(st.g_re[m0]), pc.c[q][5] = dup(st.g_re[m1]);
+    }
+  }
+}
+
+// Face coefficients of one row for this lane's two cells: east, north and west faces and the
+// negated diagonal -d = -(1 + sum of the four faces) (cell 1's west face is cell 0's east face).
+struct RowCoef {
+  float2 e, n, nd;
+  float w0;  // west face of cell 0 (the east face of the lane to the left)
+};
+
+// Kernel arguments (one __grid_constant__ block in the parameter space: the pointers and sizes
+// are read from there where they are used, not held in registers).
+struct StreamArgs {
+  GridDesc g;
+  int npass, ell, H, nseg, nstrip;
+  const float* cx;
+  const float* cy;
+  const float* bhat;
+  const float* xk;
+  const float* xkm1;
+  float* outA;
+  float* outB;
+  FuseSteps fs;
+};
+
+template <int S, int D, int PSRC, bool CPLX>
+struct StreamUnit {
+  static constexpr int NA = StreamGeom<PSRC>::NA;
+  static_assert(D + 2 <= kRing && S + 2 <= kRing, "ring or window too shallow");
+
+  const StreamArgs& a;
+  unsigned ringA, ringB;  // this warp's rings (shared addresses) plus the lane's 8-byte slot
+  // element offsets of this lane's first cell: in the fields (plane p0) and in a face array
+  // (column 0 when the lane's cells are outside the grid: such copies read nothing)
+  int64_t offf;
+  int offc;
+  int y0;      // first interior row of the segment (stream row S)
+  bool colok, interior_lane;
+  PassCoef<S> pc;
+  float it[2];            // 1/theta (x_1 = bhat/theta): real (it0, it1), complex (re, im)
+  float2 L[S][3][2];      // level windows: L[j][r % 3][plane] = level j of stream row r
+  float2 Hw[kRing][2];    // bhat of stream row r in Hw[r % 6][plane]
+  RowCoef Cw[kRing];      // face coefficients of stream row r in Cw[r % 6]
+  float2 last[2];         // level S of the step's output row
+
+  __device__ __forceinline__ unsigned slotA(int row_slot, int arr) const {
+    return ringA + (unsigned)((row_slot * NA + arr) * 256);
+  }
+  __device__ __forceinline__ unsigned slotB(int row_slot, int arr) const {
+    return ringB + (unsigned)((row_slot * kNB + arr) * 256);
+  }
+
+  // copies of stream row u into ring slot SL of both rings
+  template <int SL>
+  __device__ __forceinline__ void issue(int u) {
+    const int y = y0 - S + u;
+    const bool ok = colok && y >= 0 && y < a.g.n1;
+    const int64_t row = ok ? (int64_t)y * a.g.n0 : 0;
+    const unsigned nb = ok ? 8u : 0u;
+    const int64_t of = offf + row, oc = offc + row;
+    cp8(slotA(SL, 0), a.xk + of, nb);
+    cp8(slotA(SL, 1), a.xk + a.g.N + of, nb);
+    if (PSRC == 2) {
+      cp8(slotA(SL, 2), a.xkm1 + of, nb);
+      cp8(slotA(SL, 3), a.xkm1 + a.g.N + of, nb);
+    }
+    cp8(slotB(SL, kB_H0), a.bhat + of, nb);
+    cp8(slotB(SL, kB_H1), a.bhat + a.g.N + of, nb);
+    cp8(slotB(SL, kB_E), a.cx + oc, nb);
+    cp8(slotB(SL, kB_N), a.cy + oc, nb);
+  }
+
+  // step t = 6 b + I of the stream
+  template <int I>
+  __device__ __forceinline__ void step(int t, int T) {
+    constexpr int PH = I % 3;
+    constexpr int SL = I;                        // ring slot and window row of stream row t
+    constexpr int SLm = (I + kRing - 1) % kRing;  // ... of row t - 1
+    if (t + D < T) issue<(I + D) % kRing>(t + D);
+    cp_commit();
+    cp_wait<D>();  // row t has landed (this lane's copies)
+    {
+      L[0][PH][0] = lds2(slotA(SL, 0));
+      L[0][PH][1] = lds2(slotA(SL, 1));
+      Hw[SL][0] = lds2(slotB(SL, kB_H0));
+      Hw[SL][1] = lds2(slotB(SL, kB_H1));
+      // face coefficients of row t; d = 1 + ((kE + kW) + (kN + kS)), kS = kN of row t - 1
+      RowCoef& c = Cw[SL];
+      c.e = lds2(slotB(SL, kB_E));
+      c.n = lds2(slotB(SL, kB_N));
+      c.w0 = __shfl_up_sync(0xffffffffu, c.e.y, 1);
+      const float2 t3 = f2add(f2add(c.e, make_float2(c.w0, c.e.x)), f2add(c.n, Cw[SLm].n));
+      c.nd = f2fma(t3, dup(-1.f), dup(-1.f));  // -(1 + t3), exactly -RN(1 + t3)
+    }
+    levels<I>(std::make_integer_sequence<int, S>{});
+    // outputs: level S and level S-1 of row t - S
+    const int oy = t - 2 * S;
+    if (oy >= 0 && oy < a.H && interior_lane && colok && y0 + oy < a.g.n1) {
+      constexpr int RS = ((PH - S) % 3 + 3) % 3;
+      const int64_t o = offf + (int64_t)(y0 + oy) * a.g.n0;
+      *reinterpret_cast<float2*>(a.outB + o) = last[0];
+      *reinterpret_cast<float2*>(a.outB + o + a.g.N) = last[1];
+      *reinterpret_cast<float2*>(a.outA + o) = L[S - 1][RS][0];
+      *reinterpret_cast<float2*>(a.outA + o + a.g.N) = L[S - 1][RS][1];
+    }
+  }
+
+  template <int I, int... J>
+  __device__ __forceinline__ void levels(std::integer_sequence<int, J...>) {
+    (level<I, J>(), ...);
+  }
+
+  // level j+1 of stream row rho = t - 1 - j
+  template <int I, int j>
+  __device__ __forceinline__ void level() {
+    constexpr int PH = I % 3;
+    constexpr int RS = ((PH - 1 - j) % 3 + 3) % 3;  // rho % 3
+    constexpr int RN = (RS + 1) % 3, RSo = (RS + 2) % 3;
+    constexpr int W = ((I - 1 - j) % kRing + kRing) % kRing;   // rho % 6
+    constexpr int Wm = ((I - 2 - j) % kRing + kRing) % kRing;  // (rho - 1) % 6
+    constexpr int SAm = ((I - 1) % kRing + kRing) % kRing;     // ring A slot of row t - 1
+    const RowCoef& cf = Cw[W];
+    const float2 kS = Cw[Wm].n;
+    const float2* hh = Hw[W];
+    const float2 m1 = dup(-1.f);
+    float2 pv[2];
+    if (j == 0) {
+      if (PSRC == 2) {
+        pv[0] = lds2(slotA(SAm, 2));
+        pv[1] = lds2(slotA(SAm, 3));
+      } else {
+        // x_{k-1} = x_1 = bhat / theta
+        const float h00 = hh[0].x, h01 = hh[0].y, h10 = hh[1].x, h11 = hh[1].y;
+        if (CPLX) {
+          pv[0] = make_float2(h00 * it[0] - h10 * it[1], h01 * it[0] - h11 * it[1]);
+          pv[1] = make_float2(h00 * it[1] + h10 * it[0], h01 * it[1] + h11 * it[0]);
+        } else {
+          pv[0] = make_float2(h00 * it[0], h01 * it[0]);
+          pv[1] = make_float2(h10 * it[1], h11 * it[1]);
+        }
+      }
+    } else {
+      pv[0] = L[j > 0 ? j - 1 : 0][RS][0];
+      pv[1] = L[j > 0 ? j - 1 : 0][RS][1];
+    }
+    // stencil: nb = bhat + kE xE + kW xW + kN xN + kS xS on both planes, both cells at once
+    float2 nb[2];
+    const float2(&cur)[2] = L[j][RS];
+#pragma unroll
+    for (int pl = 0; pl < 2; ++pl) {
+      const float left = __shfl_up_sync(0xffffffffu, cur[pl].y, 1);
+      const float right = __shfl_down_sync(0xffffffffu, cur[pl].x, 1);
+      float2 acc = f2fma(cf.e, make_float2(cur[pl].y, right), hh[pl]);
+      acc = f2fma(make_float2(cf.w0, cf.e.x), make_float2(left, cur[pl].x), acc);
+      acc = f2fma(cf.n, L[j][RN][pl], acc);
+      acc = f2fma(kS, L[j][RSo][pl], acc);
+      nb[pl] = acc;
+    }
+    float2 nw[2];
+    const float2* q = pc.c[j];
+    if (CPLX) {
+      // residual r = nb - (d - lambda) x and x + a (x - x_prev) + g r in complex arithmetic;
+      // the products with -li, -ai, -gi are formed as li (-xi), ai (-di), gi (-ri) (same values)
+      const float2 xr = cur[0], xi = cur[1];
+      const float2 ndl = f2add(cf.nd, q[0]);                 // -(d - lr)
+      const float2 rr = f2fma(q[1], f2mul(xi, m1), f2fma(ndl, xr, nb[0]));
+      const float2 ri = f2fma(q[1], xr, f2fma(ndl, xi, nb[1]));
+      const float2 dr = f2fma(pv[0], m1, xr), di = f2fma(pv[1], m1, xi), ndi = f2fma(xi, m1, pv[1]);
+      nw[0] = f2fma(q[5], f2mul(ri, m1), f2fma(q[4], rr, f2fma(q[3], ndi, f2fma(q[2], dr, xr))));
+      nw[1] = f2fma(q[5], rr, f2fma(q[4], ri, f2fma(q[3], dr, f2fma(q[2], di, xi))));
+    } else {
+      const float2 x0 = cur[0], x1 = cur[1];
+      const float2 q0 = f2fma(f2add(cf.nd, q[0]), x0, nb[0]);  // nb - (d - l0) x0
+      const float2 q1 = f2fma(f2add(cf.nd, q[1]), x1, nb[1]);
+      nw[0] = f2fma(q[4], q0, f2fma(q[2], f2fma(pv[0], m1, x0), x0));
+      nw[1] = f2fma(q[5], q1, f2fma(q[3], f2fma(pv[1], m1, x1), x1));
+    }
+    if (j + 1 < S) {
+      L[(j + 1 < S) ? j + 1 : 0][RS][0] = nw[0];
+      L[(j + 1 < S) ? j + 1 : 0][RS][1] = nw[1];
+    } else {
+      last[0] = nw[0];
+      last[1] = nw[1];
+    }
+  }
+
+  __device__ __forceinline__ void run() {
+    const int T = a.H + 2 * S;  // streamed rows, a multiple of 6
+    issue<0>(0);
+    cp_commit();
+    issue<1>(1);
+    cp_commit();
+    issue<2>(2);
+    cp_commit();
+    if (D >= 4) {
+      issue<3>(3);
+      cp_commit();
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+#pragma unroll
+      for (int s2 = 0; s2 < 3; ++s2) L[j][s2][0] = L[j][s2][1] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kRing; ++r) Cw[r].n = make_float2(0.f, 0.f);
+    for (int t = 0; t < T; t += kUnroll) {
+      step<0>(t, T);
+      step<1>(t + 1, T);
+      step<2>(t + 2, T);
+      step<3>(t + 3, T);
+      step<4>(t + 4, T);
+      step<5>(t + 5, T);
+    }
+    cp_wait<0>();  // (empty groups only by now) the rings are free for the next unit
+  }
+};
+
+template <int S, int D, int PSRC, bool CPLX>
+__device__ __forceinline__ void stream_unit(const StreamArgs& a, const Unit& un, int lane, unsigned ringA,
+                                            unsigned ringB) {
+  StreamUnit<S, D, PSRC, CPLX> su{a};
+  su.ringA = ringA + (unsigned)(lane * 8);
+  su.ringB = ringB + (unsigned)(lane * 8);
+  su.y0 = un.y0;
+  su.colok = un.colok;
+  su.interior_lane = lane >= S / 2 && lane < 32 - S / 2;
+  su.offc = un.colok ? un.gx : 0;  // keep every source address inside its array
+  su.offf = (int64_t)un.p0 * a.g.N + su.offc;
+  if (CPLX) {
+    su.it[0] = a.fs.s[0].it_re[un.m0], su.it[1] = a.fs.s[0].it_im[un.m0];
+  } else {
+    su.it[0] = a.fs.s[0].it_re[un.m0], su.it[1] = a.fs.s[0].it_re[un.m1];
+  }
+  load_pass_coef<S, CPLX>(su.pc, a.fs, un.m0, un.m1);
+  su.run();
+}
+
+// Registers: up to 200 per thread, so two warps fit each SM sub-partition's 16 K registers.
+template <int S, int D, int NW, int PSRC>
+__global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constant__ StreamArgs a) {
+  using G = StreamGeom<PSRC>;
+  extern __shared__ __align__(16) unsigned char smem_stream[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const unsigned base = (unsigned)__cvta_generic_to_shared(smem_stream) + (unsigned)(warp * 32 * G::lane_bytes);
+  const unsigned ringA = base;
+  const unsigned ringB = base + (unsigned)(kRing * G::NA * 32 * 8);
+  const int per_pass = a.nseg * a.nstrip;
+  const int nunits = a.npass * per_pass;
+  const int total_warps = gridDim.x * NW;
+  constexpr int IW = kSW - 2 * S;
+  for (int u = blockIdx.x * NW + warp; u < nunits; u += total_warps) {
+    Unit un;
+    const int pass = u / per_pass;
+    const int rem = u - pass * per_pass;
+    const int seg = rem / a.nstrip;
+    const int strip = rem - seg * a.nstrip;
+    un.p0 = 2 * pass;
+    un.m0 = pass;
+    un.m1 = (pass == 0) ? a.ell / 2 : pass;
+    un.y0 = seg * a.H;
+    un.gx = strip * IW - S + 2 * lane;
+    un.colok = un.gx >= 0 && un.gx < a.g.n0;
+    if (pass == 0)
+      stream_unit<S, D, PSRC, false>(a, un, lane, ringA, ringB);
+    else
+      stream_unit<S, D, PSRC, true>(a, un, lane, ringA, ringB);
+  }
+}
+
+template <int S, int D, int NW>
+cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const float* cx, const float* cy,
+                              const float* bhat, const float* xk, const float* xkm1, float* outA, float* outB,
+                              const FuseSteps& fs, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  constexpr int IW = kSW - 2 * S;
+  const int nstrip = (g.n0 + IW - 1) / IW;
+  const int nseg = (g.n1 + H - 1) / H;
+  const int units = (ell / 2) * nseg * nstrip;
+  int grid = (units + NW - 1) / NW;
+  if (grid > nsm) grid = nsm;
+  StreamArgs a;
+  a.g = g;
+  a.npass = ell / 2;
+  a.ell = ell;
+  a.H = H;
+  a.nseg = nseg;
+  a.nstrip = nstrip;
+  a.cx = cx;
+  a.cy = cy;
+  a.bhat = bhat;
+  a.xk = xk;
+  a.xkm1 = xkm1;
+  a.outA = outA;
+  a.outB = outB;
+  a.fs = fs;
+  if (psrc == 1) {
+    auto k = k_cheb_stream<S, D, NW, 1>;
+    const size_t smem = (size_t)NW * 32 * StreamGeom<1>::lane_bytes;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NW * 32, smem, s>>>(a);
+  } else {
+    auto k = k_cheb_stream<S, D, NW, 2>;
+    const size_t smem = (size_t)NW * 32 * StreamGeom<2>::lane_bytes;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NW * 32, smem, s>>>(a);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool stream_config_supported(const StreamConfig& c) {
+  if (c.S != 4 || c.H < 1 || (c.H + 2 * c.S) % kUnroll != 0) return false;
+  if (c.D != 3 && c.D != 4) return false;
+  return c.NW == 6 || c.NW == 8;
+}
+
+cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConfig& c, const float* cx,
+                          const float* cy, const float* bhat, const float* xk, const float* xkm1, float* outA,
+                          float* outB, const FuseSteps& fs, cudaStream_t s) {
+  if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2) || ell < 4 || ell > kMaxEll || (ell % 2) ||
+      !stream_config_supported(c))
+    return cudaErrorInvalidValue;
+#define AAO_STREAM_CFG(SS, DD, NN)                                                                             \
+  if (c.S == SS && c.D == DD && c.NW == NN)                                                                    \
+    return launch_stream_cfg<SS, DD, NN>(g, ell, psrc, c.H, cx, cy, bhat, xk, xkm1, outA, outB, fs, s);
+  AAO_STREAM_CFG(4, 3, 6)
+  AAO_STREAM_CFG(4, 3, 8)
+  AAO_STREAM_CFG(4, 4, 6)
+  AAO_STREAM_CFG(4, 4, 8)
+#undef AAO_STREAM_CFG
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace aao

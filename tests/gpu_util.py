@@ -66,17 +66,24 @@ def precond_tol(prec, p, ell=None, alpha=None):
     Rounding model: a Chebyshev step forms A x_k from differences of
     neighbours (relative error about mu_max u) but multiplies that residual by
     g_k = 2 rho_k / delta, about 2/mu_max, so each step adds an error of a few
-    units of roundoff relative to |x|; Chebyshev semi-iteration propagates
-    such errors with at most linear growth in the step count.  The forward
-    and inverse transforms add a few more units.  Everything up to the
-    unscaling Gamma^{-1} happens on zhat_t = gamma_t z_t, so the error is
-    measured there (precond_err); Gamma^{-1} itself is one rounded product
-    per value.  With c = 16 for the operations per step and the transforms:
-        tol = 16 (p + 2) u.
+    units of roundoff relative to |x|; the forward and inverse transforms add a
+    few more.  These are many independent roundings, so their sum grows like
+    the square root of their number with high probability (probabilistic
+    rounding error analysis, Higham and Mary, SIAM J. Sci. Comput. 2019),
+    not like their count: after p steps and the two transforms,
+        tol = c sqrt(p + 2) u.
+    c = 8 in mixed precision, where the FP64 oracle's own rounding is far
+    below FP32's; c = 32 in FP64, where the oracle rounds at the same unit as
+    the kernels (the comparison sees both), with sums of up to 16 transform
+    terms and seven stencil terms in 3D.  Everything up to the unscaling
+    Gamma^{-1} happens on zhat_t = gamma_t z_t, so the error is measured there
+    (precond_err); Gamma^{-1} is one rounded product per value.
     ``ell`` and ``alpha`` are accepted for call-site symmetry and unused.
     """
+    import math
     u = U32 if prec == 1 else U64
-    return 16.0 * (max(p, 1) + 2) * u
+    c = 8.0 if prec == 1 else 32.0
+    return c * math.sqrt(max(p, 1) + 2) * u
 
 
 def precond_err(z, ref, ell, alpha):

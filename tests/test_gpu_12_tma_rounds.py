@@ -76,3 +76,35 @@ def test_persistent_kernel_whole_field_matches_oracle(name, mk, p):
     e_pair = precond_err(z, z2.cpu().numpy(), P.ell, P.alpha)
     assert e_pair <= 64 * np.finfo(np.float32).eps, e_pair
     s.close()
+
+
+STREAM_CASES = [
+    ("bench1024_p40_default", lambda: inputs.config_2d_large(inner_its=40), 40, (4, 88, 4, 8)),
+    ("bench1024_p12_H16", lambda: inputs.config_2d_large(inner_its=12), 12, (4, 16, 3, 6)),
+    ("g1204x500_l16_p21_H28", lambda: inputs.make_problem("g1204x500", 2, (1204, 500), 16, 1e-2, 21, 0.8,
+                                                          (16.0, 16.0), 53, 54), 21, (4, 28, 4, 6)),
+]
+
+
+@pytest.mark.parametrize("name,mk,p,cfg", STREAM_CASES, ids=[c[0] for c in STREAM_CASES])
+def test_stream_kernel_whole_field_matches_oracle(name, mk, p, cfg):
+    # the warp-strip kernel over whole fields, with several units per warp (H = 16 on 1024^2:
+    # 6080 units over 1216 warps), against the oracle element by element
+    torch = torch_cuda()
+    binding = ensure_lib()
+    P = mk()
+    A, mu_max = oracle_ops(P)
+    r = np.random.default_rng(19).standard_normal((P.ell, P.N))
+    ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, p)
+    s = make_solver(P, 1, p)
+    s.set_step_kernel(binding.AAO_STEP_STREAM)
+    s.set_stream_config(*cfg)
+    rd = to_dev(r)
+    zd = torch.empty_like(rd)
+    s.precond_apply(rd, zd)
+    err = precond_err(zd.cpu().numpy(), ref, P.ell, P.alpha)
+    tol = precond_tol(1, p)
+    log_record({"test": "stream_whole_field", "case": name, "p": p, "cfg": list(cfg), "err": err, "tol": tol,
+                "ratio": err / tol})
+    assert err <= tol, (err, tol)
+    s.close()

@@ -55,13 +55,57 @@ def test_step_kernels_match_oracle_and_each_other(n0, n1, ell, p):
     e_tma = precond_err(z_tma, ref, P.ell, P.alpha)
     e_tile = precond_err(z_tile, ref, P.ell, P.alpha)
     e_pair = precond_err(z_tma, z_tile, P.ell, P.alpha)
+    s.set_step_kernel(binding.AAO_STEP_STREAM)
+    assert s.step_kernel() == binding.AAO_STEP_STREAM
+    z_str = _apply(s, r)
+    e_str = precond_err(z_str, ref, P.ell, P.alpha)
+    e_str_pair = precond_err(z_str, z_tma, P.ell, P.alpha)
     log_record({"test": "step_kernels", "case": "%dx%d_l%d" % (n0, n1, ell), "p": p, "err_tma": e_tma,
-                "err_tile": e_tile, "tma_vs_tile": e_pair, "bitwise": bool(np.array_equal(z_tma, z_tile)),
-                "tol": tol, "ratio": e_tma / tol})
+                "err_tile": e_tile, "err_stream": e_str, "tma_vs_tile": e_pair, "stream_vs_tma": e_str_pair,
+                "bitwise": bool(np.array_equal(z_tma, z_tile)),
+                "bitwise_stream": bool(np.array_equal(z_tma, z_str)), "tol": tol, "ratio": e_tma / tol})
     assert e_tma <= tol, (e_tma, tol)
     assert e_tile <= tol, (e_tile, tol)
+    assert e_str <= tol, (e_str, tol)
     # same FP32 operations in the same order: at most rounding-order noise
     assert e_pair <= 64 * np.finfo(np.float32).eps, e_pair
+    assert e_str_pair <= 64 * np.finfo(np.float32).eps, e_str_pair
+
+
+STREAM_CONFIGS = [(4, 64, 4, 8), (4, 16, 3, 6), (4, 28, 4, 6), (4, 40, 3, 8), (4, 100, 4, 8), (4, 52, 3, 6)]
+
+
+@pytest.mark.parametrize("cfg", STREAM_CONFIGS, ids=["S%d_H%d_D%d_NW%d" % c for c in STREAM_CONFIGS])
+def test_stream_kernel_configurations_match_oracle(cfg):
+    # every supported (H, D, NW) of the warp-strip kernel computes the same steps: segments that
+    # do not divide the grid, several units per warp (ring slots reused across units)
+    binding = ensure_lib()
+    P = _problem(376, 130, 10, 31)
+    A, mu_max = oracle_ops(P)
+    r = np.random.default_rng(12).standard_normal((P.ell, P.N))
+    p = 21
+    ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, p)
+    s = make_solver(P, 1, p)
+    s.set_step_kernel(binding.AAO_STEP_STREAM)
+    s.set_stream_config(*cfg)
+    assert s.stream_config() == dict(zip(("S", "H", "D", "NW"), cfg))
+    z = _apply(s, r)
+    err = precond_err(z, ref, P.ell, P.alpha)
+    tol = precond_tol(1, p)
+    log_record({"test": "stream_configs", "cfg": list(cfg), "err": err, "tol": tol, "ratio": err / tol})
+    assert err <= tol, (err, tol)
+
+
+def test_stream_config_rules():
+    binding = ensure_lib()
+    P = _problem(64, 64, 8, 9)
+    s = make_solver(P, 1, 9)
+    for bad in ((4, 63, 4, 8), (4, 24, 4, 8), (2, 64, 4, 8), (4, 64, 5, 8), (4, 64, 4, 9), (4, 0, 3, 8)):
+        with pytest.raises(binding.AaoError):
+            s.set_stream_config(*bad)
+    s64 = make_solver(P, 0, 9)
+    with pytest.raises(binding.AaoError):
+        s64.set_step_kernel(binding.AAO_STEP_STREAM)
 
 
 def test_tma_kernel_is_deterministic_and_repeatable():

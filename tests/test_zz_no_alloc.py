@@ -36,7 +36,9 @@ def test_noalloc_matches_handle_path_twice(prec, p):
     stream = torch.cuda.current_stream().cuda_stream
     kx, ky, kz = _faces_dev(P)
     ref_solver = make_solver(P, prec, p)
-    tol = precond_tol(prec, p)
+    # both sides are GPU applies, each within precond_tol of the exact P_NC^{-1} r: their
+    # difference is within twice that
+    tol = 2.0 * precond_tol(prec, p)
     for call in range(2):
         r = to_dev(np.random.default_rng(10 + call).standard_normal((P.ell, P.N)))
         z_ref = torch.empty_like(r)
@@ -62,7 +64,7 @@ def test_noalloc_3d_and_1d_shapes():
         z = torch.empty_like(r)
         binding.aao_precond_apply_noalloc(P.dim, P.n, kx, ky, kz, P.ell, P.alpha, 1, 9, 0.0, r, z, stream)
         err = precond_err(z.cpu().numpy(), z_ref.cpu().numpy(), P.ell, P.alpha)
-        assert err <= precond_tol(1, 9)
+        assert err <= 2.0 * precond_tol(1, 9)
 
 
 def test_noalloc_refuses_problems_larger_than_its_array():
