@@ -193,8 +193,9 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
 /*
  * Kernel that runs the fused four-step Chebyshev sweeps of the 2D mixed path
  * (no counterpart in the paper; both compute the same steps of Eq. 7):
- *   AAO_STEP_AUTO  the persistent TMA kernel when its descriptors could be
- *                  built at aao_create, else the shared-memory tile kernel;
+ *   AAO_STEP_AUTO  the kernel and configuration chosen by the autotuner or the
+ *                  tune cache (aao_autotune, aao_set_tune_cache), else the
+ *                  warp-strip kernel with its default configuration;
  *   AAO_STEP_TILE  the shared-memory tile kernel (one CTA per 120 x 16 tile);
  *   AAO_STEP_TMA   the persistent TMA-fed kernel (one CTA per SM);
  *   AAO_STEP_STREAM the warp-strip kernel streamed along y: S steps per launch
@@ -224,6 +225,47 @@ int aao_set_step_kernel(aao_handle h, int kind);
  */
 int aao_set_stream_config(aao_handle h, int S, int H, int D, int NW);
 int aao_get_stream_config(aao_handle h, int32_t out[4]);
+
+/*
+ * Autotuner of the fused sweep (no counterpart in the paper: the method's steps are
+ * unchanged; only which kernel runs them, and with which launch parameters, is chosen).
+ * Candidates: AAO_STEP_TILE, AAO_STEP_TMA, and AAO_STEP_STREAM with halo depth S in {2, 4},
+ * segment heights that fill one to three rounds of the device's warps (and one segment per
+ * strip), D in {3, 4} and each supported NW.  Each candidate runs reps + 1 preconditioner
+ * applies on the handle's own staging buffers (the first untimed) and is timed by CUDA events
+ * on the handle's stream; the fastest becomes what AAO_STEP_AUTO selects on h.
+ *   results, max_results: optional array receiving up to max_results candidates with their
+ *                  mean time per apply in microseconds (us_per_apply < 0: did not run);
+ *   n_results:     optional, receives the number of candidates; best: optional, the winner.
+ * The handle needs the fused 2D mixed path (n0 % 4 == 0), P_NC and inner_its >= 3, else
+ * AAO_EINVAL.  Synchronises the handle's stream; allocates the staging buffers if absent.
+ */
+typedef struct {
+  int32_t kind;         /* AAO_STEP_TILE, AAO_STEP_TMA or AAO_STEP_STREAM */
+  int32_t S, H, D, NW;  /* warp-strip configuration (S = 4 and zeros for the other kernels) */
+  int32_t pad;
+  double us_per_apply;  /* mean time of one preconditioner apply */
+} aao_tune_entry;
+int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_results, int* n_results,
+                 aao_tune_entry* best);
+/*
+ * Tune cache: a JSON file {"version": 1, "entries": [{"device", "dim", "n": [n0, n1, n2],
+ * "ell", "prec": "mixed" | "fp64", "p", "kernel": "tile" | "tma" | "stream", "S", "H", "D",
+ * "NW", ...}]} (written by the package's tune module).  aao_set_tune_cache sets its path for
+ * every later aao_create in the process (NULL: none; without a call, the environment
+ * variable AAO_TUNE_CACHE is used); aao_create applies the entry matching the device name,
+ * dim, n, ell and precision (one with the same inner_its preferred) to AAO_STEP_AUTO, and
+ * without one uses the warp-strip kernel with S = 4, D = 3, NW = 8 and the segment height
+ * that fills one round of the device's warps.
+ * aao_tune_lookup performs that lookup on the host alone (no device needed): returns 1 and
+ * fills out = (kind, S, H, D, NW) when an entry matches, 0 when none does, and -AAO_EINVAL
+ * when the file cannot be read or parsed.  device NULL matches any device.
+ * aao_get_tuning writes (kernel in use, S, H, D, NW, 1 if chosen by the tuner or the cache).
+ */
+int aao_set_tune_cache(const char* path);
+int aao_tune_lookup(const char* path, const char* device, int dim, const int64_t n[3], int ell, int prec, int p,
+                    int32_t out[5]);
+int aao_get_tuning(aao_handle h, int32_t out[6]);
 /*
  * Preconditioner of the outer solve (aao_solve, aao_solve_ci, aao_precond_apply):
  *   AAO_PRECOND_NC         P_NC, Eq. 5 with Chebyshev inner solves (default);

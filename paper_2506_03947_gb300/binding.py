@@ -29,7 +29,8 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
             "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode",
-            "aao_set_stream_config", "aao_get_stream_config")
+            "aao_set_stream_config", "aao_get_stream_config", "aao_autotune", "aao_tune_lookup",
+            "aao_set_tune_cache", "aao_get_tuning")
 
 # preconditioner of the outer solve (aao_set_precond_mode)
 AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT, AAO_PRECOND_SP = 0, 1, 2
@@ -64,6 +65,11 @@ class aao_stats(C.Structure):
                 ("n_hist", C.c_int32), ("a_matvecs", C.c_int64), ("resid_est", C.c_double),
                 ("resid_explicit", C.c_double), ("mu_min", C.c_double), ("mu_max", C.c_double),
                 ("hist", C.c_double * AAO_MAX_HIST)]
+
+
+class aao_tune_entry(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("S", C.c_int32), ("H", C.c_int32), ("D", C.c_int32), ("NW", C.c_int32),
+                ("pad", C.c_int32), ("us_per_apply", C.c_double)]
 
 
 class aao_profile(C.Structure):
@@ -141,6 +147,15 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_set_stream_config.restype = i32
     lib.aao_get_stream_config.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.aao_get_stream_config.restype = i32
+    lib.aao_autotune.argtypes = [vp, i32, C.POINTER(aao_tune_entry), i32, C.POINTER(i32), C.POINTER(aao_tune_entry)]
+    lib.aao_autotune.restype = i32
+    lib.aao_tune_lookup.argtypes = [C.c_char_p, C.c_char_p, i32, C.POINTER(C.c_int64), i32, i32, i32,
+                                    C.POINTER(C.c_int32)]
+    lib.aao_tune_lookup.restype = i32
+    lib.aao_set_tune_cache.argtypes = [C.c_char_p]
+    lib.aao_set_tune_cache.restype = i32
+    lib.aao_get_tuning.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.aao_get_tuning.restype = i32
     lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.aao_set_wait_limit.restype = i32
     lib.aao_set_precond_mode.argtypes = [vp, i32]
@@ -326,6 +341,47 @@ def aao_get_stream_config(h):
     return {"S": out[0], "H": out[1], "D": out[2], "NW": out[3]}
 
 
+KERNEL_NAMES = {AAO_STEP_AUTO: "auto", AAO_STEP_TILE: "tile", AAO_STEP_TMA: "tma", AAO_STEP_STREAM: "stream"}
+
+
+def _tune_dict(e):
+    return {"kernel": KERNEL_NAMES.get(e.kind, str(e.kind)), "S": e.S, "H": e.H, "D": e.D, "NW": e.NW,
+            "us_per_apply": e.us_per_apply}
+
+
+def aao_autotune(h, reps: int = 3, max_results: int = 256):
+    """Time every fused-sweep candidate on the handle; returns (best, all candidates)."""
+    res = (aao_tune_entry * max_results)()
+    n = C.c_int32(0)
+    best = aao_tune_entry()
+    _check(h, load_library().aao_autotune(h, int(reps), res, int(max_results), C.byref(n), C.byref(best)))
+    return _tune_dict(best), [_tune_dict(res[i]) for i in range(min(n.value, max_results))]
+
+
+def aao_tune_lookup(path: str, device, dim: int, n: Sequence[int], ell: int, prec: int, p: int):
+    """Host-only lookup in a tune cache: the matching entry as a dict, None, or AaoError."""
+    out = (C.c_int32 * 5)()
+    g = (C.c_int64 * 3)(*_grid(n))
+    rc = load_library().aao_tune_lookup(path.encode(), device.encode() if device else None, int(dim), g, int(ell),
+                                        int(prec), int(p), out)
+    if rc < 0:
+        raise AaoError(-rc, "tune cache %s cannot be read or parsed" % path)
+    if rc == 0:
+        return None
+    return {"kernel": KERNEL_NAMES.get(out[0], str(out[0])), "S": out[1], "H": out[2], "D": out[3], "NW": out[4]}
+
+
+def aao_set_tune_cache(path) -> int:
+    return load_library().aao_set_tune_cache(path.encode() if path else None)
+
+
+def aao_get_tuning(h):
+    out = (C.c_int32 * 6)()
+    _check(h, load_library().aao_get_tuning(h, out))
+    return {"kernel": KERNEL_NAMES.get(out[0], str(out[0])), "S": out[1], "H": out[2], "D": out[3], "NW": out[4],
+            "tuned": bool(out[5])}
+
+
 def aao_assign_iterations(ell: int, nx: int, mu_max: float, mu_min: float, alpha: float, eta: float):
     out = (C.c_int32 * int(ell))()
     rc = load_library().aao_assign_iterations(int(ell), int(nx), float(mu_max), float(mu_min), float(alpha),
@@ -455,6 +511,12 @@ class Solver:
 
     def stream_config(self):
         return aao_get_stream_config(self.h)
+
+    def autotune(self, reps=3):
+        return aao_autotune(self.h, reps)
+
+    def tuning(self):
+        return aao_get_tuning(self.h)
 
     def set_wait_limit(self, cycles):
         return aao_set_wait_limit(self.h, cycles)

@@ -35,77 +35,9 @@ using aao::IdftArgs;
 using aao::ScLayout;
 using aao::StepArgs;
 
-struct aao_ctx {
-  int dim = 0;
-  int64_t n[3] = {1, 1, 1};
-  int64_t N = 0, L = 0;
-  int ell = 0;
-  double alpha = 0.0;
-  int prec = AAO_MIXED;
-  int p = 20;                    // Chebyshev steps run per apply (max over frequencies)
-  int palloc[aao::kMaxF] = {};   // per-frequency steps m = 0..ell/2 (NC2); all == p for NC1
-  bool nc2 = false;
-  int m = 64;
-  int orth = AAO_ORTH_MGS;
-  double mu_min = 1.0, mu_max = 0.0;
-  cudaStream_t stream = nullptr;
-  GridDesc g{};
+#include "aao_ctx.h"
 
-  double *cx64 = nullptr, *cy64 = nullptr, *cz64 = nullptr;
-  float *cx32 = nullptr, *cy32 = nullptr, *cz32 = nullptr;
-  void *bhat = nullptr, *xa = nullptr, *xb = nullptr;  // Chebyshev fields (float or double)
-  void *xc = nullptr, *xd = nullptr;                   // extra fields for fused step pairs (2D mixed)
-  bool pairs = false;                                  // fused two-step kernels in use
-  aao::FieldMap fmap[7];                               // TMA descriptors of xa, xb, xc, xd, bhat, cx32, cy32
-  bool tma = false;                                    // descriptors built: persistent four-step kernel usable
-  int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
-  aao::StreamConfig scfg{};                            // warp-strip kernel configuration
-  bool tma_used = false;                               // TMA kernel launched since the last fault check
-  long long wait_limit = aao::kQuadTmaWaitCycles;      // bound of the TMA waits (aao_set_wait_limit)
-
-  // CUDA graphs of Arnoldi step j (preconditioner, script-A product, Gram-Schmidt, Givens,
-  // read-back of the residual estimate), captured on first use and replayed; dropped when
-  // the tables, the step kernel or the wait limit change.
-  int pmode = AAO_PRECOND_NC;     // aao_set_precond_mode
-  aao::DctPlan* dct = nullptr;    // best-case P_alpha (AAO_PRECOND_EXACT_DCT)
-  aao::SpPlan* sp = nullptr;      // P_SP (AAO_PRECOND_SP)
-  std::vector<cudaGraphExec_t> step_graphs;
-  cudaStream_t gstream = nullptr;  // non-blocking stream the graphs are captured on and run on
-  cudaEvent_t gevent = nullptr;    // orders gstream after the caller's stream
-  std::vector<long long> step_graph_launches;
-  std::vector<char> step_graph_tma;
-  double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
-  double* sc = nullptr;                                // small scalars, ScLayout
-  unsigned* counter = nullptr;                         // last-block ticket of the MGS steps (0 at rest)
-  double* partials = nullptr;                          // reduction partials
-  int64_t part_cap = 0;
-  double *stage_a = nullptr, *stage_b = nullptr;       // staging for host pointers (L each)
-  double* pinned = nullptr;                            // pinned host scalars
-
-  std::vector<StepArgs<float>> steps32;    // index k = 0 .. p-1 (0 holds 1/theta for p = 1)
-  std::vector<StepArgs<double>> steps64;
-  DftArgs<float> dft32{};
-  DftArgs<double> dft64{};
-  IdftArgs<float> idft32{};
-  IdftArgs<double> idft64{};
-
-  aao_stats stats{};
-  std::string err;
-
-  // event timing of kernel classes (aao_profile_*)
-  struct Pending {
-    int cls;
-    int e0;
-    int launches;
-    double bytes;
-  };
-  bool prof = false;
-  std::vector<cudaEvent_t> events;
-  std::vector<Pending> pending;
-  aao_profile profacc{};
-};
-
-static std::string g_create_error;
+std::string g_create_error;
 
 namespace {
 
@@ -285,7 +217,8 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
   if (last1) return AAO_OK;
   int cur = 0, prev = -1;  // prev = -1: x_{k-1} = x_1 = bhat/theta (not stored)
   int k = 2;
-  if (h->step_kernel == AAO_STEP_STREAM) {
+  const int kind = aao::effective_step_kernel(h);
+  if (kind == AAO_STEP_STREAM) {
     // S steps per launch, warp strips streamed along y
     const int S = h->scfg.S;
     while (k + S - 1 <= p - 2) {
@@ -303,14 +236,14 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
       k += S;
     }
   }
-  while (k + 3 <= p - 2 && h->step_kernel != AAO_STEP_STREAM) {
+  while (k + 3 <= p - 2 && kind != AAO_STEP_STREAM) {
     int o[2], n = 0;
     for (int b = 0; b < 4 && n < 2; ++b)
       if (b != cur && b != prev) o[n++] = b;
     aao::QuadSteps qs;
     for (int q = 0; q < 4; ++q) qs.s[q] = st[k + q];
     pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
-    if (h->tma && h->step_kernel != AAO_STEP_TILE) {
+    if (h->tma && kind == AAO_STEP_TMA) {
       AAO_CK(h, aao::launch_quad_tma(h->g, h->ell, prev < 0 ? 1 : 2, h->fmap[5], h->fmap[6], h->fmap[cur],
                                      h->fmap[prev < 0 ? cur : prev], h->fmap[4], X[o[0]], X[o[1]], qs,
                                      h->wait_limit, s));
@@ -747,125 +680,27 @@ int solve_ci_impl(aao_ctx* h, const double* b, double* x, double tol, int max_it
 
 }  // namespace
 
-// ---- batched solve -----------------------------------------------------------------
-
-struct aao_batch_ctx {
-  int M = 0, p = 0, m = 0;
-  bool mgs = true;  // modified Gram-Schmidt when every member uses it, else CGS2
-  std::vector<aao_ctx*> mem;
-  cudaStream_t stream = nullptr;
-  bool use_graphs = true;
-  std::vector<aao::BInst> hI;
-  aao::BInst* dI = nullptr;
-  int* dact = nullptr;
-  int* dkvec = nullptr;
-  double* dout = nullptr;
-  double* hout = nullptr;  // pinned, 2M
-  std::vector<void*> owned;
-  std::vector<std::pair<int, aao::WorkList>> wdft, wstep, wquad;  // per ell
-  aao::WorkList wmv{}, wred{}, wone{}, wmgs{};
-  std::vector<cudaGraphExec_t> graphs;
-  std::vector<long long> graph_launches;
-  std::vector<aao_stats> stats;
-  std::string err;
-};
-
-namespace {
-
-int bfail(aao_batch_ctx* b, int code, const char* fmt, ...) {
+namespace aao {
+int handle_fail(aao_ctx* h, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
-  if (b) b->err = buf;
+  if (h) h->err = buf;
   else g_create_error = buf;
   return code;
 }
-
-#define AAO_BCK(b, call)                                                                                  \
-  do {                                                                                                    \
-    cudaError_t e_ = (call);                                                                              \
-    if (e_ != cudaSuccess)                                                                                \
-      return bfail((b), e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA, "%s: %s (%s:%d)", #call, \
-                   cudaGetErrorString(e_), __FILE__, __LINE__);                                           \
-  } while (0)
-
-int make_worklist(aao_batch_ctx* B, const std::vector<int>& inst, const std::vector<int>& blocks, aao::WorkList* out) {
-  std::vector<int> start(inst.size() + 1, 0);
-  for (size_t i = 0; i < inst.size(); ++i) start[i + 1] = start[i] + blocks[i];
-  int* ds = nullptr;
-  int* di = nullptr;
-  AAO_BCK(B, cudaMalloc(&ds, sizeof(int) * start.size()));
-  B->owned.push_back(ds);
-  AAO_BCK(B, cudaMalloc(&di, sizeof(int) * std::max<size_t>(1, inst.size())));
-  B->owned.push_back(di);
-  AAO_BCK(B, cudaMemcpy(ds, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
-  if (!inst.empty()) AAO_BCK(B, cudaMemcpy(di, inst.data(), sizeof(int) * inst.size(), cudaMemcpyHostToDevice));
-  out->start = ds;
-  out->inst = di;
-  out->cnt = (int)inst.size();
-  out->total = start.back();
-  return AAO_OK;
+bool is_device_ptr(const void* p) { return ::is_device_ptr(p); }
+bool is_other_device_ptr(const void* p) { return ::is_other_device_ptr(p); }
+int handle_precond(aao_ctx* h, const double* r, const double* rscale, double* z) {
+  return ::precond(h, r, rscale, z);
 }
+void handle_reset_graphs(aao_ctx* h) { ::reset_graphs(h); }
+int handle_check_tma(aao_ctx* h) { return ::check_tma(h); }
+int handle_ensure_stage(aao_ctx* h) { return ::ensure_stage(h); }
+}  // namespace aao
 
-// Phases of Arnoldi step j for every active instance, in stream order.
-int batch_step_launches(aao_batch_ctx* B, int j) {
-  cudaStream_t s = B->stream;
-  for (size_t g = 0; g < B->wdft.size(); ++g)
-    AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second,
-                                  B->wquad[g].second, B->p, j, s));
-  AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 0, j, s));
-  if (B->mgs) AAO_BCK(B, aao::batch_mgs(B->dI, B->dact, B->wmgs, j, s));
-  else AAO_BCK(B, aao::batch_gram_schmidt(B->dI, B->dact, B->wred, B->wone, j, s));
-  AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 0, j, B->dkvec, B->dout, s));
-  AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 3, j, B->dkvec, B->dout, s));
-  return AAO_OK;
-}
-
-int batch_run_step(aao_batch_ctx* B, int j) {
-  if (!B->use_graphs) return batch_step_launches(B, j);
-  if ((int)B->graphs.size() <= j) {
-    B->graphs.resize(j + 1, nullptr);
-    B->graph_launches.resize(j + 1, 0);
-  }
-  if (!B->graphs[j]) {
-    const long long c0 = aao::launch_count();
-    AAO_BCK(B, cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = batch_step_launches(B, j);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(B->stream, &graph);
-    if (rc) {
-      if (graph) cudaGraphDestroy(graph);
-      return rc;
-    }
-    AAO_BCK(B, ec);
-    cudaGraphExec_t exec = nullptr;
-    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    AAO_BCK(B, ei);
-    B->graphs[j] = exec;
-    B->graph_launches[j] = aao::launch_count() - c0;
-    aao::count_launch_add(-B->graph_launches[j]);  // captured, not run: counted at each replay
-  }
-  AAO_BCK(B, cudaGraphLaunch(B->graphs[j], B->stream));
-  aao::count_launch_add(B->graph_launches[j]);
-  return AAO_OK;
-}
-
-int batch_read(aao_batch_ctx* B) {
-  AAO_BCK(B, cudaMemcpyAsync(B->hout, B->dout, sizeof(double) * 2 * B->M, cudaMemcpyDeviceToHost, B->stream));
-  AAO_BCK(B, cudaStreamSynchronize(B->stream));
-  return AAO_OK;
-}
-
-int batch_set_active(aao_batch_ctx* B, const std::vector<int>& act) {
-  AAO_BCK(B, cudaMemcpyAsync(B->dact, act.data(), sizeof(int) * B->M, cudaMemcpyHostToDevice, B->stream));
-  AAO_BCK(B, cudaStreamSynchronize(B->stream));  // act is a host temporary
-  return AAO_OK;
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -1070,6 +905,11 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
     if (ok) ok = aao::encode_coef_map(&h->fmap[6], h->cy32, h->g) == cudaSuccess;
     cudaGetLastError();
     h->tma = ok;
+    // the default fused-sweep kernel: warp strips with a configuration sized to the device,
+    // unless the tune cache holds an entry for this grid
+    h->auto_kind = AAO_STEP_STREAM;
+    h->scfg = aao::default_stream_config(h->g, ell);
+    aao::apply_tune_cache(h);
   }
   AAO_CK_CREATE(cudaMalloc(&h->V, sizeof(double) * h->L * (h->m + 1)));
   AAO_CK_CREATE(cudaMalloc(&h->Z, sizeof(double) * h->L * h->m));
@@ -1307,8 +1147,9 @@ int aao_get_stream_config(aao_handle h, int32_t out[4]) {
 int aao_get_step_kernel(aao_handle h) {
   if (!h) return -1;
   if (!h->pairs) return AAO_STEP_AUTO;
-  if (h->step_kernel == AAO_STEP_STREAM) return AAO_STEP_STREAM;
-  return (h->tma && h->step_kernel != AAO_STEP_TILE) ? AAO_STEP_TMA : AAO_STEP_TILE;
+  const int k = aao::effective_step_kernel(h);
+  if (k == AAO_STEP_TMA && !h->tma) return AAO_STEP_TILE;
+  return k;
 }
 
 int aao_assign_iterations(int ell, int64_t nx, double mu_max, double mu_min, double alpha, double eta, int32_t* out) {
@@ -1385,257 +1226,6 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
   if (rc == AAO_OK || rc == AAO_ENOTCONV) AAO_CK(h, cudaStreamSynchronize(h->stream));
   return rc;
 }
-
-void aao_batch_destroy(aao_batch hb) {
-  if (!hb) return;
-  if (hb->stream) cudaStreamSynchronize(hb->stream);
-  for (cudaGraphExec_t g : hb->graphs)
-    if (g) cudaGraphExecDestroy(g);
-  for (void* p : hb->owned) cudaFree(p);
-  if (hb->dI) cudaFree(hb->dI);
-  if (hb->dact) cudaFree(hb->dact);
-  if (hb->dkvec) cudaFree(hb->dkvec);
-  if (hb->dout) cudaFree(hb->dout);
-  if (hb->hout) cudaFreeHost(hb->hout);
-  if (hb->stream) cudaStreamDestroy(hb->stream);
-  delete hb;
-}
-
-int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int use_graphs) {
-  if (!out) return bfail(nullptr, AAO_EINVAL, "aao_batch_create: out is NULL");
-  *out = nullptr;
-  if (count < 1 || !members) return bfail(nullptr, AAO_EINVAL, "need at least one member handle");
-  for (int i = 0; i < count; ++i) {
-    const aao_ctx* h = members[i];
-    if (!h) return bfail(nullptr, AAO_EINVAL, "member %d is NULL", i);
-    if (h->prec != AAO_MIXED || h->dim != 2 || h->n[0] % 4 != 0)
-      return bfail(nullptr, AAO_EINVAL, "member %d: the batch runs mixed-precision 2D grids with n0 %% 4 == 0", i);
-    if (h->p < 2) return bfail(nullptr, AAO_EINVAL, "member %d: the batch needs inner_its >= 2", i);
-    if (h->p != members[0]->p || h->m != members[0]->m)
-      return bfail(nullptr, AAO_EINVAL, "members must share inner_its and restart (member %d differs)", i);
-    if (h->m < 2) return bfail(nullptr, AAO_EINVAL, "restart must be >= 2");
-  }
-  aao_batch_ctx* B = new aao_batch_ctx();
-  B->M = count;
-  B->p = members[0]->p;
-  B->m = members[0]->m;
-  B->use_graphs = use_graphs != 0;
-  auto bail = [&](int code) {
-    g_create_error = B->err;
-    aao_batch_destroy(B);
-    return code;
-  };
-#define AAO_BCK_CREATE(call)               \
-  do {                                     \
-    cudaError_t e_ = (call);               \
-    if (e_ != cudaSuccess) {               \
-      bfail(B, e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-      return bail(e_ == cudaErrorMemoryAllocation ? AAO_ENOMEM : AAO_ECUDA); \
-    }                                      \
-  } while (0)
-  AAO_BCK_CREATE(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking));
-  B->hI.resize(count);
-  std::vector<int> all(count), bdft(count), bstep(count), bquad(count), bmv(count), bred(count), bmgs(count),
-      bone(count, 1);
-  std::vector<int> ells;
-  for (int i = 0; i < count; ++i) {
-    aao_ctx* h = members[i];
-    B->mem.push_back(h);
-    aao::BInst& bi = B->hI[i];
-    bi.g = h->g;
-    bi.ell = h->ell;
-    bi.m = h->m;
-    bi.L = h->L;
-    bi.nbred = aao::reduction_blocks(h->L);
-    bi.nbmgs = aao::batch_mgs_blocks(h->L);
-    bi.nbmv = (int)(((h->n[0] + 31) / 32) * ((h->n[1] + 7) / 8));
-    bi.cx32 = h->cx32;
-    bi.cy32 = h->cy32;
-    bi.cx64 = h->cx64;
-    bi.cy64 = h->cy64;
-    bi.bhat = (float*)h->bhat;
-    bi.xa = (float*)h->xa;
-    bi.xb = (float*)h->xb;
-    bi.xc = (float*)h->xc;
-    bi.xd = (float*)h->xd;
-    bi.V = h->V;
-    bi.Z = h->Z;
-    bi.sc = h->sc;
-    bi.partials = h->partials;
-    bi.counter = h->counter;
-    if (h->orth != AAO_ORTH_MGS) B->mgs = false;
-    void* dsteps = nullptr;
-    AAO_BCK_CREATE(cudaMalloc(&dsteps, sizeof(aao::StepArgs<float>) * h->steps32.size()));
-    B->owned.push_back(dsteps);
-    AAO_BCK_CREATE(cudaMemcpy(dsteps, h->steps32.data(), sizeof(aao::StepArgs<float>) * h->steps32.size(),
-                              cudaMemcpyHostToDevice));
-    void* dda = nullptr;
-    void* dia = nullptr;
-    AAO_BCK_CREATE(cudaMalloc(&dda, sizeof(aao::DftArgs<float>)));
-    B->owned.push_back(dda);
-    AAO_BCK_CREATE(cudaMalloc(&dia, sizeof(aao::IdftArgs<float>)));
-    B->owned.push_back(dia);
-    AAO_BCK_CREATE(cudaMemcpy(dda, &h->dft32, sizeof(aao::DftArgs<float>), cudaMemcpyHostToDevice));
-    AAO_BCK_CREATE(cudaMemcpy(dia, &h->idft32, sizeof(aao::IdftArgs<float>), cudaMemcpyHostToDevice));
-    bi.steps = (const aao::StepArgs<float>*)dsteps;
-    bi.da = (const aao::DftArgs<float>*)dda;
-    bi.ia = (const aao::IdftArgs<float>*)dia;
-    bi.b = nullptr;
-    bi.x = nullptr;
-    all[i] = i;
-    bdft[i] = (int)((h->N + 255) / 256);
-    bstep[i] = (int)(((h->n[0] + 127) / 128) * ((h->n[1] + 7) / 8));
-    bquad[i] = aao::batch_quad_tiles(h->g);
-    bmv[i] = bi.nbmv;
-    bred[i] = bi.nbred;
-    bmgs[i] = bi.nbmgs;
-    if (std::find(ells.begin(), ells.end(), h->ell) == ells.end()) ells.push_back(h->ell);
-  }
-  for (int ell : ells) {
-    std::vector<int> inst, nd, ns, nq;
-    for (int i = 0; i < count; ++i)
-      if (members[i]->ell == ell) {
-        inst.push_back(i);
-        nd.push_back(bdft[i]);
-        ns.push_back(bstep[i]);
-        nq.push_back(bquad[i]);
-      }
-    aao::WorkList wd, ws, wq;
-    if (make_worklist(B, inst, nd, &wd) || make_worklist(B, inst, ns, &ws) || make_worklist(B, inst, nq, &wq))
-      return bail(AAO_ECUDA);
-    B->wdft.push_back({ell, wd});
-    B->wstep.push_back({ell, ws});
-    B->wquad.push_back({ell, wq});
-  }
-  if (make_worklist(B, all, bmv, &B->wmv) || make_worklist(B, all, bred, &B->wred) ||
-      make_worklist(B, all, bmgs, &B->wmgs) || make_worklist(B, all, bone, &B->wone))
-    return bail(AAO_ECUDA);
-  AAO_BCK_CREATE(cudaMalloc(&B->dI, sizeof(aao::BInst) * count));
-  AAO_BCK_CREATE(cudaMalloc(&B->dact, sizeof(int) * count));
-  AAO_BCK_CREATE(cudaMalloc(&B->dkvec, sizeof(int) * count));
-  AAO_BCK_CREATE(cudaMalloc(&B->dout, sizeof(double) * 2 * count));
-  AAO_BCK_CREATE(cudaMallocHost(&B->hout, sizeof(double) * 2 * count));
-  B->stats.assign(count, aao_stats{});
-  *out = B;
-#undef AAO_BCK_CREATE
-  return AAO_OK;
-}
-
-int aao_batch_solve(aao_batch B, const double* const* b, double* const* x, double tol, int max_outer) {
-  if (!B) return bfail(nullptr, AAO_EINVAL, "NULL batch");
-  B->err.clear();
-  if (!b || !x) return bfail(B, AAO_EINVAL, "b and x must be arrays of M device pointers");
-  if (!(tol > 0.0 && tol < 1.0) || max_outer < 1) return bfail(B, AAO_EINVAL, "need 0 < tol < 1 and max_outer >= 1");
-  const int M = B->M;
-  for (int i = 0; i < M; ++i) {
-    if (!is_device_ptr(b[i]) || !is_device_ptr(x[i]) || b[i] == x[i])
-      return bfail(B, AAO_EINVAL, "instance %d: b and x must be distinct device pointers", i);
-    B->hI[i].b = b[i];
-    B->hI[i].x = x[i];
-  }
-  AAO_BCK(B, cudaDeviceSynchronize());  // inputs may come from any stream
-  AAO_BCK(B, cudaMemcpyAsync(B->dI, B->hI.data(), sizeof(aao::BInst) * M, cudaMemcpyHostToDevice, B->stream));
-  for (int i = 0; i < M; ++i) {
-    AAO_BCK(B, cudaMemsetAsync(x[i], 0, sizeof(double) * B->hI[i].L, B->stream));
-    B->stats[i] = aao_stats{};
-    B->stats[i].mu_min = B->mem[i]->mu_min;
-    B->stats[i].mu_max = B->mem[i]->mu_max;
-  }
-  std::vector<int> act(M, 1), done(M, 0), kvec(M, 0), total(M, 0);
-  std::vector<double> bnorm(M, 0.0), beta(M, 0.0);
-  int rc = batch_set_active(B, act);
-  if (rc) return rc;
-  AAO_BCK(B, aao::batch_norm2_b(B->dI, B->dact, B->wred, B->stream));
-  AAO_BCK(B, aao::batch_reduce(B->dI, B->dact, B->wone, 4, B->stream));
-  AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 4, 0, B->dkvec, B->dout, B->stream));
-  if ((rc = batch_read(B))) return rc;
-  for (int i = 0; i < M; ++i) {
-    bnorm[i] = B->hout[2 * i];
-    if (!std::isfinite(bnorm[i])) return bfail(B, AAO_ENUMERIC, "instance %d: ||b|| is not finite", i);
-    if (bnorm[i] == 0.0) {
-      done[i] = 1;
-      B->stats[i].converged = 1;
-    }
-  }
-  while (true) {
-    // explicit residuals of the instances still running
-    for (int i = 0; i < M; ++i) act[i] = !done[i];
-    if (std::none_of(act.begin(), act.end(), [](int v) { return v; })) break;
-    if ((rc = batch_set_active(B, act))) return rc;
-    AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 1, 0, B->stream));
-    AAO_BCK(B, aao::batch_reduce(B->dI, B->dact, B->wone, 3, B->stream));
-    AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 5, 0, B->dkvec, B->dout, B->stream));
-    if ((rc = batch_read(B))) return rc;
-    for (int i = 0; i < M; ++i) {
-      if (!act[i]) continue;
-      const double rn = B->hout[2 * i];
-      const double rel = rn / bnorm[i];
-      B->stats[i].resid_explicit = rel;
-      B->stats[i].a_matvecs += B->hI[i].ell;
-      if (!std::isfinite(rel)) return bfail(B, AAO_ENUMERIC, "instance %d: residual is not finite", i);
-      if (rel < tol) {
-        done[i] = 1;
-        B->stats[i].converged = 1;
-        act[i] = 0;
-      } else if (total[i] >= max_outer) {
-        done[i] = 1;
-        act[i] = 0;
-      } else {
-        beta[i] = rn;
-        B->stats[i].cycles++;
-      }
-    }
-    if (std::none_of(act.begin(), act.end(), [](int v) { return v; })) break;
-    if ((rc = batch_set_active(B, act))) return rc;
-    AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 1, 0, B->dkvec, B->dout, B->stream));
-    std::vector<int> part = act;
-    std::fill(kvec.begin(), kvec.end(), 0);
-    for (int j = 0; j < B->m; ++j) {
-      if ((rc = batch_run_step(B, j))) return rc;
-      if ((rc = batch_read(B))) return rc;
-      bool changed = false;
-      for (int i = 0; i < M; ++i) {
-        if (!act[i]) continue;
-        const double est = B->hout[2 * i], hn = B->hout[2 * i + 1];
-        total[i]++;
-        kvec[i] = j + 1;
-        aao_stats& st = B->stats[i];
-        st.outer_its = total[i];
-        st.resid_est = est;
-        st.a_matvecs += (int64_t)B->hI[i].ell * (B->p + 1);
-        if (st.n_hist < AAO_MAX_HIST) st.hist[st.n_hist++] = est;
-        if (!std::isfinite(est) || !std::isfinite(hn))
-          return bfail(B, AAO_ENUMERIC, "instance %d: non-finite value in Arnoldi step %d", i, total[i]);
-        if (est < tol || hn <= 1e-14 * beta[i] || total[i] >= max_outer) {
-          act[i] = 0;
-          changed = true;
-        }
-      }
-      if (std::none_of(act.begin(), act.end(), [](int v) { return v; })) break;
-      if (changed && (rc = batch_set_active(B, act))) return rc;
-    }
-    // solution update of this cycle's participants
-    if ((rc = batch_set_active(B, part))) return rc;
-    AAO_BCK(B, cudaMemcpyAsync(B->dkvec, kvec.data(), sizeof(int) * M, cudaMemcpyHostToDevice, B->stream));
-    AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 2, 0, B->dkvec, B->dout, B->stream));
-    AAO_BCK(B, aao::batch_xupdate(B->dI, B->dact, B->wred, B->dkvec, B->stream));
-    AAO_BCK(B, cudaStreamSynchronize(B->stream));  // kvec is a host temporary
-  }
-  AAO_BCK(B, cudaStreamSynchronize(B->stream));
-  int nconv = 0;
-  for (int i = 0; i < M; ++i) nconv += B->stats[i].converged;
-  if (nconv < M) return bfail(B, AAO_ENOTCONV, "%d of %d instances did not converge in %d iterations", M - nconv, M,
-                              max_outer);
-  return AAO_OK;
-}
-
-int aao_batch_get_stats(aao_batch B, int i, aao_stats* s) {
-  if (!B || !s || i < 0 || i >= B->M) return bfail(B, AAO_EINVAL, "bad batch stats request");
-  *s = B->stats[i];
-  return AAO_OK;
-}
-
-const char* aao_batch_last_error(aao_batch B) { return B ? B->err.c_str() : g_create_error.c_str(); }
 
 int aao_get_stats(aao_handle h, aao_stats* s) {
   if (!h || !s) return fail(h, AAO_EINVAL, "NULL argument");

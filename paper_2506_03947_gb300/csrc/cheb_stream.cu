@@ -337,7 +337,8 @@ __device__ __forceinline__ void stream_unit(const StreamArgs& a, const Unit& un,
   su.run();
 }
 
-// Registers: up to 200 per thread, so two warps fit each SM sub-partition's 16 K registers.
+// Registers: 8 warps of up to 200 per thread (two per SM sub-partition of 16 K registers); the
+// two-step variant with 12 warps stays within 168.
 template <int S, int D, int NW, int PSRC>
 __global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constant__ StreamArgs a) {
   using G = StreamGeom<PSRC>;
@@ -419,8 +420,9 @@ cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const
 }  // namespace
 
 bool stream_config_supported(const StreamConfig& c) {
-  if (c.S != 4 || c.H < 1 || (c.H + 2 * c.S) % kUnroll != 0) return false;
+  if ((c.S != 2 && c.S != 4) || c.H < 1 || c.H > 4096 || (c.H + 2 * c.S) % kUnroll != 0) return false;
   if (c.D != 3 && c.D != 4) return false;
+  if (c.S == 2) return c.NW == 8 || c.NW == 12 || c.NW == 16;
   return c.NW == 6 || c.NW == 8;
 }
 
@@ -437,6 +439,12 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
   AAO_STREAM_CFG(4, 3, 8)
   AAO_STREAM_CFG(4, 4, 6)
   AAO_STREAM_CFG(4, 4, 8)
+  AAO_STREAM_CFG(2, 3, 8)
+  AAO_STREAM_CFG(2, 3, 12)
+  AAO_STREAM_CFG(2, 4, 8)
+  AAO_STREAM_CFG(2, 4, 12)
+  AAO_STREAM_CFG(2, 3, 16)
+  AAO_STREAM_CFG(2, 4, 16)
 #undef AAO_STREAM_CFG
   return cudaErrorInvalidValue;
 }

@@ -50,6 +50,7 @@ def test_persistent_kernel_whole_field_matches_oracle(name, mk, p):
     r = np.random.default_rng(17).standard_normal((P.ell, P.N))
     ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, p)
     s = make_solver(P, 1, p)
+    s.set_step_kernel(binding.AAO_STEP_TMA)
     assert s.step_kernel() == binding.AAO_STEP_TMA
     rd = to_dev(r)
     zd = torch.empty_like(rd)

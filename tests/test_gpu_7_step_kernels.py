@@ -46,6 +46,8 @@ def test_step_kernels_match_oracle_and_each_other(n0, n1, ell, p):
     r = np.random.default_rng(7).standard_normal((P.ell, P.N))
     ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, p)
     s = make_solver(P, 1, p)
+    assert s.step_kernel() == binding.AAO_STEP_STREAM      # the default without a tune cache
+    s.set_step_kernel(binding.AAO_STEP_TMA)
     assert s.step_kernel() == binding.AAO_STEP_TMA
     z_tma = _apply(s, r)
     s.set_step_kernel(binding.AAO_STEP_TILE)
@@ -136,7 +138,7 @@ def test_step_kernel_selection_rules():
         sm.set_step_kernel(7)
     sm.set_step_kernel(binding.AAO_STEP_TILE)
     sm.set_step_kernel(binding.AAO_STEP_AUTO)
-    assert sm.step_kernel() == binding.AAO_STEP_TMA
+    assert sm.step_kernel() == binding.AAO_STEP_STREAM
 
 
 def test_full_solve_with_either_kernel_agrees():
@@ -146,7 +148,7 @@ def test_full_solve_with_either_kernel_agrees():
     P = _problem(260, 70, 10, 11)
     b = to_dev(P.b)
     out = {}
-    for kind in (binding.AAO_STEP_TMA, binding.AAO_STEP_TILE):
+    for kind in (binding.AAO_STEP_TMA, binding.AAO_STEP_TILE, binding.AAO_STEP_STREAM):
         s = make_solver(P, 1, 20)
         s.set_step_kernel(kind)
         x = torch.zeros_like(b)
@@ -154,8 +156,10 @@ def test_full_solve_with_either_kernel_agrees():
         out[kind] = (x.cpu().numpy(), s.stats()["outer_its"])
     xa, ia = out[binding.AAO_STEP_TMA]
     xb, ib = out[binding.AAO_STEP_TILE]
-    assert ia == ib
+    xc, ic = out[binding.AAO_STEP_STREAM]
+    assert ia == ib == ic
     assert np.abs(xa - xb).max() / np.abs(xb).max() < 1e-7
+    assert np.abs(xc - xb).max() / np.abs(xb).max() < 1e-7
 
 
 def test_expired_tma_wait_reports_timeout_and_handle_recovers():
@@ -167,6 +171,7 @@ def test_expired_tma_wait_reports_timeout_and_handle_recovers():
     P = _problem(260, 70, 10, 13)
     r = np.random.default_rng(9).standard_normal((P.ell, P.N))
     s = make_solver(P, 1, 20)
+    s.set_step_kernel(binding.AAO_STEP_TMA)
     z_ref = _apply(s, r)
     s.set_wait_limit(0)
     with pytest.raises(binding.AaoError) as ei:
