@@ -108,13 +108,14 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the headline four-step kernel's source: its translation unit and the shared
-    definitions it compiles against (grid descriptor, step tables, tile constants, TMA map)."""
+def kernel_source_hash(kind="tma"):
+    """Hash of a fused-sweep kernel's source: its translation unit and the shared definitions it
+    compiles against (grid descriptor, step tables, tile constants, TMA map, stream config)."""
     import re
     csrc = os.path.join(ROOT, "paper_2506_03947_gb300", "csrc")
     h = hashlib.sha256()
-    with open(os.path.join(csrc, "cheb_quad_tma.cu"), "rb") as fh:
+    unit = {"tma": "cheb_quad_tma.cu", "stream": "cheb_stream.cu", "tile": "cheb_d2.cu"}[kind]
+    with open(os.path.join(csrc, unit), "rb") as fh:
         h.update(fh.read())
     with open(os.path.join(csrc, "aao_internal.cuh")) as fh:
         hdr = fh.read()
@@ -122,18 +123,21 @@ def kernel_source_hash():
             r"struct alignas\(64\) FieldMap \{.*?\};", r"constexpr int kQuadTmaTY = \d+;",
             r"constexpr int kQuadTmaR = \d+;", r"constexpr long long kQuadTmaWaitCycles = [^;]*;",
             r"constexpr int kMaxEll = \d+;"]
+    if kind == "stream":
+        pats = [r"struct GridDesc \{.*?\};", r"struct StepArgs \{.*?\};", r"constexpr int kMaxFuse = \d+;",
+                r"struct FuseSteps \{.*?\};", r"struct StreamConfig \{.*?\};", r"constexpr int kMaxEll = \d+;"]
     for pat in pats:
         m = re.search(pat, hdr, re.S)
         h.update((m.group(0) if m else pat).encode())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key):
+def ncu_traffic(kernel_key, kind="tma"):
     """dram bytes per launch from profiles/ncu_traffic.txt if taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kind)
     with open(path) as f:
         for line in f:
             line = line.split("#", 1)[0].split()
@@ -260,6 +264,13 @@ def run_ours(args):
     s32 = binding.Solver(P.dim, P.n, kx, ky, None, P.ell, P.alpha, prec=binding.AAO_MIXED, inner_its=p,
                          restart=64, stream=sptr)
     sampler = ClockSampler(local) if not args.no_clocks else None
+    # the fused sweep's kernel and launch configuration, chosen by the library's autotuner
+    # (untimed: whole preconditioner applies per candidate, before any timed solve)
+    tune_top = None
+    if not args.no_tune:
+        _, cands = s32.autotune(3)
+        tune_top = sorted(cands, key=lambda c: c["us_per_apply"])[:6]
+    tuning = s32.tuning()
     quad_kind = s32.step_kernel()
     # timed solves run as the library runs them by default (each Arnoldi step replayed from
     # its CUDA graph); the per-kernel-class breakdown comes from a separate profiled pass,
@@ -315,14 +326,19 @@ def run_ours(args):
     avg_ms = mid["ms"] / max(1, mid["launches"])
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
     total_ms_prof = sum(v["ms"] for v in prof.values())
-    kernels = {"step_quad": ("k_cheb_quad_tma<10,2,2> (four fused multi-frequency Chebyshev steps, FP32, "
-                             "persistent, TMA-fed)" if quad_kind == binding.AAO_STEP_TMA else
-                             "k_cheb_quad<10,16,2> (four fused multi-frequency Chebyshev steps, FP32, "
-                             "shared-memory tile)"),
+    quad_names = {binding.AAO_STEP_TMA: "k_cheb_quad_tma<10,2,2> (four fused multi-frequency Chebyshev steps, "
+                                        "FP32, persistent, TMA-fed)",
+                  binding.AAO_STEP_TILE: "k_cheb_quad<10,16,2> (four fused multi-frequency Chebyshev steps, FP32, "
+                                         "shared-memory tile)",
+                  binding.AAO_STEP_STREAM: "k_cheb_stream<S=%d,D=%d,NW=%d> (%d fused multi-frequency Chebyshev "
+                                           "steps, FP32x2, warp strips streamed along y, H=%d, cp.async rings)"
+                                           % (tuning["S"], tuning["D"], tuning["NW"], tuning["S"], tuning["H"])}
+    kernels = {"step_quad": quad_names[quad_kind],
                "step_pair": "k_cheb_pair_v4<10,2> (two fused multi-frequency Chebyshev steps, FP32)",
                "step_mid": "k_cheb_step_v4<10,2,1,2,false> (fused multi-frequency Chebyshev step, FP32)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(dom + "_" + args.workload),
+                "frac": achieved / peak,
+                "traffic": ncu_traffic(dom + "_" + args.workload, binding.KERNEL_NAMES.get(quad_kind, "tma")),
                 "kernel": kernels[dom], "class": dom,
                 "bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
                 "launches": mid["launches"], "peak_source": peak_src + " hbm_gbs",
@@ -362,7 +378,19 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * L, "d2h_bytes_per_step": 8 * L},
         "gpu_launches": launches, "clocks": clocks, "fp64_gpu": fp64, "batch": batch, "rhs3d": rhs3d, "best_case": best,
         "sweep": sweep, "step_wall_ms": [round(w * 1e3, 3) for w in walls32],
+        "fused_sweep": {"tuning": tuning, "fastest_candidates": tune_top},
     }
+    # compact summary last, so that a truncated capture of the line still carries it
+    out["headline"] = {
+        "mixed_solves_s": round(value, 3), "e2e_solves_s": round(e2e_value, 3),
+        "fp64_solves_s": round(fp64["value"], 3) if fp64 else None,
+        "outer_its_mixed": st32["outer_its"], "outer_its_fp64": fp64["outer_its"] if fp64 else None,
+        "mixed_vs_fp64_rel_diff": fp64["mixed_vs_fp64_rel_diff"] if fp64 else None,
+        "fused_kernel": binding.KERNEL_NAMES.get(quad_kind), "fused_us_per_launch": round(avg_ms * 1e3, 2),
+        "roofline_frac": round(achieved / peak, 4),
+        "batch_instance_solves_s": round(batch["value"], 2) if batch else None,
+        "rhs3d_rhs_solves_s": round(rhs3d["value"], 3) if rhs3d else None,
+        "cpu_oracle_solves_s": cpu["value"] if cpu else None}
     if rank == 0:
         print(json.dumps(out), flush=True)
     rep.close()
@@ -725,6 +753,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2d1024_p40")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the default fused sweep)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance workload")

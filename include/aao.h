@@ -207,7 +207,7 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
  * limit (about a second of SM clock by default) makes the enclosing
  * aao_solve / aao_solve_ci / aao_precond_apply return AAO_ETIMEOUT; the
  * kernel first lets its own copies land, so the handle stays usable.  The
- * fault flag is per device.
+ * fault flag is per handle.
  */
 #define AAO_STEP_AUTO 0
 #define AAO_STEP_TILE 1

@@ -246,7 +246,7 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
     if (h->tma && kind == AAO_STEP_TMA) {
       AAO_CK(h, aao::launch_quad_tma(h->g, h->ell, prev < 0 ? 1 : 2, h->fmap[5], h->fmap[6], h->fmap[cur],
                                      h->fmap[prev < 0 ? cur : prev], h->fmap[4], X[o[0]], X[o[1]], qs,
-                                     h->wait_limit, s));
+                                     h->wait_limit, h->tma_fault, s));
       h->tma_used = true;
     } else {
       AAO_CK(h, aao::launch_quad(h->g, h->ell, prev < 0 ? 1 : 2, cx, cy, bhat, X[cur], prev < 0 ? nullptr : X[prev],
@@ -301,7 +301,7 @@ int check_tma(aao_ctx* h) {
   if (!h->tma_used) return AAO_OK;
   h->tma_used = false;
   unsigned flag = 0;
-  AAO_CK(h, aao::quad_tma_fault(&flag, h->stream));
+  AAO_CK(h, aao::quad_tma_fault(h->tma_fault, &flag, h->stream));
   if (flag & 2u) return fail(h, AAO_ECUDA, "four-step TMA kernel: shared-memory base not 128-byte aligned");
   if (flag) return fail(h, AAO_ETIMEOUT, "four-step TMA kernel: a bounded TMA wait expired");
   return AAO_OK;
@@ -725,7 +725,8 @@ void aao_destroy(aao_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   void* dev[] = {h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32, h->bhat, h->xa, h->xb, h->xc,
-                 h->xd,   h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b, h->counter};
+                 h->xd,   h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b, h->counter,
+                 h->tma_fault};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -832,6 +833,8 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
   AAO_CK_CREATE(cudaMemset(h->sc, 0, sizeof(double) * Lsc.size()));
   AAO_CK_CREATE(cudaMalloc(&h->counter, sizeof(unsigned)));
   AAO_CK_CREATE(cudaMemset(h->counter, 0, sizeof(unsigned)));
+  AAO_CK_CREATE(cudaMalloc(&h->tma_fault, sizeof(unsigned)));
+  AAO_CK_CREATE(cudaMemset(h->tma_fault, 0, sizeof(unsigned)));
   AAO_CK_CREATE(cudaMallocHost(&h->pinned, sizeof(double) * 16));
 
   // face arrays: device pointers are used in place, host arrays are staged

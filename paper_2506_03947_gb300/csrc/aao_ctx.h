@@ -54,6 +54,7 @@ struct aao_ctx {
   double *V = nullptr, *Z = nullptr;                   // Krylov bases, (m+1) and m vectors of L
   double* sc = nullptr;                                // small scalars, ScLayout
   unsigned* counter = nullptr;                         // last-block ticket of the MGS steps (0 at rest)
+  unsigned* tma_fault = nullptr;                       // the TMA kernel's fault word (device, 0 at rest)
   double* partials = nullptr;                          // reduction partials
   int64_t part_cap = 0;
   double *stage_a = nullptr, *stage_b = nullptr;       // staging for host pointers (L each)

@@ -119,10 +119,12 @@ cudaError_t encode_coef_map(FieldMap* out, const float* base, const GridDesc& g)
 // wait_limit: bound of each TMA wait in SM clocks (kQuadTmaWaitCycles normally).
 cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap& mcx, const FieldMap& mcy,
                             const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3,
-                            float* out4, const QuadSteps& qs, long long wait_limit, cudaStream_t s);
-// Read and clear the device flag of expired TMA waits (bit 0) or a misaligned
-// shared-memory base (bit 1); synchronises s.
-cudaError_t quad_tma_fault(unsigned* flag, cudaStream_t s);
+                            float* out4, const QuadSteps& qs, long long wait_limit, unsigned* fault,
+                            cudaStream_t s);
+// fault: a device word of the caller (one per handle) in which the kernel ORs 1 when one of
+// its bounded waits expired and 2 when its shared-memory base was misaligned.
+// Read the caller's fault word into *host_flag and clear it; synchronises s.
+cudaError_t quad_tma_fault(unsigned* dev_flag, unsigned* host_flag, cudaStream_t s);
 
 // Warp-strip variant streamed along y (cheb_stream.cu): S fused steps per launch
 // (k .. k+S-1), same contract as launch_quad with S in place of 4: reads xk, xkm1 (or

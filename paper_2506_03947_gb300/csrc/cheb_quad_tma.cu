@@ -26,7 +26,7 @@
 //  * After four levels the interior (lanes 1..30, rows 4..25) holds x_{k+3}
 //    and x_{k+4}; both are stored straight from registers.
 // Every wait on a TMA transaction is bounded (wait_limit SM clocks, about a
-// second by default); on expiry the block records the fault in a device flag,
+// second by default); on expiry the block records the fault in the caller's device flag,
 // waits (with the default bound) for its copies in flight and returns.
 #include <cuda.h>
 
@@ -52,8 +52,6 @@ constexpr int kCoefRows = kRows + 1;    // face coefficients: the staged rows an
 constexpr int kCoef = kCoefRows * kCols;
 constexpr unsigned kCoefBytes = 2u * kCoef * 4u;  // cx and cy boxes
 constexpr size_t kSmemBytes = (size_t)2 * kStage * 4 + (size_t)kCoefBytes + 64;
-
-__device__ unsigned int g_quad_tma_fault = 0;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -328,7 +326,8 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
     k_cheb_quad_tma(GridDesc g, int ntx, int ntiles, const __grid_constant__ FieldMap mcx,
                     const __grid_constant__ FieldMap mcy, const __grid_constant__ FieldMap mxk,
                     const __grid_constant__ FieldMap mxkm1, const __grid_constant__ FieldMap mbhat,
-                    float* __restrict__ out3, float* __restrict__ out4, QuadSteps qa, long long wait_limit) {
+                    float* __restrict__ out3, float* __restrict__ out4, QuadSteps qa, long long wait_limit,
+                    unsigned* __restrict__ fault) {
   constexpr int NPASS = ELL / 2;
   extern __shared__ __align__(1024) float sm[];
   float* coef = sm + 2 * kStage;  // cx box, then cy box: [kCoefRows][kCols], row j = staged row j - 1
@@ -349,7 +348,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
   }
   __syncthreads();
   if (*s_abort) {
-    if (threadIdx.x == 0) atomicOr(&g_quad_tma_fault, 2u);
+    if (threadIdx.x == 0) atomicOr(fault, 2u);
     return;
   }
 
@@ -433,7 +432,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
       mbar_wait(smem_u32(&bars[it & 1]), (unsigned)(it >> 1) & 1u);
       if (pass == 0 && coef_wait_failed) mbar_wait(smem_u32(&bars[2]), (unsigned)j & 1u);
       else if (pass >= 1 && j + 1 < my_tiles) mbar_wait(smem_u32(&bars[2]), (unsigned)(j + 1) & 1u);
-      atomicOr(&g_quad_tma_fault, 1u);
+      atomicOr(fault, 1u);
     }
   }
 }
@@ -441,7 +440,7 @@ __global__ void __launch_bounds__(32 * kRows / R, 1)
 template <int ELL, int R>
 cudaError_t launch_qt(const GridDesc& g, int psrc, const FieldMap& mcx, const FieldMap& mcy, const FieldMap& mxk,
                       const FieldMap& mxkm1, const FieldMap& mbhat, float* out3, float* out4, const QuadSteps& qs,
-                      long long wait_limit, cudaStream_t s) {
+                      long long wait_limit, unsigned* fault, cudaStream_t s) {
   constexpr int NT = 32 * kRows / R;
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -455,12 +454,12 @@ cudaError_t launch_qt(const GridDesc& g, int psrc, const FieldMap& mcx, const Fi
     auto k = k_cheb_quad_tma<ELL, R, 1>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit);
+    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit, fault);
   } else {
     auto k = k_cheb_quad_tma<ELL, R, 2>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit);
+    k<<<grid, NT, kSmemBytes, s>>>(g, ntx, ntiles, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit, fault);
   }
   count_launch();
   return cudaGetLastError();
@@ -525,12 +524,12 @@ cudaError_t encode_coef_map(FieldMap* out, const float* base, const GridDesc& g)
 
 cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap& mcx, const FieldMap& mcy,
                             const FieldMap& mxk, const FieldMap& mxkm1, const FieldMap& mbhat, float* out3, float* out4,
-                            const QuadSteps& qs, long long wait_limit, cudaStream_t s) {
-  if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2) || wait_limit < 0) return cudaErrorInvalidValue;
+                            const QuadSteps& qs, long long wait_limit, unsigned* fault, cudaStream_t s) {
+  if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2) || wait_limit < 0 || !fault) return cudaErrorInvalidValue;
   switch (ell) {
 #define AAO_QT_CASE(L) \
   case L:              \
-    return launch_qt<L, kQuadTmaR>(g, psrc, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit, s);
+    return launch_qt<L, kQuadTmaR>(g, psrc, mcx, mcy, mxk, mxkm1, mbhat, out3, out4, qs, wait_limit, fault, s);
     AAO_QT_CASE(4)
     AAO_QT_CASE(6)
     AAO_QT_CASE(8)
@@ -544,12 +543,11 @@ cudaError_t launch_quad_tma(const GridDesc& g, int ell, int psrc, const FieldMap
   }
 }
 
-cudaError_t quad_tma_fault(unsigned* flag, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyFromSymbolAsync(flag, g_quad_tma_fault, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+cudaError_t quad_tma_fault(unsigned* dev_flag, unsigned* host_flag, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(host_flag, dev_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && *flag) {
-    const unsigned zero = 0;
-    e = cudaMemcpyToSymbolAsync(g_quad_tma_fault, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && *host_flag) {
+    e = cudaMemsetAsync(dev_flag, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   return e;
