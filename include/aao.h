@@ -340,14 +340,17 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
  * Batched solve: many independent instances of Eq. 1 (different grids, ell,
  * alpha, diffusivities and right-hand sides) solved together.  All members
  * advance in lockstep through right-preconditioned FGMRES; every phase of an
- * Arnoldi step (transform, the Chebyshev steps - four per launch while they
- * fit before the last one -, matvec, each modified Gram-Schmidt step, Givens)
- * is one launch over all members (one per distinct ell for the Chebyshev
- * kernels), each block mapped to an (instance, tile) pair; members
- * that have converged skip their blocks.  With use_graphs != 0 each Arnoldi
- * step is captured once as a CUDA graph and replayed.  The paper solves one
- * instance at a time; batching is this library's addition for covariance
- * operators applied to many fields at once.
+ * Arnoldi step (transform, the Chebyshev steps, matvec, each modified
+ * Gram-Schmidt step, Givens) is one launch over all members.  The fused
+ * Chebyshev sweeps (four steps per launch while they fit before the last one)
+ * are one persistent warp-strip launch over the units (member, frequency
+ * pair, segment, strip) of every member whatever its ell, which the warps take
+ * from a device work queue; the transforms and single steps run one launch per
+ * distinct ell, each block mapped to an (instance, tile) pair.  Members that
+ * have converged skip their work.  With use_graphs != 0 each Arnoldi step is
+ * captured once as a CUDA graph and replayed.  The paper solves one instance
+ * at a time; batching is this library's addition for covariance operators
+ * applied to many fields at once.
  *   members    count handles created with AAO_MIXED, dim 2, n[0] % 4 == 0, and
  *              the same inner_its (>= 2) and restart; they must outlive the
  *              batch, and the batch uses their workspace (do not use the
@@ -375,6 +378,25 @@ const char* aao_batch_last_error(aao_batch hb);
 
 /* Release the batch (not its members).  NULL is allowed. */
 void aao_batch_destroy(aao_batch hb);
+
+/*
+ * Fused sweep of the batch (no counterpart in the paper: launch parameters of
+ * the same steps): AAO_STEP_STREAM with S = 4, segment height H (H + 8 a
+ * multiple of 6), D in {3, 4} and NW = 8 (the default: H = 64, D = 3, used
+ * when inner_its >= 7), or AAO_STEP_TILE (the shared-memory tile kernel, one
+ * launch per distinct ell; S, H, D, NW ignored).  Drops the captured graphs.
+ */
+int aao_batch_set_sweep(aao_batch hb, int kind, int S, int H, int D, int NW);
+/*
+ * Event timing of the batch's fused-sweep launches (graphs are not used while
+ * it is on; turning it on or off clears the totals).  aao_batch_get_profile
+ * synchronises the batch stream and writes the number of timed launches, their
+ * total milliseconds and their algorithmic bytes (x_k, x_{k-1} or none, bhat
+ * and two face arrays read and two fields written, 4-byte values, over the
+ * members active in each launch).
+ */
+int aao_batch_profile_enable(aao_batch hb, int on);
+int aao_batch_get_profile(aao_batch hb, int64_t* launches, double* ms, double* bytes);
 
 /* Copy the statistics of the last solve into *s. */
 int aao_get_stats(aao_handle h, aao_stats* s);

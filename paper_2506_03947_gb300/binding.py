@@ -30,7 +30,8 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
             "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode",
             "aao_set_stream_config", "aao_get_stream_config", "aao_autotune", "aao_tune_lookup",
-            "aao_set_tune_cache", "aao_get_tuning")
+            "aao_set_tune_cache", "aao_get_tuning", "aao_batch_set_sweep", "aao_batch_profile_enable",
+            "aao_batch_get_profile")
 
 # preconditioner of the outer solve (aao_set_precond_mode)
 AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT, AAO_PRECOND_SP = 0, 1, 2
@@ -156,6 +157,12 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_set_tune_cache.restype = i32
     lib.aao_get_tuning.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.aao_get_tuning.restype = i32
+    lib.aao_batch_set_sweep.argtypes = [vp, i32, i32, i32, i32, i32]
+    lib.aao_batch_set_sweep.restype = i32
+    lib.aao_batch_profile_enable.argtypes = [vp, i32]
+    lib.aao_batch_profile_enable.restype = i32
+    lib.aao_batch_get_profile.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.aao_batch_get_profile.restype = i32
     lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.aao_set_wait_limit.restype = i32
     lib.aao_set_precond_mode.argtypes = [vp, i32]
@@ -431,6 +438,24 @@ class Batch:
         if rc not in ok:
             raise AaoError(rc, (lib.aao_batch_last_error(self.hb) or b"").decode(errors="replace"))
         return rc
+
+    def _check(self, rc):
+        if rc != AAO_OK:
+            raise AaoError(rc, (load_library().aao_batch_last_error(self.hb) or b"").decode(errors="replace"))
+        return rc
+
+    def set_sweep(self, kind, S=4, H=64, D=3, NW=8):
+        return self._check(load_library().aao_batch_set_sweep(self.hb, int(kind), int(S), int(H), int(D), int(NW)))
+
+    def profile_enable(self, on=True):
+        return self._check(load_library().aao_batch_profile_enable(self.hb, 1 if on else 0))
+
+    def profile(self):
+        n = C.c_int64(0)
+        ms = C.c_double(0.0)
+        by = C.c_double(0.0)
+        self._check(load_library().aao_batch_get_profile(self.hb, C.byref(n), C.byref(ms), C.byref(by)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value}
 
     def stats(self, i):
         s = aao_stats()

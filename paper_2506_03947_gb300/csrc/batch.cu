@@ -284,6 +284,73 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
   return cudaSuccess;
 }
 
+template <int ELL>
+cudaError_t batch_precond_head_ell(const BInst* I, const int* act, const WorkList& wdft, const WorkList& wstep, int p,
+                                   int j, cudaStream_t s) {
+  if (wdft.cnt == 0) return cudaSuccess;
+  if (p < 3) return cudaErrorInvalidValue;  // the fused form needs a step before the last one
+  kb_dft<ELL><<<wdft.total, 256, 0, s>>>(I, act, wdft, j);
+  AAO_BCHECK();
+  const dim3 blk(32, 8, 1);
+  kb_step_first<ELL, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);  // x_2 into field 0
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+template <int ELL>
+cudaError_t batch_precond_tail_ell(const BInst* I, const int* act, const WorkList& wstep, int p, int j, int k, int cur,
+                                   int prev, cudaStream_t s) {
+  if (wstep.cnt == 0) return cudaSuccess;
+  const dim3 blk(32, 8, 1);
+  for (; k <= p - 2; ++k) {
+    int dst = prev;
+    if (dst < 0) dst = (cur == 0) ? 1 : 0;
+    if (prev < 0) kb_step_f<ELL, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    else kb_step_f<ELL, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    AAO_BCHECK();
+    prev = cur;
+    cur = dst;
+  }
+  if (prev < 0) kb_step_f<ELL, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
+  else kb_step_f<ELL, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
+                               int p, int j, cudaStream_t s) {
+  switch (ell) {
+#define AAO_BH(L) \
+  case L: return batch_precond_head_ell<L>(I, act, wdft, wstep, p, j, s);
+    AAO_BH(4)
+    AAO_BH(6)
+    AAO_BH(8)
+    AAO_BH(10)
+    AAO_BH(12)
+    AAO_BH(14)
+    AAO_BH(16)
+#undef AAO_BH
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, const WorkList& wstep, int p, int j, int kf,
+                               int cur, int prev, cudaStream_t s) {
+  switch (ell) {
+#define AAO_BT(L) \
+  case L: return batch_precond_tail_ell<L>(I, act, wstep, p, j, kf, cur, prev, s);
+    AAO_BT(4)
+    AAO_BT(6)
+    AAO_BT(8)
+    AAO_BT(10)
+    AAO_BT(12)
+    AAO_BT(14)
+    AAO_BT(16)
+#undef AAO_BT
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
                           const WorkList& wquad, int p, int j, cudaStream_t s) {
   switch (ell) {

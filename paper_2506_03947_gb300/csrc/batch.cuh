@@ -52,4 +52,28 @@ cudaError_t batch_small(const BInst* I, const int* act, const WorkList& wone, in
 cudaError_t batch_norm2_b(const BInst* I, const int* act, const WorkList& wred, cudaStream_t s);
 cudaError_t batch_xupdate(const BInst* I, const int* act, const WorkList& wred, const int* kvec, cudaStream_t s);
 
+// P_NC^{-1} of Arnoldi step j in three parts, so that the fused sweeps of all members (any
+// ell) run as single launches: batch_precond_head (transform and step 1, per ell), the
+// caller's warp-strip launches (launch_batch_stream) for steps 2 .. kf-1, and
+// batch_precond_tail (single steps kf .. p-2 and the last step with the inverse transform,
+// per ell), with x_k in field cur and x_{k-1} in field prev (-1: bhat/theta) at kf.
+cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
+                               int p, int j, cudaStream_t s);
+cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, const WorkList& wstep, int p, int j, int kf,
+                               int cur, int prev, cudaStream_t s);
+
+// Device work queue of a batched warp-strip launch: tickets are taken from next; each warp
+// adds one to done when it leaves, and the last one resets both (zero between launches).
+struct StreamQueue {
+  unsigned next, done;
+};
+// Units (plane pair x segment x strip) of one member for halo depth S and segment height H.
+int batch_stream_units(const GridDesc& g, int ell, int S, int H);
+// One launch of S fused steps k .. k+S-1 over the units of every active member (list units:
+// member inst[i] owns units [start[i], start[i+1])), persistent over a device queue; the fields
+// are the members' rotating buffers (0..3): x_k = cur, x_{k-1} = prev (psrc 2) or bhat/theta
+// (psrc 1), outputs x_{k+S-1} -> o3 and x_{k+S} -> o4.
+cudaError_t launch_batch_stream(const BInst* I, const int* act, const WorkList& units, const StreamConfig& c, int k,
+                                int psrc, int cur, int prev, int o3, int o4, StreamQueue* queue, cudaStream_t s);
+
 }  // namespace aao

@@ -36,6 +36,19 @@ struct aao_batch_ctx {
   std::vector<void*> owned;
   std::vector<std::pair<int, aao::WorkList>> wdft, wstep, wquad;  // per ell
   aao::WorkList wmv{}, wred{}, wone{}, wmgs{};
+  // fused sweeps: one warp-strip launch over the units of all members (any ell), from a device
+  // queue (sweep = AAO_STEP_STREAM), or the shared-memory tile kernel per ell (AAO_STEP_TILE)
+  int sweep = AAO_STEP_STREAM;
+  aao::StreamConfig scfg{};
+  aao::WorkList wunits{};
+  aao::StreamQueue* queue = nullptr;
+  std::vector<int> hact;  // host copy of the active flags
+  // event timing of the fused sweeps (aao_batch_profile_enable; graphs are not used meanwhile)
+  bool prof = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<double> pend_bytes;
+  double prof_ms = 0.0, prof_bytes = 0.0;
+  long long prof_launches = 0;
   std::vector<cudaGraphExec_t> graphs;
   std::vector<long long> graph_launches;
   std::vector<aao_stats> stats;
@@ -82,11 +95,76 @@ int make_worklist(aao_batch_ctx* B, const std::vector<int>& inst, const std::vec
 }
 
 // Phases of Arnoldi step j for every active instance, in stream order.
-int batch_step_launches(aao_batch_ctx* B, int j) {
+// Algorithmic bytes of one fused launch over the active members: x_k, x_{k-1} (psrc 2), bhat
+// and two face arrays read, two fields written, 4-byte values.
+double fused_bytes(const aao_batch_ctx* B, int psrc) {
+  double t = 0.0;
+  for (int i = 0; i < B->M; ++i)
+    if (B->hact.empty() || B->hact[i])
+      t += (double)B->hI[i].g.N * ((psrc == 1 ? 4.0 : 5.0) * 4.0 * B->hI[i].ell + 8.0);
+  return t;
+}
+
+int batch_precond_stream(aao_batch_ctx* B, int j) {
   cudaStream_t s = B->stream;
   for (size_t g = 0; g < B->wdft.size(); ++g)
-    AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second,
-                                  B->wquad[g].second, B->p, j, s));
+    AAO_BCK(B, aao::batch_precond_head(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second, B->p,
+                                       j, s));
+  // fused launches while steps k .. k+S-1 all come before the last step; the four fields rotate
+  // so that a launch never writes a field it reads (the single solver's schedule)
+  const int S = B->scfg.S;
+  int cur = 0, prev = -1, k = 2;
+  while (k + S - 1 <= B->p - 2) {
+    int o[2], n = 0;
+    for (int f = 0; f < 4 && n < 2; ++f)
+      if (f != cur && f != prev) o[n++] = f;
+    const int psrc = prev < 0 ? 1 : 2;
+    const int ev = B->prof ? (int)B->pend_bytes.size() : -1;
+    if (ev >= 0) {
+      while ((int)B->events.size() < 2 * ev + 2) {
+        cudaEvent_t e;
+        AAO_BCK(B, cudaEventCreate(&e));
+        B->events.push_back(e);
+      }
+      AAO_BCK(B, cudaEventRecord(B->events[2 * ev], s));
+      B->pend_bytes.push_back(fused_bytes(B, psrc));
+    }
+    AAO_BCK(B, aao::launch_batch_stream(B->dI, B->dact, B->wunits, B->scfg, k, psrc, cur, prev, o[0], o[1], B->queue,
+                                        s));
+    if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
+    prev = o[0];
+    cur = o[1];
+    k += S;
+  }
+  for (size_t g = 0; g < B->wstep.size(); ++g)
+    AAO_BCK(B, aao::batch_precond_tail(B->dI, B->dact, B->wstep[g].first, B->wstep[g].second, B->p, j, k, cur, prev,
+                                       s));
+  return AAO_OK;
+}
+
+// Resolve the recorded fused-launch events (the stream has been synchronised).
+void batch_prof_resolve(aao_batch_ctx* B) {
+  for (size_t i = 0; i < B->pend_bytes.size(); ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, B->events[2 * i], B->events[2 * i + 1]) == cudaSuccess) {
+      B->prof_ms += ms;
+      B->prof_bytes += B->pend_bytes[i];
+      B->prof_launches++;
+    }
+  }
+  B->pend_bytes.clear();
+}
+
+int batch_step_launches(aao_batch_ctx* B, int j) {
+  cudaStream_t s = B->stream;
+  if (B->sweep == AAO_STEP_STREAM) {
+    const int rc = batch_precond_stream(B, j);
+    if (rc) return rc;
+  } else {
+    for (size_t g = 0; g < B->wdft.size(); ++g)
+      AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second,
+                                    B->wquad[g].second, B->p, j, s));
+  }
   AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 0, j, s));
   if (B->mgs) AAO_BCK(B, aao::batch_mgs(B->dI, B->dact, B->wmgs, j, s));
   else AAO_BCK(B, aao::batch_gram_schmidt(B->dI, B->dact, B->wred, B->wone, j, s));
@@ -96,7 +174,7 @@ int batch_step_launches(aao_batch_ctx* B, int j) {
 }
 
 int batch_run_step(aao_batch_ctx* B, int j) {
-  if (!B->use_graphs) return batch_step_launches(B, j);
+  if (!B->use_graphs || B->prof) return batch_step_launches(B, j);
   if ((int)B->graphs.size() <= j) {
     B->graphs.resize(j + 1, nullptr);
     B->graph_launches.resize(j + 1, 0);
@@ -128,10 +206,12 @@ int batch_run_step(aao_batch_ctx* B, int j) {
 int batch_read(aao_batch_ctx* B) {
   AAO_BCK(B, cudaMemcpyAsync(B->hout, B->dout, sizeof(double) * 2 * B->M, cudaMemcpyDeviceToHost, B->stream));
   AAO_BCK(B, cudaStreamSynchronize(B->stream));
+  batch_prof_resolve(B);
   return AAO_OK;
 }
 
 int batch_set_active(aao_batch_ctx* B, const std::vector<int>& act) {
+  B->hact = act;
   AAO_BCK(B, cudaMemcpyAsync(B->dact, act.data(), sizeof(int) * B->M, cudaMemcpyHostToDevice, B->stream));
   AAO_BCK(B, cudaStreamSynchronize(B->stream));  // act is a host temporary
   return AAO_OK;
@@ -152,6 +232,8 @@ void aao_batch_destroy(aao_batch hb) {
   if (hb->dkvec) cudaFree(hb->dkvec);
   if (hb->dout) cudaFree(hb->dout);
   if (hb->hout) cudaFreeHost(hb->hout);
+  if (hb->queue) cudaFree(hb->queue);
+  for (cudaEvent_t e : hb->events) cudaEventDestroy(e);
   if (hb->stream) cudaStreamDestroy(hb->stream);
   delete hb;
 }
@@ -262,6 +344,19 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     B->wstep.push_back({ell, ws});
     B->wquad.push_back({ell, wq});
   }
+  // warp-strip units of every member (any ell) for the fused sweeps: segments of 64 rows
+  B->scfg.S = 4;
+  B->scfg.H = 64;
+  B->scfg.D = 3;
+  B->scfg.NW = 8;
+  if (B->p < 7) B->sweep = AAO_STEP_TILE;  // no step of the fused form would fit
+  {
+    std::vector<int> nunits(count);
+    for (int i = 0; i < count; ++i) nunits[i] = aao::batch_stream_units(members[i]->g, members[i]->ell, 4, B->scfg.H);
+    if (make_worklist(B, all, nunits, &B->wunits)) return bail(AAO_ECUDA);
+  }
+  AAO_BCK_CREATE(cudaMalloc(&B->queue, sizeof(aao::StreamQueue)));
+  AAO_BCK_CREATE(cudaMemset(B->queue, 0, sizeof(aao::StreamQueue)));
   if (make_worklist(B, all, bmv, &B->wmv) || make_worklist(B, all, bred, &B->wred) ||
       make_worklist(B, all, bmgs, &B->wmgs) || make_worklist(B, all, bone, &B->wone))
     return bail(AAO_ECUDA);
@@ -391,5 +486,60 @@ int aao_batch_get_stats(aao_batch B, int i, aao_stats* s) {
 }
 
 const char* aao_batch_last_error(aao_batch B) { return B ? B->err.c_str() : g_create_error.c_str(); }
+
+int aao_batch_set_sweep(aao_batch B, int kind, int S, int H, int D, int NW) {
+  if (!B) return bfail(nullptr, AAO_EINVAL, "NULL batch");
+  if (kind == AAO_STEP_TILE) {
+    B->sweep = kind;
+  } else if (kind == AAO_STEP_STREAM) {
+    aao::StreamConfig c;
+    c.S = S;
+    c.H = H;
+    c.D = D;
+    c.NW = NW;
+    if (!aao::stream_config_supported(c) || S != 4 || NW != 8)
+      return bfail(B, AAO_EINVAL, "the batched warp-strip launch runs S = 4, NW = 8 (got S=%d H=%d D=%d NW=%d)", S, H,
+                   D, NW);
+    if (B->p - 2 < S + 1) return bfail(B, AAO_EINVAL, "inner_its %d leaves no fused launch", B->p);
+    std::vector<int> all(B->M), nunits(B->M);
+    for (int i = 0; i < B->M; ++i) {
+      all[i] = i;
+      nunits[i] = aao::batch_stream_units(B->hI[i].g, B->hI[i].ell, S, H);
+    }
+    aao::WorkList wl{};
+    const int rc = make_worklist(B, all, nunits, &wl);
+    if (rc) return rc;
+    B->wunits = wl;
+    B->scfg = c;
+    B->sweep = kind;
+  } else {
+    return bfail(B, AAO_EINVAL, "unknown sweep kind %d", kind);
+  }
+  for (cudaGraphExec_t g : B->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  B->graphs.clear();
+  B->graph_launches.clear();
+  return AAO_OK;
+}
+
+int aao_batch_profile_enable(aao_batch B, int on) {
+  if (!B) return bfail(nullptr, AAO_EINVAL, "NULL batch");
+  AAO_BCK(B, cudaStreamSynchronize(B->stream));
+  B->pend_bytes.clear();
+  B->prof_ms = B->prof_bytes = 0.0;
+  B->prof_launches = 0;
+  B->prof = on != 0;
+  return AAO_OK;
+}
+
+int aao_batch_get_profile(aao_batch B, int64_t* launches, double* ms, double* bytes) {
+  if (!B) return bfail(nullptr, AAO_EINVAL, "NULL batch");
+  AAO_BCK(B, cudaStreamSynchronize(B->stream));
+  batch_prof_resolve(B);
+  if (launches) *launches = B->prof_launches;
+  if (ms) *ms = B->prof_ms;
+  if (bytes) *bytes = B->prof_bytes;
+  return AAO_OK;
+}
 
 }  // extern "C"

@@ -33,6 +33,7 @@
 #include <utility>
 
 #include "aao_internal.cuh"
+#include "batch.cuh"
 
 namespace aao {
 
@@ -88,10 +89,10 @@ struct PassCoef {
 };
 
 template <int S, bool CPLX>
-__device__ __forceinline__ void load_pass_coef(PassCoef<S>& pc, const FuseSteps& fs, int m0, int m1) {
+__device__ __forceinline__ void load_pass_coef(PassCoef<S>& pc, const StepArgs<float>* steps, int m0, int m1) {
 #pragma unroll
   for (int q = 0; q < S; ++q) {
-    const StepArgs<float>& st = fs.s[q];
+    const StepArgs<float>& st = steps[q];
     if (CPLX) {
       pc.c[q][0] = dup(st.lam_re[m0]), pc.c[q][1] = dup(st.lam_im[m0]);
       pc.c[q][2] = dup(st.a_re[m0]), pc.c[q][3] = dup(st.a_im[m0]);
@@ -111,9 +112,10 @@ struct RowCoef {
   float w0;  // west face of cell 0 (the east face of the lane to the left)
 };
 
-// Kernel arguments (one __grid_constant__ block in the parameter space: the pointers and sizes
-// are read from there where they are used, not held in registers).
-struct StreamArgs {
+// Geometry and fields of one instance's launch.  For a single instance it sits in the kernel's
+// __grid_constant__ parameter block, for a batch in a per-warp shared-memory copy; either way
+// the pointers and sizes are read where they are used, not held in registers.
+struct StreamGeo {
   GridDesc g;
   int npass, ell, H, nseg, nstrip;
   const float* cx;
@@ -123,6 +125,10 @@ struct StreamArgs {
   const float* xkm1;
   float* outA;
   float* outB;
+};
+
+struct StreamArgs {
+  StreamGeo geo;
   FuseSteps fs;
 };
 
@@ -131,7 +137,7 @@ struct StreamUnit {
   static constexpr int NA = StreamGeom<PSRC>::NA;
   static_assert(D + 2 <= kRing && S + 2 <= kRing, "ring or window too shallow");
 
-  const StreamArgs& a;
+  const StreamGeo& a;
   unsigned ringA, ringB;  // this warp's rings (shared addresses) plus the lane's 8-byte slot
   // element offsets of this lane's first cell: in the fields (plane p0) and in a face array
   // (column 0 when the lane's cells are outside the grid: such copies read nothing)
@@ -318,8 +324,8 @@ struct StreamUnit {
 };
 
 template <int S, int D, int PSRC, bool CPLX>
-__device__ __forceinline__ void stream_unit(const StreamArgs& a, const Unit& un, int lane, unsigned ringA,
-                                            unsigned ringB) {
+__device__ __forceinline__ void stream_unit(const StreamGeo& a, const StepArgs<float>* steps, const Unit& un,
+                                            int lane, unsigned ringA, unsigned ringB) {
   StreamUnit<S, D, PSRC, CPLX> su{a};
   su.ringA = ringA + (unsigned)(lane * 8);
   su.ringB = ringB + (unsigned)(lane * 8);
@@ -329,18 +335,19 @@ __device__ __forceinline__ void stream_unit(const StreamArgs& a, const Unit& un,
   su.offc = un.colok ? un.gx : 0;  // keep every source address inside its array
   su.offf = (int64_t)un.p0 * a.g.N + su.offc;
   if (CPLX) {
-    su.it[0] = a.fs.s[0].it_re[un.m0], su.it[1] = a.fs.s[0].it_im[un.m0];
+    su.it[0] = steps[0].it_re[un.m0], su.it[1] = steps[0].it_im[un.m0];
   } else {
-    su.it[0] = a.fs.s[0].it_re[un.m0], su.it[1] = a.fs.s[0].it_re[un.m1];
+    su.it[0] = steps[0].it_re[un.m0], su.it[1] = steps[0].it_re[un.m1];
   }
-  load_pass_coef<S, CPLX>(su.pc, a.fs, un.m0, un.m1);
+  load_pass_coef<S, CPLX>(su.pc, steps, un.m0, un.m1);
   su.run();
 }
 
 // Registers: 8 warps of up to 200 per thread (two per SM sub-partition of 16 K registers); the
 // two-step variant with 12 warps stays within 168.
 template <int S, int D, int NW, int PSRC>
-__global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constant__ StreamArgs a) {
+__global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constant__ StreamArgs args) {
+  const StreamGeo& a = args.geo;
   using G = StreamGeom<PSRC>;
   extern __shared__ __align__(16) unsigned char smem_stream[];
   const int lane = threadIdx.x & 31;
@@ -365,9 +372,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constan
     un.gx = strip * IW - S + 2 * lane;
     un.colok = un.gx >= 0 && un.gx < a.g.n0;
     if (pass == 0)
-      stream_unit<S, D, PSRC, false>(a, un, lane, ringA, ringB);
+      stream_unit<S, D, PSRC, false>(a, args.fs.s, un, lane, ringA, ringB);
     else
-      stream_unit<S, D, PSRC, true>(a, un, lane, ringA, ringB);
+      stream_unit<S, D, PSRC, true>(a, args.fs.s, un, lane, ringA, ringB);
   }
 }
 
@@ -386,19 +393,19 @@ cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const
   int grid = (units + NW - 1) / NW;
   if (grid > nsm) grid = nsm;
   StreamArgs a;
-  a.g = g;
-  a.npass = ell / 2;
-  a.ell = ell;
-  a.H = H;
-  a.nseg = nseg;
-  a.nstrip = nstrip;
-  a.cx = cx;
-  a.cy = cy;
-  a.bhat = bhat;
-  a.xk = xk;
-  a.xkm1 = xkm1;
-  a.outA = outA;
-  a.outB = outB;
+  a.geo.g = g;
+  a.geo.npass = ell / 2;
+  a.geo.ell = ell;
+  a.geo.H = H;
+  a.geo.nseg = nseg;
+  a.geo.nstrip = nstrip;
+  a.geo.cx = cx;
+  a.geo.cy = cy;
+  a.geo.bhat = bhat;
+  a.geo.xk = xk;
+  a.geo.xkm1 = xkm1;
+  a.geo.outA = outA;
+  a.geo.outB = outB;
   a.fs = fs;
   if (psrc == 1) {
     auto k = k_cheb_stream<S, D, NW, 1>;
@@ -446,6 +453,165 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
   AAO_STREAM_CFG(2, 3, 16)
   AAO_STREAM_CFG(2, 4, 16)
 #undef AAO_STREAM_CFG
+  return cudaErrorInvalidValue;
+}
+
+
+// ---- batched form: one persistent launch over the units of every member -------------------
+
+namespace {
+
+// Unit u of a batched launch belongs to list entry li with ustart[li] <= u < ustart[li + 1]
+// (member uinst[li]); units are taken from a device queue, one ticket per warp and unit.
+struct StreamBatchArgs {
+  const BInst* I;
+  const int* act;
+  const int* ustart;
+  const int* uinst;
+  int cnt;       // list entries
+  int total;     // units over all entries
+  int H;         // segment height of every member
+  int k;         // first fused step: steps k .. k+S-1 of every member
+  int cur, prev, o3, o4;  // the members' rotating fields: x_k, x_{k-1} (PSRC 2), outputs
+  StreamQueue* queue;
+};
+
+__device__ __forceinline__ float* bfield(const BInst& b, int i) {
+  return i == 0 ? b.xa : i == 1 ? b.xb : i == 2 ? b.xc : b.xd;
+}
+
+template <int S, int D, int NW, int PSRC>
+__global__ void __launch_bounds__(NW * 32, 1) kb_cheb_stream(const __grid_constant__ StreamBatchArgs ba) {
+  using G = StreamGeom<PSRC>;
+  extern __shared__ __align__(16) unsigned char smem_stream[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const unsigned base = (unsigned)__cvta_generic_to_shared(smem_stream) + (unsigned)(warp * 32 * G::lane_bytes);
+  const unsigned ringA = base;
+  const unsigned ringB = base + (unsigned)(kRing * G::NA * 32 * 8);
+  // this warp's copy of the current member's geometry, after all warps' rings
+  StreamGeo* geo = reinterpret_cast<StreamGeo*>(smem_stream + (size_t)NW * 32 * G::lane_bytes) + warp;
+  constexpr int IW = kSW - 2 * S;
+  while (true) {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(&ba.queue->next, 1u);
+    const int u = (int)__shfl_sync(0xffffffffu, t, 0);
+    if (u >= ba.total) break;
+    int lo = 0, hi = ba.cnt;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (ba.ustart[mid] <= u) lo = mid;
+      else hi = mid;
+    }
+    const int inst = ba.uinst[lo];
+    if (!ba.act[inst]) continue;
+    const BInst& b = ba.I[inst];
+    __syncwarp();  // every lane is done with the previous unit's geometry
+    if (lane == 0) {
+      StreamGeo gg;
+      gg.g = b.g;
+      gg.ell = b.ell;
+      gg.npass = b.ell / 2;
+      gg.H = ba.H;
+      gg.nseg = (b.g.n1 + ba.H - 1) / ba.H;
+      gg.nstrip = (b.g.n0 + IW - 1) / IW;
+      gg.cx = b.cx32;
+      gg.cy = b.cy32;
+      gg.bhat = b.bhat;
+      gg.xk = bfield(b, ba.cur);
+      gg.xkm1 = (PSRC == 2) ? bfield(b, ba.prev) : nullptr;
+      gg.outA = bfield(b, ba.o3);
+      gg.outB = bfield(b, ba.o4);
+      *geo = gg;
+    }
+    __syncwarp();
+    const StreamGeo& a = *geo;
+    const int lu = u - ba.ustart[lo];
+    const int per_pass = a.nseg * a.nstrip;
+    Unit un;
+    const int pass = lu / per_pass;
+    const int rem = lu - pass * per_pass;
+    const int seg = rem / a.nstrip;
+    const int strip = rem - seg * a.nstrip;
+    un.p0 = 2 * pass;
+    un.m0 = pass;
+    un.m1 = (pass == 0) ? a.ell / 2 : pass;
+    un.y0 = seg * a.H;
+    un.gx = strip * IW - S + 2 * lane;
+    un.colok = un.gx >= 0 && un.gx < a.g.n0;
+    const StepArgs<float>* steps = b.steps + ba.k;
+    if (pass == 0)
+      stream_unit<S, D, PSRC, false>(a, steps, un, lane, ringA, ringB);
+    else
+      stream_unit<S, D, PSRC, true>(a, steps, un, lane, ringA, ringB);
+  }
+  // every warp ends here once, after its ticket past the end: the last one resets the queue
+  // for the next launch
+  if (lane == 0) {
+    const unsigned d = atomicAdd(&ba.queue->done, 1u);
+    if (d == gridDim.x * NW - 1) {
+      atomicExch(&ba.queue->next, 0u);
+      atomicExch(&ba.queue->done, 0u);
+    }
+  }
+}
+
+template <int S, int D, int NW>
+cudaError_t launch_batch_stream_cfg(const StreamBatchArgs& ba, int psrc, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int grid = (ba.total + NW - 1) / NW;
+  if (grid > nsm) grid = nsm;
+  if (grid < 1) grid = 1;
+  if (psrc == 1) {
+    auto k = kb_cheb_stream<S, D, NW, 1>;
+    const size_t smem = (size_t)NW * 32 * StreamGeom<1>::lane_bytes + (size_t)NW * sizeof(StreamGeo);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NW * 32, smem, s>>>(ba);
+  } else {
+    auto k = kb_cheb_stream<S, D, NW, 2>;
+    const size_t smem = (size_t)NW * 32 * StreamGeom<2>::lane_bytes + (size_t)NW * sizeof(StreamGeo);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NW * 32, smem, s>>>(ba);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int batch_stream_units(const GridDesc& g, int ell, int S, int H) {
+  const int IW = kSW - 2 * S;
+  return (ell / 2) * ((g.n1 + H - 1) / H) * ((g.n0 + IW - 1) / IW);
+}
+
+cudaError_t launch_batch_stream(const BInst* I, const int* act, const WorkList& units, const StreamConfig& c, int k,
+                                int psrc, int cur, int prev, int o3, int o4, StreamQueue* queue, cudaStream_t s) {
+  if (!stream_config_supported(c) || (psrc != 1 && psrc != 2) || !queue) return cudaErrorInvalidValue;
+  if (units.total == 0) return cudaSuccess;
+  StreamBatchArgs ba;
+  ba.I = I;
+  ba.act = act;
+  ba.ustart = units.start;
+  ba.uinst = units.inst;
+  ba.cnt = units.cnt;
+  ba.total = units.total;
+  ba.H = c.H;
+  ba.k = k;
+  ba.cur = cur;
+  ba.prev = prev < 0 ? 0 : prev;
+  ba.o3 = o3;
+  ba.o4 = o4;
+  ba.queue = queue;
+#define AAO_BSTREAM_CFG(SS, DD, NN) \
+  if (c.S == SS && c.D == DD && c.NW == NN) return launch_batch_stream_cfg<SS, DD, NN>(ba, psrc, s);
+  AAO_BSTREAM_CFG(4, 3, 8)
+  AAO_BSTREAM_CFG(4, 4, 8)
+#undef AAO_BSTREAM_CFG
   return cudaErrorInvalidValue;
 }
 

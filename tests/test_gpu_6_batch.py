@@ -144,3 +144,49 @@ def test_batch_argument_checks():
         binding.Batch([make_solver(P, 1, 8), make_solver(P, 1, 9)])   # different inner_its
     with pytest.raises(binding.AaoError):
         binding.Batch([make_solver(P, 0, 8)])                         # FP64 members
+
+
+def test_batch_warp_strip_queue_matches_tile_sweep():
+    # The fused sweeps as one persistent warp-strip launch over all members (any ell), units taken
+    # from the device queue, against the same batch with the shared-memory tile kernel per ell:
+    # the steps are the same arithmetic in the same order, so the solves agree to rounding (the
+    # queue is reset by its last warp, so every launch of every Arnoldi step covers all units)
+    torch = torch_cuda()
+    binding = ensure_lib()
+    probs = _members()
+    solvers = [make_solver(P, 1, 12, restart=32) for P in probs]
+    bs = [to_dev(P.b) for P in probs]
+    out = {}
+    for kind in (binding.AAO_STEP_STREAM, binding.AAO_STEP_TILE):
+        xs = [torch.zeros_like(b) for b in bs]
+        batch = binding.Batch(solvers, use_graphs=True)
+        batch.set_sweep(kind)
+        batch.solve(bs, xs, 1e-8, 200)
+        out[kind] = ([x.cpu().numpy() for x in xs], [batch.stats(i)["outer_its"] for i in range(len(probs))])
+        batch.close()
+    (xa, ia), (xb, ib) = out[binding.AAO_STEP_STREAM], out[binding.AAO_STEP_TILE]
+    assert ia == ib
+    same = all(np.array_equal(a, b) for a, b in zip(xa, xb))
+    diff = max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(xa, xb))
+    log_record({"test": "batch_stream_vs_tile", "its": ia, "bitwise": same, "rel_diff": diff})
+    assert diff <= 1e-12
+
+
+def test_batch_profile_reports_fused_sweeps():
+    torch = torch_cuda()
+    binding = ensure_lib()
+    probs = _members()[:3]
+    solvers = [make_solver(P, 1, 12, restart=32) for P in probs]
+    bs = [to_dev(P.b) for P in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = binding.Batch(solvers, use_graphs=True)
+    batch.profile_enable(True)
+    batch.solve(bs, xs, 1e-8, 200)
+    prof = batch.profile()
+    its = max(batch.stats(i)["outer_its"] for i in range(len(probs)))
+    # two fused launches per Arnoldi step at p = 12 (steps 2..5 and 6..9)
+    assert prof["launches"] == 2 * its and prof["ms"] > 0
+    cells = sum(P.N * (9.0 * 4 * P.ell + 2 * 8) / 2 for P in probs)   # one launch of each psrc per step
+    assert 0 < prof["bytes"] <= 2 * its * cells * 1.01
+    with pytest.raises(binding.AaoError):
+        batch.set_sweep(binding.AAO_STEP_STREAM, 4, 63, 3, 8)       # H + 8 not a multiple of 6
