@@ -547,7 +547,7 @@ def run_best_case_leg(args, binding, torch, sptr):
     return {"workload": "2d_const_256x256_l10 (kappa 5), tol 1e-8; outer iterations",
             "alpha_sweep": rows,
             "best_case_1024": {"alpha": 1e-2, "outer_its": its1024, "ms_per_solve": e0.elapsed_time(e1),
-                               "note": "FP64, spatial DCT as batched cuBLAS DGEMMs"}}
+                               "note": "FP64, spatial DCT by the library's own FFT-based kernels (power-of-two axes)"}}
 
 
 def run_sweep_leg(args, binding, torch, sptr):

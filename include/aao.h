@@ -274,7 +274,9 @@ int aao_get_tuning(aao_handle h, int32_t out[6]);
  *                          diffusivities that are constant along each axis, X is the
  *                          orthonormal DCT-II along every axis and
  *                          Phi = 1 + sum_a kappa_a 4 sin^2(pi k_a / (2 n_a)).  The spatial
- *                          transforms run as batched FP64 GEMMs (cuBLAS); FP64 handles only.
+ *                          transforms are this library's kernels (a fast DCT through one FFT
+ *                          per line for power-of-two axes, direct sums otherwise); FP64
+ *                          handles only.
  *   AAO_PRECOND_SP         P_SP (Section 4): the real shifts (frequencies 0 and ell/2) by
  *                          p steps of CG on A - lambda I, each complex shift by p steps of
  *                          MINRES on the saddle-point system of twice the size with the

@@ -74,7 +74,7 @@ def build(verbose: bool = False, force: bool = False, jobs: int = 0) -> str:
         with cf.ThreadPoolExecutor(max_workers=n) as ex:
             list(ex.map(compile_one, todo))
     if force or todo or _newer(objs, LIB):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart", "-lcublas"]
+        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

@@ -359,7 +359,13 @@ __global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constan
   const int nunits = a.npass * per_pass;
   const int total_warps = gridDim.x * NW;
   constexpr int IW = kSW - 2 * S;
-  for (int u = blockIdx.x * NW + warp; u < nunits; u += total_warps) {
+  // CTA b takes the contiguous chunk [b units / grid, (b + 1) units / grid) of units (strip
+  // fastest): every SM gets work, and neighbouring strips, which share halo columns, run on
+  // the same SM
+  const int u_begin = (int)((int64_t)blockIdx.x * nunits / gridDim.x);
+  const int u_end = (int)((int64_t)(blockIdx.x + 1) * nunits / gridDim.x);
+  (void)total_warps;
+  for (int u = u_begin + warp; u < u_end; u += NW) {
     Unit un;
     const int pass = u / per_pass;
     const int rem = u - pass * per_pass;
@@ -390,8 +396,7 @@ cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const
   const int nstrip = (g.n0 + IW - 1) / IW;
   const int nseg = (g.n1 + H - 1) / H;
   const int units = (ell / 2) * nseg * nstrip;
-  int grid = (units + NW - 1) / NW;
-  if (grid > nsm) grid = nsm;
+  const int grid = units < nsm ? units : nsm;
   StreamArgs a;
   a.geo.g = g;
   a.geo.npass = ell / 2;

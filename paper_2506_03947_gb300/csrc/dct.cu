@@ -5,12 +5,22 @@
 // For the finite-volume Neumann operator with diffusivity kappa_a on every face of axis a,
 // X is the orthonormal DCT-II along each axis and Phi = 1 + sum_a kappa_a 4 sin^2(pi k_a / (2 n_a)).
 // The apply is: the time DFT (the path's own kernel), the spatial DCT of every frequency plane
-// as batched FP64 GEMMs with the n_a x n_a DCT matrices (cuBLAS: plain dense products), the
-// division by (phi - lambda_m) per cell and frequency, the inverse DCT, and the inverse time
-// DFT with Gamma^{-1}.  This is the comparison preconditioner of the paper's experiments
+// (each of the ell packed planes is a real field: the transform acts on Re and Im parts alike),
+// the division by (phi - lambda_m) per cell and frequency, the inverse DCT, and the inverse
+// time DFT with Gamma^{-1}.  This is the comparison preconditioner of the paper's experiments
 // ("best case"), not part of the inner Chebyshev path.
-#include <cublas_v2.h>
-
+//
+// The spatial transforms are this library's kernels, one launch per axis, in place: a block
+// loads a few whole lines of the axis into shared memory and transforms them.
+//  * Power-of-two lengths: the orthonormal DCT-II of a real line x through one complex FFT of
+//    the same length (Makhoul, IEEE Trans. ASSP 28(1), 1980): v = (x_0, x_2, ..., x_3, x_1)
+//    (even entries, then odd entries reversed), V = FFT(v), y_k = c_k Re(e^{-i pi k/(2n)} V_k),
+//    c_0 = sqrt(1/n), c_k = sqrt(2/n).  The inverse (DCT-III) builds
+//    V_k = e^{i pi k/(2n)} (y_k/c_k - i y_{n-k}/c_{n-k}) (y_n = 0), v = IFFT(V) (real) and undoes
+//    the reordering.  The FFT is radix-2 in shared memory with FP64 twiddles from the host.
+//    O(n log n) per line instead of the O(n^2) of a dense product.
+//  * Other lengths: the direct sums y_k = sum_j C_kj x_j (inverse: x_j = sum_k C_kj y_k) with the
+//    orthonormal DCT-II matrix C_kj = c_k cos(pi k (2j + 1)/(2n)) from the host.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -68,10 +78,140 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-cudaError_t blas_error(cublasStatus_t st) {
-  if (st == CUBLAS_STATUS_SUCCESS) return cudaSuccess;
-  if (st == CUBLAS_STATUS_ALLOC_FAILED) return cudaErrorMemoryAllocation;
-  return cudaErrorUnknown;
+}  // namespace
+
+namespace {
+
+// Lines of one axis: a field of `planes` planes of N values, each plane seen as
+// [outer][n][inner] (x: inner 1, y: inner n0, z: inner n0 n1); line (p, o, i) has its values at
+// p N + o n inner + i + j inner, j < n.  A block takes `per` lines with consecutive (p, o, i),
+// i fastest, so that for inner > 1 the block's loads of one j are contiguous.
+struct AxisLines {
+  int n, inner, outer, per;
+  int64_t N;
+  int64_t total;  // planes * outer * inner lines
+};
+
+__device__ __forceinline__ int64_t line_base(const AxisLines& a, int64_t l) {
+  const int64_t i = l % a.inner;
+  const int64_t r = l / a.inner;
+  const int64_t o = r % a.outer;
+  const int64_t p = r / a.outer;
+  return p * a.N + o * (int64_t)a.n * a.inner + i;
+}
+
+__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
+
+// Orthonormal DCT-II (INV = false) or DCT-III (INV = true) of the block's lines, power-of-two n.
+// Shared memory: per line n complex values (the FFT) and n reals (the input line).
+// tw[k] = exp(-2 pi i k / n), k < n/2; rot[k] = exp(-i pi k / (2n)), k < n.
+template <bool INV>
+__global__ void __launch_bounds__(256) k_dct_axis_fft(double* __restrict__ v, AxisLines a, int bits,
+                                                      const double2* __restrict__ tw,
+                                                      const double2* __restrict__ rot) {
+  extern __shared__ double2 dsm[];
+  const int n = a.n, per = a.per;
+  double2* buf = dsm;                                                  // [per][n]
+  double* lin = reinterpret_cast<double*>(dsm + (size_t)per * n);      // [per][n]
+  const int64_t l0 = (int64_t)blockIdx.x * per;
+  const int nl = (int)((a.total - l0) < per ? (a.total - l0) : per);
+  const double sq1 = sqrt(1.0 / n), sq2 = sqrt(2.0 / n);
+  // load the lines (j outer, line inner: contiguous when inner > 1)
+  for (int idx = threadIdx.x; idx < per * n; idx += blockDim.x) {
+    const int ll = (a.inner > 1) ? idx % per : idx / n;
+    const int j = (a.inner > 1) ? idx / per : idx % n;
+    if (ll < nl) lin[ll * n + j] = v[line_base(a, l0 + ll) + (int64_t)j * a.inner];
+  }
+  __syncthreads();
+  // FFT input in bit-reversed order
+  for (int idx = threadIdx.x; idx < per * n; idx += blockDim.x) {
+    const int ll = idx / n, k = idx % n;
+    if (ll >= nl) continue;
+    const double* x = lin + ll * n;
+    double2 val;
+    if (!INV) {
+      // v_k: even entries, then odd entries reversed
+      const double xv = (k < n / 2) ? x[2 * k] : x[2 * (n - 1 - k) + 1];
+      val = make_double2(xv, 0.0);
+    } else {
+      // V_k = e^{i pi k/(2n)} (Y_k - i Y_{n-k}),  Y_k = y_k / c_k,  Y_n = 0
+      const double yk = x[k] / (k == 0 ? sq1 : sq2);
+      const double ynk = (k == 0) ? 0.0 : x[n - k] / sq2;
+      const double2 r = rot[k];  // e^{-i pi k/(2n)}: use its conjugate
+      const double cr = r.x, ci = -r.y;
+      // (cr + i ci)(yk - i ynk)
+      val = make_double2(cr * yk + ci * ynk, ci * yk - cr * ynk);
+    }
+    buf[ll * n + bitrev((unsigned)k, bits)] = val;
+  }
+  __syncthreads();
+  // radix-2 stages
+  for (int s = 1; s <= bits; ++s) {
+    const int half = 1 << (s - 1);
+    const int stride = n >> s;  // twiddle index step
+    for (int idx = threadIdx.x; idx < per * (n / 2); idx += blockDim.x) {
+      const int ll = idx / (n / 2), b = idx % (n / 2);
+      if (ll >= nl) continue;
+      const int grp = b / half, pos = b % half;
+      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
+      double2 w = tw[pos * stride];
+      if (INV) w.y = -w.y;
+      double2* line = buf + ll * n;
+      const double2 u = line[i0], t = line[i1];
+      const double2 wt = make_double2(w.x * t.x - w.y * t.y, w.x * t.y + w.y * t.x);
+      line[i0] = make_double2(u.x + wt.x, u.y + wt.y);
+      line[i1] = make_double2(u.x - wt.x, u.y - wt.y);
+    }
+    __syncthreads();
+  }
+  // outputs
+  for (int idx = threadIdx.x; idx < per * n; idx += blockDim.x) {
+    const int ll = (a.inner > 1) ? idx % per : idx / n;
+    const int j = (a.inner > 1) ? idx / per : idx % n;
+    if (ll >= nl) continue;
+    const double2* V = buf + ll * n;
+    double out;
+    if (!INV) {
+      // y_j = c_j Re(e^{-i pi j/(2n)} V_j)
+      const double2 r = rot[j];
+      out = (j == 0 ? sq1 : sq2) * (r.x * V[j].x - r.y * V[j].y);
+    } else {
+      // x_{2m} = v_m, x_{2m+1} = v_{n-1-m}, v = IFFT(V) = (1/n) sum_k V_k e^{+2 pi i m k/n}
+      const int m = (j % 2 == 0) ? j / 2 : n - 1 - j / 2;
+      out = V[m].x / n;
+    }
+    v[line_base(a, l0 + ll) + (int64_t)j * a.inner] = out;
+  }
+}
+
+// Direct sums for any n: y_k = sum_j C_kj x_j (INV = false) or x_j = sum_k C_kj y_k (INV = true),
+// C row-major n x n (C[k n + j]).
+template <bool INV>
+__global__ void __launch_bounds__(256) k_dct_axis_direct(double* __restrict__ v, AxisLines a,
+                                                         const double* __restrict__ C) {
+  extern __shared__ double2 dsm[];
+  double* lin = reinterpret_cast<double*>(dsm);  // [per][n]
+  const int n = a.n, per = a.per;
+  const int64_t l0 = (int64_t)blockIdx.x * per;
+  const int nl = (int)((a.total - l0) < per ? (a.total - l0) : per);
+  for (int idx = threadIdx.x; idx < per * n; idx += blockDim.x) {
+    const int ll = (a.inner > 1) ? idx % per : idx / n;
+    const int j = (a.inner > 1) ? idx / per : idx % n;
+    if (ll < nl) lin[ll * n + j] = v[line_base(a, l0 + ll) + (int64_t)j * a.inner];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < per * n; idx += blockDim.x) {
+    const int ll = (a.inner > 1) ? idx % per : idx / n;
+    const int k = (a.inner > 1) ? idx / per : idx % n;
+    if (ll >= nl) continue;
+    const double* x = lin + ll * n;
+    double acc = 0.0;
+    if (!INV)
+      for (int j = 0; j < n; ++j) acc = fma(C[(int64_t)k * n + j], x[j], acc);
+    else
+      for (int j = 0; j < n; ++j) acc = fma(C[(int64_t)j * n + k], x[j], acc);
+    v[line_base(a, l0 + ll) + (int64_t)k * a.inner] = acc;
+  }
 }
 
 }  // namespace
@@ -79,24 +219,26 @@ cudaError_t blas_error(cublasStatus_t st) {
 struct DctPlan {
   int dim = 0;
   int n[3] = {1, 1, 1};
-  double* C[3] = {nullptr, nullptr, nullptr};   // column-major C[k + n i] = s_k cos(pi k (i + 1/2) / n)
-  double* ev[3] = {nullptr, nullptr, nullptr};  // kappa_a 4 sin^2(pi k / (2 n_a))
-  double* work = nullptr;                       // ell N
-  cublasHandle_t blas = nullptr;
+  int bits[3] = {0, 0, 0};                      // log2 n for power-of-two axes, else 0
+  double2* tw[3] = {nullptr, nullptr, nullptr};   // exp(-2 pi i k/n), k < n/2
+  double2* rot[3] = {nullptr, nullptr, nullptr};  // exp(-i pi k/(2n)), k < n
+  double* C[3] = {nullptr, nullptr, nullptr};     // row-major DCT-II matrix (other lengths)
+  double* ev[3] = {nullptr, nullptr, nullptr};    // kappa_a 4 sin^2(pi k / (2 n_a))
 };
 
 void dct_plan_destroy(DctPlan* p) {
   if (!p) return;
   for (int a = 0; a < 3; ++a) {
+    if (p->tw[a]) cudaFree(p->tw[a]);
+    if (p->rot[a]) cudaFree(p->rot[a]);
     if (p->C[a]) cudaFree(p->C[a]);
     if (p->ev[a]) cudaFree(p->ev[a]);
   }
-  if (p->work) cudaFree(p->work);
-  if (p->blas) cublasDestroy(p->blas);
   delete p;
 }
 
 cudaError_t dct_plan_create(DctPlan** out, const GridDesc& g, int dim, int ell, const double kappa[3]) {
+  (void)ell;
   *out = nullptr;
   DctPlan* p = new DctPlan();
   p->dim = dim;
@@ -107,21 +249,35 @@ cudaError_t dct_plan_create(DctPlan** out, const GridDesc& g, int dim, int ell, 
   const double pi = 3.14159265358979323846;
   for (int a = 0; a < dim && e == cudaSuccess; ++a) {
     const int n = p->n[a];
-    std::vector<double> C((size_t)n * n), ev(n);
+    std::vector<double> ev(n);
     for (int k = 0; k < n; ++k) {
-      const double s = (k == 0) ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
-      for (int i = 0; i < n; ++i) C[(size_t)k + (size_t)n * i] = s * std::cos(pi * k * (i + 0.5) / n);
       const double sn = std::sin(pi * k / (2.0 * n));
       ev[k] = kappa[a] * 4.0 * sn * sn;
     }
-    e = cudaMalloc(&p->C[a], sizeof(double) * C.size());
-    if (e == cudaSuccess) e = cudaMemcpy(p->C[a], C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&p->ev[a], sizeof(double) * n);
+    e = cudaMalloc(&p->ev[a], sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMemcpy(p->ev[a], ev.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    const bool pow2 = n >= 2 && (n & (n - 1)) == 0 && n <= 4096;
+    if (pow2) {
+      int b = 0;
+      while ((1 << b) < n) ++b;
+      p->bits[a] = b;
+      std::vector<double2> tw(n / 2), rot(n);
+      for (int k = 0; k < n / 2; ++k) tw[k] = make_double2(std::cos(2.0 * pi * k / n), -std::sin(2.0 * pi * k / n));
+      for (int k = 0; k < n; ++k) rot[k] = make_double2(std::cos(pi * k / (2.0 * n)), -std::sin(pi * k / (2.0 * n)));
+      if (e == cudaSuccess) e = cudaMalloc(&p->tw[a], sizeof(double2) * tw.size());
+      if (e == cudaSuccess) e = cudaMemcpy(p->tw[a], tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMalloc(&p->rot[a], sizeof(double2) * rot.size());
+      if (e == cudaSuccess) e = cudaMemcpy(p->rot[a], rot.data(), sizeof(double2) * rot.size(), cudaMemcpyHostToDevice);
+    } else {
+      std::vector<double> C((size_t)n * n);
+      for (int k = 0; k < n; ++k) {
+        const double c = (k == 0) ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+        for (int j = 0; j < n; ++j) C[(size_t)k * n + j] = c * std::cos(pi * k * (2.0 * j + 1.0) / (2.0 * n));
+      }
+      if (e == cudaSuccess) e = cudaMalloc(&p->C[a], sizeof(double) * C.size());
+      if (e == cudaSuccess) e = cudaMemcpy(p->C[a], C.data(), sizeof(double) * C.size(), cudaMemcpyHostToDevice);
+    }
   }
-  if (e == cudaSuccess) e = cudaMalloc(&p->work, sizeof(double) * (size_t)ell * (size_t)g.N);
-  if (e == cudaSuccess) e = blas_error(cublasCreate(&p->blas));
-  if (e == cudaSuccess) e = blas_error(cublasSetMathMode(p->blas, CUBLAS_DEFAULT_MATH));
   if (e != cudaSuccess) {
     dct_plan_destroy(p);
     return e;
@@ -131,35 +287,41 @@ cudaError_t dct_plan_create(DctPlan** out, const GridDesc& g, int dim, int ell, 
 }
 
 // Spatial DCT (inverse = false) or its inverse of every plane of v (ell planes of N), in place,
-// through p->work.  Each axis is one strided-batched GEMM with the axis' DCT matrix.
+// one launch per axis.
 static cudaError_t dct_planes(DctPlan* p, int ell, double* v, bool inverse, cudaStream_t s) {
-  const int n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
-  const long long N = (long long)n0 * n1 * n2;
-  const double one = 1.0, zero = 0.0;
-  cublasStatus_t st = cublasSetStream(p->blas, s);
-  double* src = v;
-  double* dst = p->work;
-  const cublasOperation_t tC = inverse ? CUBLAS_OP_T : CUBLAS_OP_N;   // C or C^T applied from the left
-  const cublasOperation_t tCr = inverse ? CUBLAS_OP_N : CUBLAS_OP_T;  // C^T or C applied from the right
-  // x: each plane as a column-major n0 x (n1 n2) matrix M, M <- C_x M (or C_x^T M)
-  if (st == CUBLAS_STATUS_SUCCESS)
-    st = cublasDgemmStridedBatched(p->blas, tC, CUBLAS_OP_N, n0, n1 * n2, n0, &one, p->C[0], n0, 0, src, n0, N,
-                                   &zero, dst, n0, N, ell);
-  std::swap(src, dst);
-  if (p->dim >= 2 && st == CUBLAS_STATUS_SUCCESS) {
-    // y: every z-slab as an n0 x n1 matrix, M <- M C_y^T (or M C_y)
-    st = cublasDgemmStridedBatched(p->blas, CUBLAS_OP_N, tCr, n0, n1, n1, &one, src, n0, (long long)n0 * n1,
-                                   p->C[1], n1, 0, &zero, dst, n0, (long long)n0 * n1, ell * n2);
-    std::swap(src, dst);
+  const int64_t N = (int64_t)p->n[0] * p->n[1] * p->n[2];
+  for (int a = 0; a < p->dim; ++a) {
+    AxisLines al;
+    al.n = p->n[a];
+    al.inner = (a == 0) ? 1 : (a == 1 ? p->n[0] : p->n[0] * p->n[1]);
+    al.outer = (a == 0) ? p->n[1] * p->n[2] : (a == 1 ? p->n[2] : 1);
+    al.N = N;
+    al.total = (int64_t)ell * al.outer * al.inner;
+    const bool fft = p->bits[a] > 0;
+    const size_t per_line = fft ? (size_t)al.n * (sizeof(double2) + sizeof(double)) : (size_t)al.n * sizeof(double);
+    int per = (int)(96 * 1024 / per_line);
+    if (per < 1) per = 1;
+    if (per > 32) per = 32;
+    if ((int64_t)per > al.total) per = (int)al.total;
+    al.per = per;
+    const size_t smem = per_line * per;
+    const unsigned grid = (unsigned)((al.total + per - 1) / per);
+    cudaError_t e;
+    if (fft) {
+      auto k = inverse ? k_dct_axis_fft<true> : k_dct_axis_fft<false>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, 256, smem, s>>>(v, al, p->bits[a], p->tw[a], p->rot[a]);
+    } else {
+      auto k = inverse ? k_dct_axis_direct<true> : k_dct_axis_direct<false>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, 256, smem, s>>>(v, al, p->C[a]);
+    }
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  if (p->dim == 3 && st == CUBLAS_STATUS_SUCCESS) {
-    // z: each plane as an (n0 n1) x n2 matrix, M <- M C_z^T (or M C_z)
-    st = cublasDgemmStridedBatched(p->blas, CUBLAS_OP_N, tCr, n0 * n1, n2, n2, &one, src, n0 * n1, N, p->C[2], n2, 0,
-                                   &zero, dst, n0 * n1, N, ell);
-    std::swap(src, dst);
-  }
-  if (st != CUBLAS_STATUS_SUCCESS) return blas_error(st);
-  if (src != v) return cudaMemcpyAsync(v, src, sizeof(double) * (size_t)ell * N, cudaMemcpyDeviceToDevice, s);
   return cudaSuccess;
 }
 
