@@ -403,6 +403,28 @@ int aao_batch_get_profile(aao_batch hb, int64_t* launches, double* ms, double* b
 /* Copy the statistics of the last solve into *s. */
 int aao_get_stats(aao_handle h, aao_stats* s);
 
+/*
+ * Several right-hand sides of h's operator (Eq. 1 with the same A, ell and
+ * alpha), solved together: b and x are arrays of nrhs DEVICE pointers (ell N
+ * doubles each, block-major), x from x_0 = 0 to explicit relative residual <
+ * tol, at most max_outer Arnoldi steps each.  The right-hand sides advance in
+ * lockstep through right-preconditioned FGMRES, as a batch (aao_batch_*) of
+ * views of h: each view has its own Chebyshev fields and Krylov spaces
+ * (restart as h) and uses h's face coefficients, shifts and step tables, so
+ * each single-step Chebyshev launch loads a tile's stencil once and applies it
+ * to every active right-hand side (on 2D grids the fused sweeps are the
+ * batch's warp-strip launches).  The paper solves one right-hand side at a
+ * time; this is the library's form for covariance operators applied to many
+ * fields.  Needs the mixed path on a 2D or 3D grid with n0 % 4 == 0, P_NC,
+ * inner_its >= 3 (one count for all frequencies) and restart >= 2.  The views
+ * (nrhs x (2 restart + 1) Krylov vectors) are allocated on the first call and
+ * kept on h until nrhs, inner_its or the tables change, or h is destroyed.
+ * Returns AAO_ENOTCONV if some right-hand side did not converge (all x[i] hold
+ * their iterates); aao_multi_get_stats gives right-hand side i's statistics.
+ */
+int aao_solve_multi(aao_handle h, int nrhs, const double* const* b, double* const* x, double tol, int max_outer);
+int aao_multi_get_stats(aao_handle h, int i, aao_stats* s);
+
 /* Spectral bounds used for A: mu_min and mu_max (Lemma 2's segment ends). */
 int aao_get_bounds(aao_handle h, double* mu_min, double* mu_max);
 

@@ -31,7 +31,7 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode",
             "aao_set_stream_config", "aao_get_stream_config", "aao_autotune", "aao_tune_lookup",
             "aao_set_tune_cache", "aao_get_tuning", "aao_batch_set_sweep", "aao_batch_profile_enable",
-            "aao_batch_get_profile")
+            "aao_batch_get_profile", "aao_solve_multi", "aao_multi_get_stats")
 
 # preconditioner of the outer solve (aao_set_precond_mode)
 AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT, AAO_PRECOND_SP = 0, 1, 2
@@ -163,6 +163,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_batch_profile_enable.restype = i32
     lib.aao_batch_get_profile.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.aao_batch_get_profile.restype = i32
+    lib.aao_solve_multi.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp), dbl, i32]
+    lib.aao_solve_multi.restype = i32
+    lib.aao_multi_get_stats.argtypes = [vp, i32, C.POINTER(aao_stats)]
+    lib.aao_multi_get_stats.restype = i32
     lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.aao_set_wait_limit.restype = i32
     lib.aao_set_precond_mode.argtypes = [vp, i32]
@@ -536,6 +540,23 @@ class Solver:
 
     def stream_config(self):
         return aao_get_stream_config(self.h)
+
+    def solve_multi(self, bs, xs, tol, max_outer, allow_notconv=False):
+        """Several right-hand sides of this operator in lockstep (device arrays, ell*N each)."""
+        n = len(bs)
+        if len(xs) != n:
+            raise ValueError("solve_multi: need one x per b (%d), got %d" % (n, len(xs)))
+        pb = (C.c_void_p * n)(*[_ptr(v, self.L, "b[%d]" % i) for i, v in enumerate(bs)])
+        px = (C.c_void_p * n)(*[_ptr(v, self.L, "x[%d]" % i) for i, v in enumerate(xs)])
+        rc = load_library().aao_solve_multi(self.h, n, pb, px, float(tol), int(max_outer))
+        if rc != AAO_OK and not (allow_notconv and rc == AAO_ENOTCONV):
+            _check(self.h, rc)
+        return rc
+
+    def multi_stats(self, i):
+        s = aao_stats()
+        _check(self.h, load_library().aao_multi_get_stats(self.h, int(i), C.byref(s)))
+        return _stats_dict(s)
 
     def autotune(self, reps=3):
         return aao_autotune(self.h, reps)

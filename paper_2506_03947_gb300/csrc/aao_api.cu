@@ -724,6 +724,13 @@ void aao_destroy(aao_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  if (h->multi) aao::multi_destroy(h->multi);
+  h->multi = nullptr;
+  if (!h->owns_coeffs) {
+    // a view: the face arrays belong to the handle it was made from
+    h->cx64 = h->cy64 = h->cz64 = nullptr;
+    h->cx32 = h->cy32 = h->cz32 = nullptr;
+  }
   void* dev[] = {h->cx64, h->cy64, h->cz64, h->cx32, h->cy32, h->cz32, h->bhat, h->xa, h->xb, h->xc,
                  h->xd,   h->V,    h->Z,    h->sc,   h->partials, h->stage_a, h->stage_b, h->counter,
                  h->tma_fault};

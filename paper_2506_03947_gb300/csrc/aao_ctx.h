@@ -10,6 +10,8 @@
 #include "aao.h"
 #include "aao_internal.cuh"
 
+struct aao_multi;  // right-hand-side views of a handle and their batch (multi.cu)
+
 struct aao_ctx {
   int dim = 0;
   int64_t n[3] = {1, 1, 1};
@@ -36,6 +38,8 @@ struct aao_ctx {
   int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
   aao::StreamConfig scfg{};                            // warp-strip kernel configuration
   int auto_kind = AAO_STEP_TMA;                        // the kernel AAO_STEP_AUTO selects
+  bool owns_coeffs = true;                             // false for a view sharing another handle's operator
+  aao_multi* multi = nullptr;                          // cached views of aao_solve_multi
   bool tuned = false;                                  // kernel and configuration from the autotuner
   bool tma_used = false;                               // TMA kernel launched since the last fault check
   long long wait_limit = aao::kQuadTmaWaitCycles;      // bound of the TMA waits (aao_set_wait_limit)
@@ -109,4 +113,6 @@ inline int effective_step_kernel(const aao_ctx* h) {
 StreamConfig default_stream_config(const GridDesc& g, int ell);
 // Apply the tune cache's entry for h, if a cache is configured and holds one (tune.cu).
 void apply_tune_cache(aao_ctx* h);
+// Release the views of aao_solve_multi (multi.cu).
+void multi_destroy(aao_multi* m);
 }  // namespace aao

@@ -40,19 +40,28 @@ __global__ void __launch_bounds__(256) kb_dft(const BInst* __restrict__ I, const
                        gs);
 }
 
+// Member-local block lb of the single-step kernels (32 x 8 threads, four cells per thread along
+// x) as block coordinates (bx, by, bz) of the member's grid.
+__device__ __forceinline__ void step_block(const GridDesc& g, int lb, int& bx, int& by, int& bz) {
+  const int gx = (g.n0 + 127) / 128, gy = (g.n1 + 7) / 8;
+  bx = lb % gx;
+  by = (lb / gx) % gy;
+  bz = lb / (gx * gy);
+}
+
 // Step k = 1 from x_1 = bhat/theta (x_0 = 0): x_2 into field 0, or (LAST, p = 2) the inverse
 // transform into Z_j.
-template <int ELL, bool LAST>
+template <int ELL, int DIM, bool LAST>
 __global__ void __launch_bounds__(256) kb_step_first(const BInst* __restrict__ I, const int* __restrict__ act,
                                                       WorkList wl, int j) {
   const int li = wl_find(wl, blockIdx.x);
   const int inst = wl.inst[li];
   if (!act[inst]) return;
   const BInst& b = I[inst];
-  const int lb = blockIdx.x - wl.start[li];
-  const int gx = (b.g.n0 + 127) / 128;
-  cheb_step_v4_body<ELL, 2, 0, 0, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, nullptr, b.xa,
-                                        b.Z + (int64_t)j * b.L, b.steps[1], *b.ia);
+  int bx, by, bz;
+  step_block(b.g, blockIdx.x - wl.start[li], bx, by, bz);
+  cheb_step_v4_body<ELL, DIM, 0, 0, LAST>(b.g, bx, by, bz, b.cx32, b.cy32, b.cz32, b.bhat, nullptr, b.xa,
+                                          b.Z + (int64_t)j * b.L, b.steps[1], *b.ia);
 }
 
 __device__ __forceinline__ float* field(const BInst& b, int i) {
@@ -79,23 +88,45 @@ __global__ void __launch_bounds__(kQuadTileNT, 2) kb_quad(const BInst* __restric
 
 // One step k from x_k = field cur; x_{k-1} = field io (PSRC 2, overwritten by x_{k+1}) or
 // bhat/theta (PSRC 1, x_{k+1} into field io); LAST: inverse transform into Z_j instead.
-template <int ELL, int PSRC, bool LAST>
+template <int ELL, int DIM, int PSRC, bool LAST>
 __global__ void __launch_bounds__(256) kb_step_f(const BInst* __restrict__ I, const int* __restrict__ act,
                                                   WorkList wl, int k, int j, int cur, int io) {
   const int li = wl_find(wl, blockIdx.x);
   const int inst = wl.inst[li];
   if (!act[inst]) return;
   const BInst& b = I[inst];
-  const int lb = blockIdx.x - wl.start[li];
-  const int gx = (b.g.n0 + 127) / 128;
-  cheb_step_v4_body<ELL, 2, 1, PSRC, LAST>(b.g, lb % gx, lb / gx, 0, b.cx32, b.cy32, nullptr, b.bhat, field(b, cur),
-                                           field(b, io), b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
+  int bx, by, bz;
+  step_block(b.g, blockIdx.x - wl.start[li], bx, by, bz);
+  cheb_step_v4_body<ELL, DIM, 1, PSRC, LAST>(b.g, bx, by, bz, b.cx32, b.cy32, b.cz32, b.bhat, field(b, cur),
+                                             field(b, io), b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
+}
+
+// Members that share one grid and its face coefficients (right-hand sides of one operator):
+// one block per tile of that grid; the tile's stencil is loaded once and applied to every
+// active member's fields.  KSRC 0: step k = 1 from x_1 = bhat/theta into field 0 (or Z_j).
+template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
+__global__ void __launch_bounds__(256) kb_step_shared(const BInst* __restrict__ I, const int* __restrict__ act, int M,
+                                                       int k, int j, int cur, int io) {
+  const BInst& b0 = I[0];
+  int bx, by, bz;
+  step_block(b0.g, blockIdx.x, bx, by, bz);
+  Stencil4<DIM> st;
+  int64_t c = 0;
+  if (!make_stencil4<DIM>(b0.g, bx, by, bz, b0.cx32, b0.cy32, b0.cz32, st, c)) return;
+  for (int r = 0; r < M; ++r) {
+    if (!act[r]) continue;
+    const BInst& b = I[r];
+    const float* xk = (KSRC == 0) ? nullptr : field(b, cur);
+    float* xio = (KSRC == 0) ? b.xa : field(b, io);
+    cheb_step_v4_apply<ELL, DIM, KSRC, PSRC, LAST>(b.g, st, c, b.bhat, xk, xio, b.Z + (int64_t)j * b.L,
+                                                   b.steps[KSRC == 0 ? 1 : k], *b.ia);
+  }
 }
 
 // ---- FP64 outer solve ----------------------------------------------------------
 
 // mode 0: V_{j+1} = script-A Z_j; mode 1: V_0 = b - script-A x with norm partials
-template <int MODE>
+template <int MODE, int DIM>
 __global__ void __launch_bounds__(256) kb_matvec(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl,
                                                   int j) {
   const int li = wl_find(wl, blockIdx.x);
@@ -103,12 +134,13 @@ __global__ void __launch_bounds__(256) kb_matvec(const BInst* __restrict__ I, co
   if (!act[inst]) return;
   const BInst& b = I[inst];
   const int lb = blockIdx.x - wl.start[li];
-  const int gx = (b.g.n0 + 31) / 32;
+  const int gx = (b.g.n0 + 31) / 32, gy = (b.g.n1 + 7) / 8;
+  const int bx = lb % gx, by = (lb / gx) % gy, bz = lb / (gx * gy);
   if (MODE == 0)
-    aao_matvec_body<2, 0>(b.g, b.ell, lb % gx, lb / gx, 0, lb, b.cx64, b.cy64, nullptr, b.Z + (int64_t)j * b.L,
-                          nullptr, b.V + (int64_t)(j + 1) * b.L, nullptr);
+    aao_matvec_body<DIM, 0>(b.g, b.ell, bx, by, bz, lb, b.cx64, b.cy64, b.cz64, b.Z + (int64_t)j * b.L, nullptr,
+                            b.V + (int64_t)(j + 1) * b.L, nullptr);
   else
-    aao_matvec_body<2, 1>(b.g, b.ell, lb % gx, lb / gx, 0, lb, b.cx64, b.cy64, nullptr, b.x, b.b, b.V, b.partials);
+    aao_matvec_body<DIM, 1>(b.g, b.ell, bx, by, bz, lb, b.cx64, b.cy64, b.cz64, b.x, b.b, b.V, b.partials);
 }
 
 template <int G>
@@ -237,11 +269,11 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
   const dim3 blk(32, 8, 1);
   // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in field 0 (or Z_j if p == 2)
   if (p == 2) {
-    kb_step_first<ELL, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
+    kb_step_first<ELL, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
     AAO_BCHECK();
     return cudaSuccess;
   }
-  kb_step_first<ELL, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
+  kb_step_first<ELL, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
   AAO_BCHECK();
   // Four-step launches while steps k .. k+3 all come before the last step; the four fields
   // rotate so that a launch never writes a field it reads (same schedule as the single solver).
@@ -271,57 +303,83 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
   for (; k <= p - 2; ++k) {
     int dst = prev;
     if (dst < 0) dst = (cur == 0) ? 1 : 0;
-    if (prev < 0) kb_step_f<ELL, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
-    else kb_step_f<ELL, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    if (prev < 0) kb_step_f<ELL, 2, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    else kb_step_f<ELL, 2, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
     AAO_BCHECK();
     prev = cur;
     cur = dst;
   }
   // the last step k = p - 1, fused with the inverse transform into Z_j
-  if (prev < 0) kb_step_f<ELL, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
-  else kb_step_f<ELL, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
+  if (prev < 0) kb_step_f<ELL, 2, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
+  else kb_step_f<ELL, 2, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
   AAO_BCHECK();
   return cudaSuccess;
 }
 
-template <int ELL>
-cudaError_t batch_precond_head_ell(const BInst* I, const int* act, const WorkList& wdft, const WorkList& wstep, int p,
-                                   int j, cudaStream_t s) {
+template <int ELL, int DIM>
+cudaError_t batch_precond_head_ell(const BInst* I, const int* act, const SharedSteps& sh, const WorkList& wdft,
+                                   const WorkList& wstep, int p, int j, cudaStream_t s) {
   if (wdft.cnt == 0) return cudaSuccess;
-  if (p < 3) return cudaErrorInvalidValue;  // the fused form needs a step before the last one
+  if (p < 3) return cudaErrorInvalidValue;  // the split schedule needs a step before the last one
   kb_dft<ELL><<<wdft.total, 256, 0, s>>>(I, act, wdft, j);
   AAO_BCHECK();
   const dim3 blk(32, 8, 1);
-  kb_step_first<ELL, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);  // x_2 into field 0
+  if (sh.on) kb_step_shared<ELL, DIM, 0, 0, false><<<sh.ntiles, blk, 0, s>>>(I, act, sh.M, 1, j, 0, 0);
+  else kb_step_first<ELL, DIM, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);  // x_2 into field 0
   AAO_BCHECK();
   return cudaSuccess;
 }
 
-template <int ELL>
-cudaError_t batch_precond_tail_ell(const BInst* I, const int* act, const WorkList& wstep, int p, int j, int k, int cur,
-                                   int prev, cudaStream_t s) {
-  if (wstep.cnt == 0) return cudaSuccess;
+template <int ELL, int DIM>
+cudaError_t batch_steps_mid_ell(const BInst* I, const int* act, const SharedSteps& sh, const WorkList& wstep, int p,
+                                int j, int k, int* curp, int* prevp, cudaStream_t s) {
+  if (!sh.on && wstep.cnt == 0) return cudaSuccess;
   const dim3 blk(32, 8, 1);
+  const unsigned nb = sh.on ? (unsigned)sh.ntiles : (unsigned)wstep.total;
+  int cur = *curp, prev = *prevp;
   for (; k <= p - 2; ++k) {
     int dst = prev;
     if (dst < 0) dst = (cur == 0) ? 1 : 0;
-    if (prev < 0) kb_step_f<ELL, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
-    else kb_step_f<ELL, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    if (sh.on) {
+      if (prev < 0) kb_step_shared<ELL, DIM, 1, 1, false><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, dst);
+      else kb_step_shared<ELL, DIM, 1, 2, false><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, dst);
+    } else {
+      if (prev < 0) kb_step_f<ELL, DIM, 1, false><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+      else kb_step_f<ELL, DIM, 2, false><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    }
     AAO_BCHECK();
     prev = cur;
     cur = dst;
   }
-  if (prev < 0) kb_step_f<ELL, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
-  else kb_step_f<ELL, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
+  *curp = cur;
+  *prevp = prev;
+  return cudaSuccess;
+}
+
+template <int ELL, int DIM>
+cudaError_t batch_step_last_ell(const BInst* I, const int* act, const SharedSteps& sh, const WorkList& wstep, int p,
+                                int j, int cur, int prev, cudaStream_t s) {
+  if (!sh.on && wstep.cnt == 0) return cudaSuccess;
+  const dim3 blk(32, 8, 1);
+  const unsigned nb = sh.on ? (unsigned)sh.ntiles : (unsigned)wstep.total;
+  const int k = p - 1;
+  if (sh.on) {
+    if (prev < 0) kb_step_shared<ELL, DIM, 1, 1, true><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, cur);
+    else kb_step_shared<ELL, DIM, 1, 2, true><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, prev);
+  } else {
+    if (prev < 0) kb_step_f<ELL, DIM, 1, true><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
+    else kb_step_f<ELL, DIM, 2, true><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
+  }
   AAO_BCHECK();
   return cudaSuccess;
 }
 
-cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
-                               int p, int j, cudaStream_t s) {
-  switch (ell) {
-#define AAO_BH(L) \
-  case L: return batch_precond_head_ell<L>(I, act, wdft, wstep, p, j, s);
+cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                               const WorkList& wdft, const WorkList& wstep, int p, int j, cudaStream_t s) {
+  switch (ell * 10 + dim) {
+#define AAO_BH(L)                                                                         \
+  case L * 10 + 2: return batch_precond_head_ell<L, 2>(I, act, sh, wdft, wstep, p, j, s); \
+  case L * 10 + 3: return batch_precond_head_ell<L, 3>(I, act, sh, wdft, wstep, p, j, s);
     AAO_BH(4)
     AAO_BH(6)
     AAO_BH(8)
@@ -334,21 +392,47 @@ cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, const Wo
   }
 }
 
-cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, const WorkList& wstep, int p, int j, int kf,
-                               int cur, int prev, cudaStream_t s) {
-  switch (ell) {
-#define AAO_BT(L) \
-  case L: return batch_precond_tail_ell<L>(I, act, wstep, p, j, kf, cur, prev, s);
-    AAO_BT(4)
-    AAO_BT(6)
-    AAO_BT(8)
-    AAO_BT(10)
-    AAO_BT(12)
-    AAO_BT(14)
-    AAO_BT(16)
-#undef AAO_BT
+cudaError_t batch_steps_mid(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                            const WorkList& wstep, int p, int j, int kf, int* cur, int* prev, cudaStream_t s) {
+  switch (ell * 10 + dim) {
+#define AAO_BM(L)                                                                               \
+  case L * 10 + 2: return batch_steps_mid_ell<L, 2>(I, act, sh, wstep, p, j, kf, cur, prev, s); \
+  case L * 10 + 3: return batch_steps_mid_ell<L, 3>(I, act, sh, wstep, p, j, kf, cur, prev, s);
+    AAO_BM(4)
+    AAO_BM(6)
+    AAO_BM(8)
+    AAO_BM(10)
+    AAO_BM(12)
+    AAO_BM(14)
+    AAO_BM(16)
+#undef AAO_BM
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t batch_step_last(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                            const WorkList& wstep, int p, int j, int cur, int prev, cudaStream_t s) {
+  switch (ell * 10 + dim) {
+#define AAO_BL(L)                                                                            \
+  case L * 10 + 2: return batch_step_last_ell<L, 2>(I, act, sh, wstep, p, j, cur, prev, s); \
+  case L * 10 + 3: return batch_step_last_ell<L, 3>(I, act, sh, wstep, p, j, cur, prev, s);
+    AAO_BL(4)
+    AAO_BL(6)
+    AAO_BL(8)
+    AAO_BL(10)
+    AAO_BL(12)
+    AAO_BL(14)
+    AAO_BL(16)
+#undef AAO_BL
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                               const WorkList& wstep, int p, int j, int kf, int cur, int prev, cudaStream_t s) {
+  cudaError_t e = batch_steps_mid(I, act, ell, dim, sh, wstep, p, j, kf, &cur, &prev, s);
+  if (e != cudaSuccess) return e;
+  return batch_step_last(I, act, ell, dim, sh, wstep, p, j, cur, prev, s);
 }
 
 cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
@@ -365,10 +449,20 @@ cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkLis
   }
 }
 
-cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, cudaStream_t s) {
+int batch_step_blocks(const GridDesc& g) { return ((g.n0 + 127) / 128) * ((g.n1 + 7) / 8) * g.n2; }
+
+int batch_matvec_blocks(const GridDesc& g) { return ((g.n0 + 31) / 32) * ((g.n1 + 7) / 8) * g.n2; }
+
+cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, int dim,
+                         cudaStream_t s) {
   const dim3 blk(32, 8, 1);
-  if (mode == 0) kb_matvec<0><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
-  else kb_matvec<1><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+  if (dim == 3) {
+    if (mode == 0) kb_matvec<0, 3><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+    else kb_matvec<1, 3><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+  } else {
+    if (mode == 0) kb_matvec<0, 2><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+    else kb_matvec<1, 2><<<wmv.total, blk, 0, s>>>(I, act, wmv, j);
+  }
   AAO_BCHECK();
   return cudaSuccess;
 }

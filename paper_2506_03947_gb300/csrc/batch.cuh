@@ -19,8 +19,8 @@ struct BInst {
   GridDesc g;
   int ell, m, nbred, nbmv, nbmgs;  // reduction, matvec and modified Gram-Schmidt blocks
   int64_t L;
-  const float *cx32, *cy32;
-  const double *cx64, *cy64;
+  const float *cx32, *cy32, *cz32;
+  const double *cx64, *cy64, *cz64;
   float *bhat, *xa, *xb, *xc, *xd;  // transformed rhs and the four rotating Chebyshev fields
   double *V, *Z, *sc, *partials;
   unsigned* counter;             // the member's last-block ticket (modified Gram-Schmidt)
@@ -38,7 +38,8 @@ int batch_quad_tiles(const GridDesc& g);
 // steps for the rest (list wstep), the last step fused with the inverse transform into Z_j.
 cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
                           const WorkList& wquad, int p, int j, cudaStream_t s);
-cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, cudaStream_t s);
+cudaError_t batch_matvec(const BInst* I, const int* act, const WorkList& wmv, int mode, int j, int dim,
+                         cudaStream_t s);
 cudaError_t batch_gram_schmidt(const BInst* I, const int* act, const WorkList& wred, const WorkList& wone, int j,
                                cudaStream_t s);
 // Modified Gram-Schmidt of Arnoldi step j: j + 2 fused launches over the list (one per basis
@@ -57,10 +58,30 @@ cudaError_t batch_xupdate(const BInst* I, const int* act, const WorkList& wred, 
 // caller's warp-strip launches (launch_batch_stream) for steps 2 .. kf-1, and
 // batch_precond_tail (single steps kf .. p-2 and the last step with the inverse transform,
 // per ell), with x_k in field cur and x_{k-1} in field prev (-1: bhat/theta) at kf.
-cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,
-                               int p, int j, cudaStream_t s);
-cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, const WorkList& wstep, int p, int j, int kf,
-                               int cur, int prev, cudaStream_t s);
+// dim: 2 or 3 (every member).  shared: every member has the same grid and face coefficients
+// (right-hand sides of one operator); the step kernels then take one block per tile of that
+// grid, load the tile's stencil once and apply it to every active member (M members,
+// ntiles = the tile count of the grid), and wstep is not used.
+struct SharedSteps {
+  bool on;
+  int M;
+  int ntiles;
+};
+cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                               const WorkList& wdft, const WorkList& wstep, int p, int j, cudaStream_t s);
+cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                               const WorkList& wstep, int p, int j, int kf, int cur, int prev, cudaStream_t s);
+// The middle single steps k = kf .. p-2 alone (no last step): cur and prev are updated to the
+// fields holding x_{p-1} and x_{p-2} (prev -1: bhat/theta).  batch_step_last then runs the last
+// step with the inverse transform.  Together they are batch_precond_tail.
+cudaError_t batch_steps_mid(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                            const WorkList& wstep, int p, int j, int kf, int* cur, int* prev, cudaStream_t s);
+cudaError_t batch_step_last(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
+                            const WorkList& wstep, int p, int j, int cur, int prev, cudaStream_t s);
+// Blocks of the single-step kernels (32 x 8 threads, four cells each along x) for one grid.
+int batch_step_blocks(const GridDesc& g);
+// Blocks of the matvec kernel (32 x 8 threads, one cell each) for one grid.
+int batch_matvec_blocks(const GridDesc& g);
 
 // Device work queue of a batched warp-strip launch: tickets are taken from next; each warp
 // adds one to done when it leaves, and the last one resets both (zero between launches).

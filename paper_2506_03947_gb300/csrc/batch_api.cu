@@ -19,6 +19,9 @@ void count_launch_add(long long n);
 
 using aao::is_device_ptr;
 
+// Batch sweep without fused launches: one Chebyshev step per launch (3D members).
+constexpr int kSweepSingle = -1;
+
 // ---- batched solve -----------------------------------------------------------------
 
 struct aao_batch_ctx {
@@ -38,7 +41,9 @@ struct aao_batch_ctx {
   aao::WorkList wmv{}, wred{}, wone{}, wmgs{};
   // fused sweeps: one warp-strip launch over the units of all members (any ell), from a device
   // queue (sweep = AAO_STEP_STREAM), or the shared-memory tile kernel per ell (AAO_STEP_TILE)
-  int sweep = AAO_STEP_STREAM;
+  int sweep = AAO_STEP_STREAM;  // AAO_STEP_STREAM, AAO_STEP_TILE or kSweepSingle
+  int dim = 2;                  // every member's
+  aao::SharedSteps shared{false, 0, 0};  // right-hand sides of one operator
   aao::StreamConfig scfg{};
   aao::WorkList wunits{};
   aao::StreamQueue* queue = nullptr;
@@ -108,7 +113,8 @@ double fused_bytes(const aao_batch_ctx* B, int psrc) {
 int batch_precond_stream(aao_batch_ctx* B, int j) {
   cudaStream_t s = B->stream;
   for (size_t g = 0; g < B->wdft.size(); ++g)
-    AAO_BCK(B, aao::batch_precond_head(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second, B->p,
+    AAO_BCK(B, aao::batch_precond_head(B->dI, B->dact, B->wdft[g].first, B->dim, B->shared, B->wdft[g].second,
+                                       B->wstep[g].second, B->p,
                                        j, s));
   // fused launches while steps k .. k+S-1 all come before the last step; the four fields rotate
   // so that a launch never writes a field it reads (the single solver's schedule)
@@ -137,7 +143,8 @@ int batch_precond_stream(aao_batch_ctx* B, int j) {
     k += S;
   }
   for (size_t g = 0; g < B->wstep.size(); ++g)
-    AAO_BCK(B, aao::batch_precond_tail(B->dI, B->dact, B->wstep[g].first, B->wstep[g].second, B->p, j, k, cur, prev,
+    AAO_BCK(B, aao::batch_precond_tail(B->dI, B->dact, B->wstep[g].first, B->dim, B->shared, B->wstep[g].second,
+                                       B->p, j, k, cur, prev,
                                        s));
   return AAO_OK;
 }
@@ -160,12 +167,20 @@ int batch_step_launches(aao_batch_ctx* B, int j) {
   if (B->sweep == AAO_STEP_STREAM) {
     const int rc = batch_precond_stream(B, j);
     if (rc) return rc;
+  } else if (B->sweep == kSweepSingle) {
+    // one Chebyshev step per launch: transform and step 1, then steps 2 .. p-1
+    for (size_t g = 0; g < B->wdft.size(); ++g)
+      AAO_BCK(B, aao::batch_precond_head(B->dI, B->dact, B->wdft[g].first, B->dim, B->shared, B->wdft[g].second,
+                                         B->wstep[g].second, B->p, j, s));
+    for (size_t g = 0; g < B->wstep.size(); ++g)
+      AAO_BCK(B, aao::batch_precond_tail(B->dI, B->dact, B->wstep[g].first, B->dim, B->shared, B->wstep[g].second,
+                                         B->p, j, 2, 0, -1, s));
   } else {
     for (size_t g = 0; g < B->wdft.size(); ++g)
       AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second,
                                     B->wquad[g].second, B->p, j, s));
   }
-  AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 0, j, s));
+  AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 0, j, B->dim, s));
   if (B->mgs) AAO_BCK(B, aao::batch_mgs(B->dI, B->dact, B->wmgs, j, s));
   else AAO_BCK(B, aao::batch_gram_schmidt(B->dI, B->dact, B->wred, B->wone, j, s));
   AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 0, j, B->dkvec, B->dout, s));
@@ -245,8 +260,10 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
   for (int i = 0; i < count; ++i) {
     const aao_ctx* h = members[i];
     if (!h) return bfail(nullptr, AAO_EINVAL, "member %d is NULL", i);
-    if (h->prec != AAO_MIXED || h->dim != 2 || h->n[0] % 4 != 0)
-      return bfail(nullptr, AAO_EINVAL, "member %d: the batch runs mixed-precision 2D grids with n0 %% 4 == 0", i);
+    if (h->prec != AAO_MIXED || (h->dim != 2 && h->dim != 3) || h->n[0] % 4 != 0)
+      return bfail(nullptr, AAO_EINVAL, "member %d: the batch runs mixed-precision 2D or 3D grids with n0 %% 4 == 0", i);
+    if (h->dim != members[0]->dim) return bfail(nullptr, AAO_EINVAL, "members must share the grid dimension");
+    if (h->dim == 3 && h->p < 3) return bfail(nullptr, AAO_EINVAL, "member %d: 3D batches need inner_its >= 3", i);
     if (h->p < 2) return bfail(nullptr, AAO_EINVAL, "member %d: the batch needs inner_its >= 2", i);
     if (h->p != members[0]->p || h->m != members[0]->m)
       return bfail(nullptr, AAO_EINVAL, "members must share inner_its and restart (member %d differs)", i);
@@ -285,11 +302,13 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     bi.L = h->L;
     bi.nbred = aao::reduction_blocks(h->L);
     bi.nbmgs = aao::batch_mgs_blocks(h->L);
-    bi.nbmv = (int)(((h->n[0] + 31) / 32) * ((h->n[1] + 7) / 8));
+    bi.nbmv = aao::batch_matvec_blocks(h->g);
     bi.cx32 = h->cx32;
     bi.cy32 = h->cy32;
+    bi.cz32 = h->cz32;
     bi.cx64 = h->cx64;
     bi.cy64 = h->cy64;
+    bi.cz64 = h->cz64;
     bi.bhat = (float*)h->bhat;
     bi.xa = (float*)h->xa;
     bi.xb = (float*)h->xb;
@@ -321,7 +340,7 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     bi.x = nullptr;
     all[i] = i;
     bdft[i] = (int)((h->N + 255) / 256);
-    bstep[i] = (int)(((h->n[0] + 127) / 128) * ((h->n[1] + 7) / 8));
+    bstep[i] = aao::batch_step_blocks(h->g);
     bquad[i] = aao::batch_quad_tiles(h->g);
     bmv[i] = bi.nbmv;
     bred[i] = bi.nbred;
@@ -349,7 +368,23 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
   B->scfg.H = 64;
   B->scfg.D = 3;
   B->scfg.NW = 8;
+  B->dim = members[0]->dim;
   if (B->p < 7) B->sweep = AAO_STEP_TILE;  // no step of the fused form would fit
+  if (B->dim == 3) B->sweep = kSweepSingle;  // the fused kernels are 2D
+  {
+    // right-hand sides of one operator: same grid, same face arrays (and the same step tables)
+    bool same = true;
+    for (int i = 1; i < count && same; ++i) {
+      const aao_ctx* a = members[i];
+      const aao_ctx* b0 = members[0];
+      same = a->g.n0 == b0->g.n0 && a->g.n1 == b0->g.n1 && a->g.n2 == b0->g.n2 && a->cx32 == b0->cx32 &&
+             a->cy32 == b0->cy32 && a->cz32 == b0->cz32 && a->ell == b0->ell && a->alpha == b0->alpha &&
+             a->mu_max == b0->mu_max;
+    }
+    B->shared.on = same && count > 1;
+    B->shared.M = count;
+    B->shared.ntiles = aao::batch_step_blocks(members[0]->g);
+  }
   {
     std::vector<int> nunits(count);
     for (int i = 0; i < count; ++i) nunits[i] = aao::batch_stream_units(members[i]->g, members[i]->ell, 4, B->scfg.H);
@@ -412,7 +447,7 @@ int aao_batch_solve(aao_batch B, const double* const* b, double* const* x, doubl
     for (int i = 0; i < M; ++i) act[i] = !done[i];
     if (std::none_of(act.begin(), act.end(), [](int v) { return v; })) break;
     if ((rc = batch_set_active(B, act))) return rc;
-    AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 1, 0, B->stream));
+    AAO_BCK(B, aao::batch_matvec(B->dI, B->dact, B->wmv, 1, 0, B->dim, B->stream));
     AAO_BCK(B, aao::batch_reduce(B->dI, B->dact, B->wone, 3, B->stream));
     AAO_BCK(B, aao::batch_small(B->dI, B->dact, B->wone, 5, 0, B->dkvec, B->dout, B->stream));
     if ((rc = batch_read(B))) return rc;
@@ -489,7 +524,12 @@ const char* aao_batch_last_error(aao_batch B) { return B ? B->err.c_str() : g_cr
 
 int aao_batch_set_sweep(aao_batch B, int kind, int S, int H, int D, int NW) {
   if (!B) return bfail(nullptr, AAO_EINVAL, "NULL batch");
-  if (kind == AAO_STEP_TILE) {
+  if (B->dim == 3 && kind != AAO_STEP_AUTO)
+    return bfail(B, AAO_EINVAL, "3D batches run single steps only (AAO_STEP_AUTO)");
+  if (kind == AAO_STEP_AUTO) {
+    if (B->p < 3) return bfail(B, AAO_EINVAL, "single-step sweeps need inner_its >= 3");
+    B->sweep = kSweepSingle;
+  } else if (kind == AAO_STEP_TILE) {
     B->sweep = kind;
   } else if (kind == AAO_STEP_STREAM) {
     aao::StreamConfig c;

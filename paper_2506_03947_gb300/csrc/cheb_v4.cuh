@@ -77,24 +77,21 @@ __device__ __forceinline__ F4 apply_A4(const float* __restrict__ p, int64_t c, i
   return a;
 }
 
-// Body of one block (bx, by, bz) of the step; shared by the single-instance and
-// the batched kernels.
-template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
-__device__ __forceinline__ void cheb_step_v4_body(const GridDesc& g, int bx, int by, int bz,
-                                                  const float* __restrict__ cx, const float* __restrict__ cy,
-                                                  const float* __restrict__ cz, const float* __restrict__ bhat,
-                                                  const float* __restrict__ xk, float* xio,
-                                                  double* __restrict__ z, const StepArgs<float>& sa,
-                                                  const IdftArgs<float>& ia) {
+// The thread's four cells of block (bx, by, bz): their first cell index and the face
+// coefficients of the stencil (loaded once; the multi-right-hand-side kernels apply them to
+// several fields).  Returns false when the thread's row is outside the grid (uniform across a
+// warp, which shares j and k).
+template <int DIM>
+__device__ __forceinline__ bool make_stencil4(const GridDesc& g, int bx, int by, int bz, const float* __restrict__ cx,
+                                              const float* __restrict__ cy, const float* __restrict__ cz,
+                                              Stencil4<DIM>& st, int64_t& c) {
   const int lane = threadIdx.x & 31;
   const int i0 = (bx * blockDim.x + threadIdx.x) * 4;
   const int j = by * blockDim.y + threadIdx.y;
   const int k = bz;
-  if (j >= g.n1) return;  // uniform across the warp (a warp shares j and k)
-  const int64_t N = g.N;
+  if (j >= g.n1) return false;
   const int64_t pl = (int64_t)g.n0 * g.n1;
-  const int64_t c = (int64_t)g.n0 * (j + (int64_t)g.n1 * k) + i0;
-  Stencil4<DIM> st;
+  c = (int64_t)g.n0 * (j + (int64_t)g.n1 * k) + i0;
   st.act = i0 < g.n0;
   st.west = i0 > 0;
   st.east = i0 + 4 < g.n0;
@@ -117,6 +114,17 @@ __device__ __forceinline__ void cheb_step_v4_body(const GridDesc& g, int bx, int
     st.kU = st.act ? ld4(cz + c) : zero4();
     st.kD = (st.act && k > 0) ? ld4(cz + c - pl) : zero4();
   }
+  return true;
+}
+
+// One Chebyshev step of one field set on the thread's four cells (stencil from make_stencil4).
+template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
+__device__ __forceinline__ void cheb_step_v4_apply(const GridDesc& g, const Stencil4<DIM>& st, int64_t c,
+                                                   const float* __restrict__ bhat, const float* __restrict__ xk,
+                                                   float* xio, double* __restrict__ z, const StepArgs<float>& sa,
+                                                   const IdftArgs<float>& ia) {
+  const int lane = threadIdx.x & 31;
+  const int64_t N = g.N;
   const float* src = (KSRC == 0) ? bhat : xk;
 
   float zt[LAST ? 4 : 1][LAST ? ELL : 1];
@@ -241,6 +249,21 @@ __device__ __forceinline__ void cheb_step_v4_body(const GridDesc& g, int bx, int
       }
     }
   }
+}
+
+// Body of one block (bx, by, bz) of the step; shared by the single-instance and
+// the batched kernels.
+template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
+__device__ __forceinline__ void cheb_step_v4_body(const GridDesc& g, int bx, int by, int bz,
+                                                  const float* __restrict__ cx, const float* __restrict__ cy,
+                                                  const float* __restrict__ cz, const float* __restrict__ bhat,
+                                                  const float* __restrict__ xk, float* xio,
+                                                  double* __restrict__ z, const StepArgs<float>& sa,
+                                                  const IdftArgs<float>& ia) {
+  Stencil4<DIM> st;
+  int64_t c = 0;
+  if (!make_stencil4<DIM>(g, bx, by, bz, cx, cy, cz, st, c)) return;
+  cheb_step_v4_apply<ELL, DIM, KSRC, PSRC, LAST>(g, st, c, bhat, xk, xio, z, sa, ia);
 }
 
 template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>

@@ -116,3 +116,30 @@ def test_solves_full_size_3d(problem, block_op):
     log_record({"test": "mixed_vs_fp64_fullsize_3d", "its32": its32, "its64": its64, "rel_diff": d})
     assert its32 <= its64 + 2
     assert d <= 1e-7
+
+
+def test_multi_rhs_full_size_3d(problem, block_op):
+    # the eight right-hand sides of the workload together (aao_solve_multi): every residual
+    # certified by the oracle's script-A, the same iterations as a single solve (+-1), and the
+    # first and last solutions equal to the single solves' to solver tolerance
+    torch = torch_cuda()
+    P = problem
+    s = make_solver(P, 1, P_INNER)
+    bs = [to_dev(P.b[i]) for i in range(P.b.shape[0])]
+    xs = [torch.zeros_like(b) for b in bs]
+    s.solve_multi(bs, xs, 1e-8, 64)
+    its = []
+    for i in range(len(bs)):
+        st = s.multi_stats(i)
+        x = xs[i].cpu().numpy()
+        res = np.linalg.norm(P.b[i] - allatonce.aao_apply(block_op, x)) / np.linalg.norm(P.b[i])
+        log_record({"test": "multi_rhs_fullsize_3d", "rhs": i, "its": st["outer_its"], "resid": res})
+        assert st["converged"] and res <= 1e-8
+        its.append(st["outer_its"])
+    for i in (0, len(bs) - 1):
+        x1 = torch.zeros_like(bs[i])
+        s.solve(bs[i], x1, 1e-8, 64)
+        assert abs(s.stats()["outer_its"] - its[i]) <= 1
+        d = float(torch.linalg.norm(x1 - xs[i]) / torch.linalg.norm(x1))
+        assert d <= 1e-7, d
+    s.close()
