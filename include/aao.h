@@ -216,15 +216,26 @@ int aao_set_inner_alloc(aao_handle h, const int32_t* p, int ell);
 int aao_set_step_kernel(aao_handle h, int kind);
 /*
  * Configuration of the warp-strip kernel (AAO_STEP_STREAM): S fused Chebyshev
- * steps per launch (the halo width; 4), H interior rows per segment (H + 2S a
- * multiple of 3), D rows prefetched ahead (3 or 4) and NW warps per CTA
- * (D = 3: 8, 12 or 13; D = 4: 8, 10 or 11).  No counterpart in the paper:
- * these are launch parameters of this library's kernel (Eq. 7's steps are
- * unchanged).  AAO_EINVAL for an unsupported combination.
+ * steps per launch (the halo width; 2 or 4), H interior rows per segment
+ * (1 <= H <= 4096, H + 2S a multiple of 6), D rows prefetched ahead (3 or 4)
+ * and NW warps per CTA (S = 4: 6 or 8; S = 2: 8, 12 or 16).  No counterpart
+ * in the paper: these are launch parameters of this library's kernel (Eq. 7's
+ * steps are unchanged).  AAO_EINVAL for an unsupported combination.
  * aao_get_stream_config writes (S, H, D, NW) to out[0..3].
+ *
+ * With the warp-strip kernel the sweep runs steps 2 .. p-1 (step 1 and, when
+ * their count p - 2 is odd, step 2 run alone): launches of S steps, and with
+ * S = 4 and a remainder of two steps one two-step launch configured by
+ * aao_set_stream_tail (H + 4 a multiple of 6, D in {3, 4}, NW in {8, 12, 16};
+ * default: D = 3, NW = 16 and the height that fills one round of the device's
+ * warps).  The final launch writes x_p alone and a separate kernel applies
+ * Eq. 5's inverse transform and Gamma^{-1} to it.  aao_get_stream_tail writes
+ * (H, D, NW) to out[0..2].
  */
 int aao_set_stream_config(aao_handle h, int S, int H, int D, int NW);
 int aao_get_stream_config(aao_handle h, int32_t out[4]);
+int aao_set_stream_tail(aao_handle h, int H, int D, int NW);
+int aao_get_stream_tail(aao_handle h, int32_t out[3]);
 
 /*
  * Autotuner of the fused sweep (no counterpart in the paper: the method's steps are
@@ -233,7 +244,11 @@ int aao_get_stream_config(aao_handle h, int32_t out[4]);
  * segment heights that fill one to three rounds of the device's warps (and one segment per
  * strip), D in {3, 4} and each supported NW.  Each candidate runs reps + 1 preconditioner
  * applies on the handle's own staging buffers (the first untimed) and is timed by CUDA events
- * on the handle's stream; the fastest becomes what AAO_STEP_AUTO selects on h.
+ * on the handle's stream; the fastest becomes what AAO_STEP_AUTO selects on h.  When the
+ * winner is the warp-strip kernel with S = 4 and the sweep ends in a two-step launch, the
+ * two-step configurations (NW in {8, 12, 16}, D in {3, 4}, one to three rounds of units) are
+ * timed next under the winner (entries with tail = 1) and the fastest becomes h's tail
+ * (aao_set_stream_tail).
  *   results, max_results: optional array receiving up to max_results candidates with their
  *                  mean time per apply in microseconds (us_per_apply < 0: did not run);
  *   n_results:     optional, receives the number of candidates; best: optional, the winner.
@@ -243,7 +258,7 @@ int aao_get_stream_config(aao_handle h, int32_t out[4]);
 typedef struct {
   int32_t kind;         /* AAO_STEP_TILE, AAO_STEP_TMA or AAO_STEP_STREAM */
   int32_t S, H, D, NW;  /* warp-strip configuration (S = 4 and zeros for the other kernels) */
-  int32_t pad;
+  int32_t tail;         /* 1: a two-step final launch (S = 2) timed under the best sweep */
   double us_per_apply;  /* mean time of one preconditioner apply */
 } aao_tune_entry;
 int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_results, int* n_results,
@@ -390,12 +405,17 @@ void aao_batch_destroy(aao_batch hb);
  */
 int aao_batch_set_sweep(aao_batch hb, int kind, int S, int H, int D, int NW);
 /*
- * Event timing of the batch's fused-sweep launches (graphs are not used while
- * it is on; turning it on or off clears the totals).  aao_batch_get_profile
- * synchronises the batch stream and writes the number of timed launches, their
- * total milliseconds and their algorithmic bytes (x_k, x_{k-1} or none, bhat
- * and two face arrays read and two fields written, 4-byte values, over the
- * members active in each launch).
+ * Event timing of the batch's Chebyshev sweeps (graphs are not used while it
+ * is on; turning it on or off clears the totals).  With a fused sweep each
+ * fused launch is timed: x_k, x_{k-1} or none, bhat and two face arrays read
+ * and two fields written.  With single steps (the default, and every 3D batch)
+ * the middle steps k = 2 .. p-2 of each ell group are timed as one span of
+ * p - 3 launches: x_k, x_{k-1} (none at k = 2) and bhat read and x_{k+1}
+ * written per member, and the dim face arrays once per member, or once for
+ * the whole group when the members share one operator.  4-byte values, over
+ * the members active in each launch.  aao_batch_get_profile synchronises the
+ * batch stream and writes the number of timed launches, their total
+ * milliseconds and their algorithmic bytes.
  */
 int aao_batch_profile_enable(aao_batch hb, int on);
 int aao_batch_get_profile(aao_batch hb, int64_t* launches, double* ms, double* bytes);
@@ -424,6 +444,14 @@ int aao_get_stats(aao_handle h, aao_stats* s);
  */
 int aao_solve_multi(aao_handle h, int nrhs, const double* const* b, double* const* x, double tol, int max_outer);
 int aao_multi_get_stats(aao_handle h, int i, aao_stats* s);
+/*
+ * Event timing of the Chebyshev sweeps of aao_solve_multi on h (the batch
+ * profile above, applied to the right-hand sides' batch; the totals restart
+ * when the views are rebuilt).  aao_multi_get_profile writes zeros before the
+ * first aao_solve_multi.
+ */
+int aao_multi_profile_enable(aao_handle h, int on);
+int aao_multi_get_profile(aao_handle h, int64_t* launches, double* ms, double* bytes);
 
 /* Spectral bounds used for A: mu_min and mu_max (Lemma 2's segment ends). */
 int aao_get_bounds(aao_handle h, double* mu_min, double* mu_max);

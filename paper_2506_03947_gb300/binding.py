@@ -29,9 +29,11 @@ EXPORTED = ("aao_default_options", "aao_create", "aao_matvec", "aao_precond_appl
             "aao_set_inner_alloc", "aao_assign_iterations", "aao_solve_ci", "aao_batch_create",
             "aao_batch_solve", "aao_batch_get_stats", "aao_batch_last_error", "aao_batch_destroy",
             "aao_set_step_kernel", "aao_get_step_kernel", "aao_set_wait_limit", "aao_set_precond_mode",
-            "aao_set_stream_config", "aao_get_stream_config", "aao_autotune", "aao_tune_lookup",
+            "aao_set_stream_config", "aao_get_stream_config", "aao_set_stream_tail", "aao_get_stream_tail",
+            "aao_autotune", "aao_tune_lookup",
             "aao_set_tune_cache", "aao_get_tuning", "aao_batch_set_sweep", "aao_batch_profile_enable",
-            "aao_batch_get_profile", "aao_solve_multi", "aao_multi_get_stats")
+            "aao_batch_get_profile", "aao_solve_multi", "aao_multi_get_stats", "aao_multi_profile_enable",
+            "aao_multi_get_profile")
 
 # preconditioner of the outer solve (aao_set_precond_mode)
 AAO_PRECOND_NC, AAO_PRECOND_EXACT_DCT, AAO_PRECOND_SP = 0, 1, 2
@@ -70,7 +72,7 @@ class aao_stats(C.Structure):
 
 class aao_tune_entry(C.Structure):
     _fields_ = [("kind", C.c_int32), ("S", C.c_int32), ("H", C.c_int32), ("D", C.c_int32), ("NW", C.c_int32),
-                ("pad", C.c_int32), ("us_per_apply", C.c_double)]
+                ("tail", C.c_int32), ("us_per_apply", C.c_double)]
 
 
 class aao_profile(C.Structure):
@@ -148,6 +150,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_set_stream_config.restype = i32
     lib.aao_get_stream_config.argtypes = [vp, C.POINTER(C.c_int32)]
     lib.aao_get_stream_config.restype = i32
+    lib.aao_set_stream_tail.argtypes = [vp, i32, i32, i32]
+    lib.aao_set_stream_tail.restype = i32
+    lib.aao_get_stream_tail.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.aao_get_stream_tail.restype = i32
     lib.aao_autotune.argtypes = [vp, i32, C.POINTER(aao_tune_entry), i32, C.POINTER(i32), C.POINTER(aao_tune_entry)]
     lib.aao_autotune.restype = i32
     lib.aao_tune_lookup.argtypes = [C.c_char_p, C.c_char_p, i32, C.POINTER(C.c_int64), i32, i32, i32,
@@ -167,6 +173,10 @@ def load_library(path: Optional[str] = None) -> C.CDLL:
     lib.aao_solve_multi.restype = i32
     lib.aao_multi_get_stats.argtypes = [vp, i32, C.POINTER(aao_stats)]
     lib.aao_multi_get_stats.restype = i32
+    lib.aao_multi_profile_enable.argtypes = [vp, i32]
+    lib.aao_multi_profile_enable.restype = i32
+    lib.aao_multi_get_profile.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.aao_multi_get_profile.restype = i32
     lib.aao_set_wait_limit.argtypes = [vp, C.c_int64]
     lib.aao_set_wait_limit.restype = i32
     lib.aao_set_precond_mode.argtypes = [vp, i32]
@@ -352,12 +362,22 @@ def aao_get_stream_config(h):
     return {"S": out[0], "H": out[1], "D": out[2], "NW": out[3]}
 
 
+def aao_set_stream_tail(h, H: int, D: int, NW: int) -> int:
+    return _check(h, load_library().aao_set_stream_tail(h, int(H), int(D), int(NW)))
+
+
+def aao_get_stream_tail(h):
+    out = (C.c_int32 * 3)()
+    _check(h, load_library().aao_get_stream_tail(h, out))
+    return {"S": 2, "H": out[0], "D": out[1], "NW": out[2]}
+
+
 KERNEL_NAMES = {AAO_STEP_AUTO: "auto", AAO_STEP_TILE: "tile", AAO_STEP_TMA: "tma", AAO_STEP_STREAM: "stream"}
 
 
 def _tune_dict(e):
     return {"kernel": KERNEL_NAMES.get(e.kind, str(e.kind)), "S": e.S, "H": e.H, "D": e.D, "NW": e.NW,
-            "us_per_apply": e.us_per_apply}
+            "tail": bool(e.tail), "us_per_apply": e.us_per_apply}
 
 
 def aao_autotune(h, reps: int = 3, max_results: int = 256):
@@ -541,6 +561,12 @@ class Solver:
     def stream_config(self):
         return aao_get_stream_config(self.h)
 
+    def set_stream_tail(self, H, D=3, NW=16):
+        return aao_set_stream_tail(self.h, H, D, NW)
+
+    def stream_tail(self):
+        return aao_get_stream_tail(self.h)
+
     def solve_multi(self, bs, xs, tol, max_outer, allow_notconv=False):
         """Several right-hand sides of this operator in lockstep (device arrays, ell*N each)."""
         n = len(bs)
@@ -557,6 +583,17 @@ class Solver:
         s = aao_stats()
         _check(self.h, load_library().aao_multi_get_stats(self.h, int(i), C.byref(s)))
         return _stats_dict(s)
+
+    def multi_profile_enable(self, on=True):
+        """Event timing of the Chebyshev sweeps of solve_multi (graphs off meanwhile)."""
+        _check(self.h, load_library().aao_multi_profile_enable(self.h, 1 if on else 0))
+
+    def multi_profile(self):
+        n = C.c_int64(0)
+        ms = C.c_double(0.0)
+        by = C.c_double(0.0)
+        _check(self.h, load_library().aao_multi_get_profile(self.h, C.byref(n), C.byref(ms), C.byref(by)))
+        return {"launches": n.value, "ms": ms.value, "bytes": by.value}
 
     def autotune(self, reps=3):
         return aao_autotune(self.h, reps)

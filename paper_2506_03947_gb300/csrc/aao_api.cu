@@ -192,10 +192,13 @@ int precond_impl(aao_ctx* h, const double* r, const double* rscale, double* z, c
   return AAO_OK;
 }
 
-// Mixed 2D schedule with fused step pairs: k = 1 alone, then pairs (k, k+1)
-// while both are before the last step, at most one single step, then the
-// last step fused with the inverse transform.  Four field buffers rotate so
-// that a pair never writes a buffer it (or a neighbouring tile) reads.
+// Mixed 2D schedule with fused steps: k = 1 alone, then
+//  * warp strips (AAO_STEP_STREAM): S-step launches up to and including the last step, whose
+//    output x_p goes through a separate inverse transform (see the branch below);
+//  * TMA and tile kernels: four-step launches while all four come before the last step, pairs,
+//    at most one single step, then the last step fused with the inverse transform.
+// Four field buffers rotate so that a launch never writes a buffer it (or a neighbouring tile)
+// reads.
 int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) {
   const int p = h->p;
   cudaStream_t s = h->stream;
@@ -218,23 +221,52 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
   int cur = 0, prev = -1;  // prev = -1: x_{k-1} = x_1 = bhat/theta (not stored)
   int k = 2;
   const int kind = aao::effective_step_kernel(h);
-  if (kind == AAO_STEP_STREAM) {
-    // S steps per launch, warp strips streamed along y
-    const int S = h->scfg.S;
-    while (k + S - 1 <= p - 2) {
+  if (kind == AAO_STEP_STREAM && p - 2 >= 2) {
+    // Steps 2 .. p-1 by warp-strip launches (S steps each, streamed along y): one single step
+    // first when their count is odd, launches of the handle's S, one two-step launch for a
+    // remainder of two.  The final launch keeps x_p alone and the inverse transform reads it.
+    int R = p - 2;
+    if (R % 2 == 1) {
+      const int dst = 1;  // x_3 (x_2 is in field 0, x_1 = bhat/theta)
+      pi = prof_begin(h, AAO_PROF_STEP_SECOND, N * (3.0 * 4.0 * ell + 8.0));
+      AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 1, 1, false, cx, cy, cz, bhat, X[cur], X[dst], z, st[k],
+                                        ia, s));
+      prof_end(h, pi);
+      prev = cur;
+      cur = dst;
+      ++k;
+      --R;
+    }
+    while (R > 0) {
+      const bool four = h->scfg.S == 4 && R >= 4;
+      const aao::StreamConfig& c = (four || h->scfg.S == 2) ? h->scfg : h->tail;
+      const int S = c.S;
+      const bool fin = (R == S);
       int o[2], n = 0;
       for (int b = 0; b < 4 && n < 2; ++b)
         if (b != cur && b != prev) o[n++] = b;
       aao::FuseSteps fs;
       for (int q = 0; q < S; ++q) fs.s[q] = st[k + q];
-      pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * ((prev < 0 ? 4.0 : 5.0) * 4.0 * ell + 8.0));
-      AAO_CK(h, aao::launch_stream(h->g, h->ell, prev < 0 ? 1 : 2, h->scfg, cx, cy, bhat, X[cur],
-                                   prev < 0 ? nullptr : X[prev], X[o[0]], X[o[1]], fs, s));
+      const double sets = (prev < 0 ? 2.0 : 3.0) + (fin ? 1.0 : 2.0);
+      pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * (sets * 4.0 * ell + 8.0));
+      AAO_CK(h, aao::launch_stream(h->g, h->ell, prev < 0 ? 1 : 2, c, cx, cy, bhat, X[cur],
+                                   prev < 0 ? nullptr : X[prev], fin ? nullptr : X[o[0]], fin ? X[o[0]] : X[o[1]],
+                                   fs, s));
       prof_end(h, pi);
-      prev = o[0];
-      cur = o[1];
+      if (fin) {
+        cur = o[0];
+      } else {
+        prev = o[0];
+        cur = o[1];
+      }
       k += S;
+      R -= S;
     }
+    // z = Gamma^{-1} U x_p
+    pi = prof_begin(h, AAO_PROF_STEP_LAST, N * (4.0 * ell + 8.0 * ell));
+    AAO_CK(h, aao::launch_idft_planes(h->g, h->ell, X[cur], z, ia, s));
+    prof_end(h, pi);
+    return AAO_OK;
   }
   while (k + 3 <= p - 2 && kind != AAO_STEP_STREAM) {
     int o[2], n = 0;
@@ -919,6 +951,7 @@ int aao_create(aao_handle* out, int dim, const int64_t n[3], const double* kx, c
     // unless the tune cache holds an entry for this grid
     h->auto_kind = AAO_STEP_STREAM;
     h->scfg = aao::default_stream_config(h->g, ell);
+    h->tail = aao::default_tail_config(h->g, ell);
     aao::apply_tune_cache(h);
   }
   AAO_CK_CREATE(cudaMalloc(&h->V, sizeof(double) * h->L * (h->m + 1)));
@@ -1142,6 +1175,28 @@ int aao_set_stream_config(aao_handle h, int S, int H, int D, int NW) {
     return fail(h, AAO_EINVAL, "unsupported warp-strip configuration S=%d H=%d D=%d NW=%d", S, H, D, NW);
   h->scfg = c;
   reset_graphs(h);
+  return AAO_OK;
+}
+
+int aao_set_stream_tail(aao_handle h, int H, int D, int NW) {
+  if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
+  aao::StreamConfig c;
+  c.S = 2;
+  c.H = H;
+  c.D = D;
+  c.NW = NW;
+  if (!aao::stream_config_supported(c))
+    return fail(h, AAO_EINVAL, "unsupported two-step configuration H=%d D=%d NW=%d", H, D, NW);
+  h->tail = c;
+  reset_graphs(h);
+  return AAO_OK;
+}
+
+int aao_get_stream_tail(aao_handle h, int32_t out[3]) {
+  if (!h || !out) return fail(h, AAO_EINVAL, "NULL argument");
+  out[0] = h->tail.H;
+  out[1] = h->tail.D;
+  out[2] = h->tail.NW;
   return AAO_OK;
 }
 

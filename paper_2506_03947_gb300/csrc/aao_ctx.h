@@ -37,9 +37,11 @@ struct aao_ctx {
   bool tma = false;                                    // descriptors built: persistent four-step kernel usable
   int step_kernel = AAO_STEP_AUTO;                     // aao_set_step_kernel
   aao::StreamConfig scfg{};                            // warp-strip kernel configuration
+  aao::StreamConfig tail{};  // the two-step final launch of a sweep whose remaining step count is 2 mod 4
   int auto_kind = AAO_STEP_TMA;                        // the kernel AAO_STEP_AUTO selects
   bool owns_coeffs = true;                             // false for a view sharing another handle's operator
   aao_multi* multi = nullptr;                          // cached views of aao_solve_multi
+  bool multi_prof = false;  // aao_multi_profile_enable: event timing of the sweeps of aao_solve_multi
   bool tuned = false;                                  // kernel and configuration from the autotuner
   bool tma_used = false;                               // TMA kernel launched since the last fault check
   long long wait_limit = aao::kQuadTmaWaitCycles;      // bound of the TMA waits (aao_set_wait_limit)
@@ -109,8 +111,13 @@ int handle_ensure_stage(aao_ctx* h);
 inline int effective_step_kernel(const aao_ctx* h) {
   return h->step_kernel == AAO_STEP_AUTO ? h->auto_kind : h->step_kernel;
 }
-// Warp-strip configuration used without a cache entry (tune.cu).
+// Warp-strip configurations used without a cache entry (tune.cu): the fused sweep (S = 4) and
+// its two-step final launch (S = 2).
 StreamConfig default_stream_config(const GridDesc& g, int ell);
+StreamConfig default_tail_config(const GridDesc& g, int ell);
+// Configuration (S, D, NW) with the smallest segment height that puts all units of one launch
+// into `waves` rounds over the device's warps.
+StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW, int waves);
 // Apply the tune cache's entry for h, if a cache is configured and holds one (tune.cu).
 void apply_tune_cache(aao_ctx* h);
 // Release the views of aao_solve_multi (multi.cu).

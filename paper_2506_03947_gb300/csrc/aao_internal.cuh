@@ -147,6 +147,10 @@ bool stream_config_supported(const StreamConfig& c);
 cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConfig& c, const float* cx,
                           const float* cy, const float* bhat, const float* xk, const float* xkm1, float* outA,
                           float* outB, const FuseSteps& fs, cudaStream_t s);
+// z = Gamma^{-1} U x_p from the packed FP32 planes of x_p (2 cells per thread; N even, x 8-byte
+// and z 16-byte aligned).
+cudaError_t launch_idft_planes(const GridDesc& g, int ell, const float* x, double* z, const IdftArgs<float>& ia,
+                               cudaStream_t s);
 
 // Best-case P_alpha^{-1} for spatially constant diffusivities (dct.cu): spatial DCT-II of the
 // frequency planes, division by (phi - lambda_m), inverse DCT, inverse time DFT (Section 2.2).

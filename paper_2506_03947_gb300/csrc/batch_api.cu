@@ -48,10 +48,12 @@ struct aao_batch_ctx {
   aao::WorkList wunits{};
   aao::StreamQueue* queue = nullptr;
   std::vector<int> hact;  // host copy of the active flags
-  // event timing of the fused sweeps (aao_batch_profile_enable; graphs are not used meanwhile)
+  // event timing of the Chebyshev sweeps (aao_batch_profile_enable; graphs are not used
+  // meanwhile): each fused launch, or the middle single steps of each ell group, is one span
   bool prof = false;
   std::vector<cudaEvent_t> events;
   std::vector<double> pend_bytes;
+  std::vector<int> pend_launches;
   double prof_ms = 0.0, prof_bytes = 0.0;
   long long prof_launches = 0;
   std::vector<cudaGraphExec_t> graphs;
@@ -110,6 +112,37 @@ double fused_bytes(const aao_batch_ctx* B, int psrc) {
   return t;
 }
 
+// Algorithmic bytes of one single-step launch over the active members of the group with this
+// ell: x_k, x_{k-1} (psrc 2) and bhat read, x_{k+1} written, 4-byte values; the dim face arrays
+// once for the group when the members share them, else once per member.
+double single_bytes(const aao_batch_ctx* B, int ell, int psrc) {
+  double t = 0.0, faces = 0.0;
+  for (int i = 0; i < B->M; ++i)
+    if ((B->hact.empty() || B->hact[i]) && B->hI[i].ell == ell) {
+      const double n = (double)B->hI[i].g.N;
+      t += n * (psrc == 1 ? 3.0 : 4.0) * 4.0 * ell;
+      const double f = n * 4.0 * B->dim;
+      faces = B->shared.on ? f : faces + f;
+    }
+  return t + faces;
+}
+
+// Record the start of a profiled span of `launches` launches carrying `bytes`; returns its slot
+// (-1 if profiling is off, -2 on a CUDA error).
+int prof_begin(aao_batch_ctx* B, double bytes, int launches) {
+  if (!B->prof) return -1;
+  const int ev = (int)B->pend_bytes.size();
+  while ((int)B->events.size() < 2 * ev + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -2;
+    B->events.push_back(e);
+  }
+  if (cudaEventRecord(B->events[2 * ev], B->stream) != cudaSuccess) return -2;
+  B->pend_bytes.push_back(bytes);
+  B->pend_launches.push_back(launches);
+  return ev;
+}
+
 int batch_precond_stream(aao_batch_ctx* B, int j) {
   cudaStream_t s = B->stream;
   for (size_t g = 0; g < B->wdft.size(); ++g)
@@ -125,16 +158,8 @@ int batch_precond_stream(aao_batch_ctx* B, int j) {
     for (int f = 0; f < 4 && n < 2; ++f)
       if (f != cur && f != prev) o[n++] = f;
     const int psrc = prev < 0 ? 1 : 2;
-    const int ev = B->prof ? (int)B->pend_bytes.size() : -1;
-    if (ev >= 0) {
-      while ((int)B->events.size() < 2 * ev + 2) {
-        cudaEvent_t e;
-        AAO_BCK(B, cudaEventCreate(&e));
-        B->events.push_back(e);
-      }
-      AAO_BCK(B, cudaEventRecord(B->events[2 * ev], s));
-      B->pend_bytes.push_back(fused_bytes(B, psrc));
-    }
+    const int ev = prof_begin(B, B->prof ? fused_bytes(B, psrc) : 0.0, 1);
+    if (ev == -2) return bfail(B, AAO_ECUDA, "profiling events could not be created or recorded");
     AAO_BCK(B, aao::launch_batch_stream(B->dI, B->dact, B->wunits, B->scfg, k, psrc, cur, prev, o[0], o[1], B->queue,
                                         s));
     if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
@@ -156,10 +181,11 @@ void batch_prof_resolve(aao_batch_ctx* B) {
     if (cudaEventElapsedTime(&ms, B->events[2 * i], B->events[2 * i + 1]) == cudaSuccess) {
       B->prof_ms += ms;
       B->prof_bytes += B->pend_bytes[i];
-      B->prof_launches++;
+      B->prof_launches += B->pend_launches[i];
     }
   }
   B->pend_bytes.clear();
+  B->pend_launches.clear();
 }
 
 int batch_step_launches(aao_batch_ctx* B, int j) {
@@ -172,9 +198,21 @@ int batch_step_launches(aao_batch_ctx* B, int j) {
     for (size_t g = 0; g < B->wdft.size(); ++g)
       AAO_BCK(B, aao::batch_precond_head(B->dI, B->dact, B->wdft[g].first, B->dim, B->shared, B->wdft[g].second,
                                          B->wstep[g].second, B->p, j, s));
-    for (size_t g = 0; g < B->wstep.size(); ++g)
-      AAO_BCK(B, aao::batch_precond_tail(B->dI, B->dact, B->wstep[g].first, B->dim, B->shared, B->wstep[g].second,
-                                         B->p, j, 2, 0, -1, s));
+    for (size_t g = 0; g < B->wstep.size(); ++g) {
+      const int ell = B->wstep[g].first;
+      int cur = 0, prev = -1;
+      // profiled: the middle steps 2 .. p-2 of the group as one timed span (p-3 launches)
+      double bytes = 0.0;
+      if (B->prof)
+        for (int k = 2; k <= B->p - 2; ++k) bytes += single_bytes(B, ell, k == 2 ? 1 : 2);
+      const int ev = B->p > 3 ? prof_begin(B, bytes, B->p - 3) : -1;
+      if (ev == -2) return bfail(B, AAO_ECUDA, "profiling events could not be created or recorded");
+      AAO_BCK(B, aao::batch_steps_mid(B->dI, B->dact, ell, B->dim, B->shared, B->wstep[g].second, B->p, j, 2, &cur,
+                                      &prev, s));
+      if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
+      AAO_BCK(B, aao::batch_step_last(B->dI, B->dact, ell, B->dim, B->shared, B->wstep[g].second, B->p, j, cur, prev,
+                                      s));
+    }
   } else {
     for (size_t g = 0; g < B->wdft.size(); ++g)
       AAO_BCK(B, aao::batch_precond(B->dI, B->dact, B->wdft[g].first, B->wdft[g].second, B->wstep[g].second,
@@ -566,6 +604,7 @@ int aao_batch_profile_enable(aao_batch B, int on) {
   if (!B) return bfail(nullptr, AAO_EINVAL, "NULL batch");
   AAO_BCK(B, cudaStreamSynchronize(B->stream));
   B->pend_bytes.clear();
+  B->pend_launches.clear();
   B->prof_ms = B->prof_bytes = 0.0;
   B->prof_launches = 0;
   B->prof = on != 0;

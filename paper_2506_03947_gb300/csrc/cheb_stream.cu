@@ -209,8 +209,10 @@ struct StreamUnit {
       const int64_t o = offf + (int64_t)(y0 + oy) * a.g.n0;
       *reinterpret_cast<float2*>(a.outB + o) = last[0];
       *reinterpret_cast<float2*>(a.outB + o + a.g.N) = last[1];
-      *reinterpret_cast<float2*>(a.outA + o) = L[S - 1][RS][0];
-      *reinterpret_cast<float2*>(a.outA + o + a.g.N) = L[S - 1][RS][1];
+      if (a.outA) {  // null on the sweep's final launch, which keeps x_p alone
+        *reinterpret_cast<float2*>(a.outA + o) = L[S - 1][RS][0];
+        *reinterpret_cast<float2*>(a.outA + o + a.g.N) = L[S - 1][RS][1];
+      }
     }
   }
 
@@ -459,6 +461,73 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
   AAO_STREAM_CFG(2, 4, 16)
 #undef AAO_STREAM_CFG
   return cudaErrorInvalidValue;
+}
+
+// ---- inverse transform of x_p (the sweep's final output) -------------------------------------
+
+namespace {
+
+// z_t = gamma_t^{-1} sum_m (Re x_p(m) ci[t][m] - Im x_p(m) si[t][m]) (Eq. 5's Gamma^{-1} U) for
+// two consecutive cells per thread: the packed frequency planes of x_p in FP32 (plane 0 =
+// f_0, plane 1 = f_{ell/2}, planes 2m, 2m+1 = Re, Im f_m), z in FP64 (exact conversions of the
+// FP32 values, block-major like r).  Same summation order as the last-step kernel: f_0, then
+// f_{ell/2}, then m = 1 .. ell/2 - 1.
+template <int ELL>
+__global__ void __launch_bounds__(256, 4) k_idft_planes(int64_t N2, int64_t N, const float* __restrict__ x,
+                                                        double* __restrict__ z,
+                                                        const __grid_constant__ IdftArgs<float> ia) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N2) return;
+  const int64_t c = 2 * q;
+  // all ELL planes of the two cells first (ELL 8-byte loads in flight), then one time block at
+  // a time
+  float2 v[ELL];
+#pragma unroll
+  for (int pl = 0; pl < ELL; ++pl) v[pl] = __ldcs(reinterpret_cast<const float2*>(x + (int64_t)pl * N + c));
+#pragma unroll
+  for (int t = 0; t < ELL; ++t) {
+    float a0 = 0.f, a1 = 0.f;
+    const float c0 = ia.ci[t][0], c1 = ia.ci[t][ELL / 2];
+    a0 += v[0].x * c0, a1 += v[0].y * c0;
+    a0 += v[1].x * c1, a1 += v[1].y * c1;
+#pragma unroll
+    for (int m = 1; m < ELL / 2; ++m) {
+      const float cr = ia.ci[t][m], si = ia.si[t][m];
+      const float2 r = v[2 * m], im = v[2 * m + 1];
+      a0 += r.x * cr - im.x * si;
+      a1 += r.y * cr - im.y * si;
+    }
+    const float gmul = ia.igamma_T[t];
+    *reinterpret_cast<double2*>(z + (int64_t)t * N + c) = make_double2(f2d_exact(a0 * gmul), f2d_exact(a1 * gmul));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_idft_planes(const GridDesc& g, int ell, const float* x, double* z, const IdftArgs<float>& ia,
+                               cudaStream_t s) {
+  if (g.N % 2 != 0 || (reinterpret_cast<uintptr_t>(x) & 7) != 0 || (reinterpret_cast<uintptr_t>(z) & 15) != 0)
+    return cudaErrorInvalidValue;
+  const int64_t N2 = g.N / 2;
+  const unsigned nb = (unsigned)((N2 + 255) / 256);
+  switch (ell) {
+#define AAO_IDFT(L)                                                  \
+  case L:                                                            \
+    k_idft_planes<L><<<nb, 256, 0, s>>>(N2, g.N, x, z, ia);          \
+    break;
+    AAO_IDFT(4)
+    AAO_IDFT(6)
+    AAO_IDFT(8)
+    AAO_IDFT(10)
+    AAO_IDFT(12)
+    AAO_IDFT(14)
+    AAO_IDFT(16)
+#undef AAO_IDFT
+    default:
+      return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 

@@ -59,6 +59,7 @@ cudaError_t make_view(const aao_ctx* h, aao_ctx** out) {
   v->pairs = h->pairs;
   v->tma = false;
   v->scfg = h->scfg;
+  v->tail = h->tail;
   v->auto_kind = h->auto_kind;
   v->steps32 = h->steps32;
   v->steps64 = h->steps64;
@@ -142,6 +143,14 @@ int aao_solve_multi(aao_handle h, int nrhs, const double* const* b, double* cons
       aao::multi_destroy(m);
       return handle_fail(h, rc, "%s", msg.c_str());
     }
+    if (h->multi_prof) {
+      const int rp = aao_batch_profile_enable(m->batch, 1);
+      if (rp != AAO_OK) {
+        const std::string msg = aao_batch_last_error(m->batch);
+        aao::multi_destroy(m);
+        return handle_fail(h, rp, "%s", msg.c_str());
+      }
+    }
     h->multi = m;
   }
   const int rc = aao_batch_solve(m->batch, b, x, tol, max_outer);
@@ -154,6 +163,28 @@ int aao_multi_get_stats(aao_handle h, int i, aao_stats* s) {
   if (!h->multi || i < 0 || i >= h->multi->nrhs)
     return aao::handle_fail(h, AAO_EINVAL, "no multi-right-hand-side solve with right-hand side %d", i);
   return aao_batch_get_stats(h->multi->batch, i, s);
+}
+
+int aao_multi_profile_enable(aao_handle h, int on) {
+  if (!h) return aao::handle_fail(nullptr, AAO_EINVAL, "NULL handle");
+  h->multi_prof = on != 0;
+  if (!h->multi) return AAO_OK;
+  const int rc = aao_batch_profile_enable(h->multi->batch, on);
+  if (rc != AAO_OK) return aao::handle_fail(h, rc, "%s", aao_batch_last_error(h->multi->batch));
+  return AAO_OK;
+}
+
+int aao_multi_get_profile(aao_handle h, int64_t* launches, double* ms, double* bytes) {
+  if (!h) return aao::handle_fail(nullptr, AAO_EINVAL, "NULL handle");
+  if (!h->multi) {
+    if (launches) *launches = 0;
+    if (ms) *ms = 0.0;
+    if (bytes) *bytes = 0.0;
+    return AAO_OK;
+  }
+  const int rc = aao_batch_get_profile(h->multi->batch, launches, ms, bytes);
+  if (rc != AAO_OK) return aao::handle_fail(h, rc, "%s", aao_batch_last_error(h->multi->batch));
+  return AAO_OK;
 }
 
 }  // extern "C"

@@ -246,27 +246,36 @@ int round_h(int h, int S) {
 
 namespace aao {
 
-// The warp-strip configuration used without a cache entry: S = 4, D = 3, 8 warps per CTA and
-// the smallest segment height that puts all units of one launch into one round over the
-// device's warps (units = ell/2 passes x segments x strips of 56 interior columns).
-StreamConfig default_stream_config(const GridDesc& g, int ell) {
+// Configuration (S, D, NW) with the smallest segment height that puts all units of one launch
+// into `waves` rounds over the device's warps (units = ell/2 passes x segments x strips of
+// 64 - 2S interior columns), at most one segment per strip.
+StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW, int waves) {
   StreamConfig c;
-  c.S = 4;
-  c.D = 3;
-  c.NW = 8;
+  c.S = S;
+  c.D = D;
+  c.NW = NW;
   int dev = 0, nsm = 148;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
                                                 cudaSuccess) {
     cudaGetLastError();
     nsm = 148;
   }
-  const int nstrip = (g.n0 + 55) / 56;
+  const int iw = 64 - 2 * S;
+  const int nstrip = (g.n0 + iw - 1) / iw;
   const int per_seg = (ell / 2) * nstrip;
-  const int segs = std::max(1, nsm * c.NW / std::max(1, per_seg));
-  c.H = round_h((g.n1 + segs - 1) / segs, c.S);
-  if (c.H > round_h(g.n1, c.S)) c.H = round_h(g.n1, c.S);
+  const int segs = std::max(1, waves * nsm * NW / std::max(1, per_seg));
+  c.H = round_h((g.n1 + segs - 1) / segs, S);
+  if (c.H > round_h(g.n1, S)) c.H = round_h(g.n1, S);
   return c;
 }
+
+// The warp-strip configuration used without a cache entry: S = 4, D = 3, 8 warps per CTA, one
+// round of units.
+StreamConfig default_stream_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 4, 3, 8, 1); }
+
+// The two-step final launch: S = 2, D = 3, 16 warps per CTA (the two-step kernel stays within
+// 128 registers), one round of units.
+StreamConfig default_tail_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 2, 3, 16, 1); }
 
 // Apply the cache entry for this handle, if a cache is configured and holds one.
 void apply_tune_cache(aao_ctx* h) {
@@ -390,36 +399,76 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
   }
 
   const int saved_kind = h->step_kernel, saved_auto = h->auto_kind;
-  const aao::StreamConfig saved_cfg = h->scfg;
+  const aao::StreamConfig saved_cfg = h->scfg, saved_tail = h->tail;
   const bool saved_prof = h->prof;
   h->prof = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  int best_i = -1;
-  for (size_t i = 0; i < cand.size() && e == cudaSuccess && rc == AAO_OK; ++i) {
-    aao_tune_entry& c = cand[i];
-    h->step_kernel = c.kind;
-    if (c.kind == AAO_STEP_STREAM) {
-      h->scfg.S = c.S;
-      h->scfg.H = c.H;
-      h->scfg.D = c.D;
-      h->scfg.NW = c.NW;
+  // time candidates [i0, cand.size()): whole applies with the candidate set on the handle
+  // (a sweep candidate, or with tail = 1 a two-step final launch under the best sweep)
+  auto run = [&](size_t i0, int& best_i) {
+    for (size_t i = i0; i < cand.size() && e == cudaSuccess && rc == AAO_OK; ++i) {
+      aao_tune_entry& c = cand[i];
+      aao::StreamConfig& dst = c.tail ? h->tail : h->scfg;
+      if (!c.tail) h->step_kernel = c.kind;
+      if (c.kind == AAO_STEP_STREAM) {
+        dst.S = c.S;
+        dst.H = c.H;
+        dst.D = c.D;
+        dst.NW = c.NW;
+      }
+      rc = aao::handle_precond(h, h->stage_a, nullptr, h->stage_b);  // warm-up
+      for (int r = 0; r < reps && rc == AAO_OK; ++r) {
+        if (r == 0 && (e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+        rc = aao::handle_precond(h, h->stage_a, nullptr, h->stage_b);
+      }
+      if (rc == AAO_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (rc == AAO_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (rc == AAO_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == AAO_OK) rc = aao::handle_check_tma(h);
+      if (rc == AAO_OK && e == cudaSuccess) {
+        c.us_per_apply = 1e3 * ms / reps;
+        if (best_i < 0 || c.us_per_apply < cand[best_i].us_per_apply) best_i = (int)i;
+      }
     }
-    rc = aao::handle_precond(h, h->stage_a, nullptr, h->stage_b);  // warm-up
-    for (int r = 0; r < reps && rc == AAO_OK; ++r) {
-      if (r == 0 && (e = cudaEventRecord(e0, s)) != cudaSuccess) break;
-      rc = aao::handle_precond(h, h->stage_a, nullptr, h->stage_b);
-    }
-    if (rc == AAO_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (rc == AAO_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.0f;
-    if (rc == AAO_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (rc == AAO_OK) rc = aao::handle_check_tma(h);
-    if (rc == AAO_OK && e == cudaSuccess) {
-      c.us_per_apply = 1e3 * ms / reps;
-      if (best_i < 0 || c.us_per_apply < cand[best_i].us_per_apply) best_i = (int)i;
-    }
+  };
+  int best_i = -1, tail_i = -1;
+  run(0, best_i);
+  // the two-step final launch, when the best sweep has S = 4 and the remaining step count
+  // (after at most one single step) is 2 mod 4: NW in {8, 12, 16}, D in {3, 4}, one to three
+  // rounds of units
+  int R = h->p - 2;
+  if (R % 2) --R;
+  if (rc == AAO_OK && e == cudaSuccess && best_i >= 0 && cand[best_i].kind == AAO_STEP_STREAM &&
+      cand[best_i].S == 4 && R >= 2 && R % 4 == 2) {
+    const aao_tune_entry b = cand[best_i];
+    h->step_kernel = AAO_STEP_STREAM;
+    h->scfg.S = b.S;
+    h->scfg.H = b.H;
+    h->scfg.D = b.D;
+    h->scfg.NW = b.NW;
+    const size_t i0 = cand.size();
+    for (int NW : {8, 12, 16})
+      for (int D : {3, 4})
+        for (int w = 1; w <= 3; ++w) {
+          const aao::StreamConfig c = aao::wave_stream_config(h->g, h->ell, 2, D, NW, w);
+          bool dup = false;
+          for (size_t i = i0; i < cand.size(); ++i)
+            dup = dup || (cand[i].H == c.H && cand[i].D == D && cand[i].NW == NW);
+          if (dup || !aao::stream_config_supported(c)) continue;
+          aao_tune_entry t{};
+          t.kind = AAO_STEP_STREAM;
+          t.S = 2;
+          t.H = c.H;
+          t.D = D;
+          t.NW = NW;
+          t.tail = 1;
+          t.us_per_apply = -1.0;
+          cand.push_back(t);
+        }
+    run(i0, tail_i);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -427,11 +476,12 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
   h->step_kernel = saved_kind;
   h->auto_kind = saved_auto;
   h->scfg = saved_cfg;
+  h->tail = saved_tail;
   aao::handle_reset_graphs(h);
   if (rc) return rc;
   if (e != cudaSuccess) return handle_fail(h, AAO_ECUDA, "tuning: %s", cudaGetErrorString(e));
   if (best_i < 0) return handle_fail(h, AAO_ECUDA, "tuning: no candidate ran");
-  // the fastest candidate becomes the handle's default kernel
+  // the fastest candidate becomes the handle's default kernel, the fastest tail its final launch
   const aao_tune_entry& b = cand[best_i];
   h->step_kernel = AAO_STEP_AUTO;
   h->auto_kind = b.kind;
@@ -440,6 +490,13 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
     h->scfg.H = b.H;
     h->scfg.D = b.D;
     h->scfg.NW = b.NW;
+  }
+  if (tail_i >= 0) {
+    const aao_tune_entry& t = cand[tail_i];
+    h->tail.S = 2;
+    h->tail.H = t.H;
+    h->tail.D = t.D;
+    h->tail.NW = t.NW;
   }
   h->tuned = true;
   if (best) *best = b;

@@ -27,27 +27,42 @@ def _apply(s, r):
 def test_every_candidate_matches_the_oracle():
     binding = ensure_lib()
     P = inputs.make_problem("t", 2, (248, 180), 10, 1e-2, 1, 0.5, (16.0, 16.0), 61, 62)
-    p = 14
+    p = 16                                # steps 2 .. 15: three four-step launches and a two-step one
     A, mu_max = oracle_ops(P)
     r = np.random.default_rng(21).standard_normal((P.ell, P.N))
     ref = precond.pnc_apply(A, r, P.alpha, 1.0, mu_max, p)
     s = make_solver(P, 1, p)
     best, cands = s.autotune(2)
-    assert len(cands) >= 10 and all(c["us_per_apply"] > 0 for c in cands)
-    assert best["us_per_apply"] == min(c["us_per_apply"] for c in cands)
+    sweeps = [c for c in cands if not c["tail"]]
+    tails = [c for c in cands if c["tail"]]
+    assert len(sweeps) >= 10 and all(c["us_per_apply"] > 0 for c in cands)
+    assert best["us_per_apply"] == min(c["us_per_apply"] for c in sweeps)
     assert s.tuning()["tuned"] and s.tuning()["kernel"] == best["kernel"]
+    if best["kernel"] == "stream" and best["S"] == 4:
+        # the two-step final launch was tuned under the winner; the fastest is the handle's tail
+        assert len(tails) >= 6 and all(c["S"] == 2 for c in tails)
+        bt = min(tails, key=lambda c: c["us_per_apply"])
+        assert s.stream_tail() == {"S": 2, "H": bt["H"], "D": bt["D"], "NW": bt["NW"]}
     tol = precond_tol(1, p)
     kinds = {"tile": binding.AAO_STEP_TILE, "tma": binding.AAO_STEP_TMA, "stream": binding.AAO_STEP_STREAM}
     worst = 0.0
-    for c in cands:
+    for c in sweeps:
         s.set_step_kernel(kinds[c["kernel"]])
         if c["kernel"] == "stream":
             s.set_stream_config(c["S"], c["H"], c["D"], c["NW"])
         err = precond_err(_apply(s, r), ref, P.ell, P.alpha)
         worst = max(worst, err)
         assert err <= tol, (c, err, tol)
-    log_record({"test": "autotune_candidates", "n": len(cands), "worst_err": worst, "tol": tol,
-                "ratio": worst / tol, "best": best})
+    if tails:
+        s.set_step_kernel(binding.AAO_STEP_STREAM)
+        s.set_stream_config(best["S"], best["H"], best["D"], best["NW"])
+        for c in tails:
+            s.set_stream_tail(c["H"], c["D"], c["NW"])
+            err = precond_err(_apply(s, r), ref, P.ell, P.alpha)
+            worst = max(worst, err)
+            assert err <= tol, (c, err, tol)
+    log_record({"test": "autotune_candidates", "n": len(cands), "tails": len(tails), "worst_err": worst,
+                "tol": tol, "ratio": worst / tol, "best": best})
     # the tuned default (AAO_STEP_AUTO) is the winner
     s.set_step_kernel(binding.AAO_STEP_AUTO)
     assert s.step_kernel() == kinds[best["kernel"]]

@@ -76,3 +76,35 @@ def test_multi_rhs_argument_checks():
         s.multi_stats(0)                                   # no multi solve yet
     s.solve_multi(bs, xs, 1e-8, 50)
     assert s.multi_stats(1)["converged"]
+
+
+def test_multi_rhs_profile_counts_middle_steps():
+    """Event timing of the middle Chebyshev steps (k = 2 .. p-2, one span of p - 3 launches per
+    Arnoldi step); the profiled solve runs without graphs and gives the same bits."""
+    torch = torch_cuda()
+    P = inputs.make_problem("m3p", 3, (40, 32, 24), 10, 1e-2, 7, 0.7, (8.0, 8.0, 4.0), 91, [92, 93, 94])
+    p = 7
+    s = make_solver(P, 1, p, restart=48)
+    nr = P.b.shape[0]
+    bs = [to_dev(P.b[i]) for i in range(nr)]
+    assert s.multi_profile() == {"launches": 0, "ms": 0.0, "bytes": 0.0}
+    xs = [torch.zeros_like(b) for b in bs]
+    s.solve_multi(bs, xs, 1e-8, 200)
+    s.multi_profile_enable(True)
+    xp = [torch.zeros_like(b) for b in bs]
+    s.solve_multi(bs, xp, 1e-8, 200)
+    prof = s.multi_profile()
+    s.multi_profile_enable(False)
+    its = [s.multi_stats(i)["outer_its"] for i in range(nr)]
+    for a, b in zip(xs, xp):
+        assert torch.equal(a, b)
+    spans, rem = divmod(prof["launches"], p - 3)
+    assert rem == 0 and max(its) <= spans <= sum(its)
+    N, ell = P.N, P.ell
+    one = sum((3.0 if k == 2 else 4.0) * 4.0 * ell * N + 12.0 * N for k in range(2, p - 1))
+    full = sum((3.0 if k == 2 else 4.0) * 4.0 * ell * N * nr + 12.0 * N for k in range(2, p - 1))
+    assert spans * one <= prof["bytes"] <= spans * full + 1.0
+    assert prof["ms"] > 0.0
+    log_record({"test": "multi_rhs_profile", "spans": spans, "its": its, "ms": prof["ms"],
+                "gbs": prof["bytes"] / (prof["ms"] * 1e-3) / 1e9})
+    s.close()
