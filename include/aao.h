@@ -105,10 +105,12 @@ typedef struct {
 
 /* Kernel classes timed by the built-in profiler (aao_profile_*). */
 #define AAO_PROF_DFT 0        /* forward transform (Eq. 5's U* Gamma)                      */
-#define AAO_PROF_STEP_FIRST 1 /* Chebyshev step k = 1 (x_1 = bhat/theta)                   */
+#define AAO_PROF_STEP_FIRST 1 /* Chebyshev step k = 1 (x_1 = bhat/theta); on the 2D mixed
+                                 path one launch with the forward transform               */
 #define AAO_PROF_STEP_SECOND 2 /* Chebyshev step k = 2                                     */
 #define AAO_PROF_STEP_MID 3   /* Chebyshev steps 3 <= k <= p-2 (the fused sweep)           */
-#define AAO_PROF_STEP_LAST 4  /* last Chebyshev step fused with the inverse transform      */
+#define AAO_PROF_STEP_LAST 4  /* last Chebyshev step fused with the inverse transform
+                                 (after a warp-strip sweep: the inverse transform of x_p)  */
 #define AAO_PROF_MATVEC 5     /* script-A matvec and explicit residual                      */
 #define AAO_PROF_ORTH 6       /* Gram-Schmidt multi-dots, updates and their reductions     */
 #define AAO_PROF_STEP_PAIR 7  /* two fused Chebyshev steps (2D mixed path)                 */

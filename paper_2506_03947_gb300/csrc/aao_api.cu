@@ -192,7 +192,7 @@ int precond_impl(aao_ctx* h, const double* r, const double* rscale, double* z, c
   return AAO_OK;
 }
 
-// Mixed 2D schedule with fused steps: k = 1 alone, then
+// Mixed 2D schedule with fused steps: the transform and k = 1 in one launch, then
 //  * warp strips (AAO_STEP_STREAM): S-step launches up to and including the last step, whose
 //    output x_p goes through a separate inverse transform (see the branch below);
 //  * TMA and tile kernels: four-step launches while all four come before the last step, pairs,
@@ -208,16 +208,21 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
   float* X[4] = {(float*)h->xa, (float*)h->xb, (float*)h->xc, (float*)h->xd};
   const float *cx = h->cx32, *cy = h->cy32, *cz = h->cz32;
   const double N = (double)h->N, ell = (double)h->ell;
-  int pi = prof_begin(h, AAO_PROF_DFT, N * (8.0 * ell + 4.0 * ell));
-  AAO_CK(h, aao::launch_dft<float>(h->g, h->dim, h->ell, r, rscale, bhat, h->dft32, s));
+  int pi = -1;
+  if (p == 2) {
+    pi = prof_begin(h, AAO_PROF_DFT, N * (8.0 * ell + 4.0 * ell));
+    AAO_CK(h, aao::launch_dft<float>(h->g, h->dim, h->ell, r, rscale, bhat, h->dft32, s));
+    prof_end(h, pi);
+    pi = prof_begin(h, AAO_PROF_STEP_LAST, N * (4.0 * ell + 8.0 + 8.0 * ell));
+    AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 0, 0, true, cx, cy, cz, bhat, nullptr, X[0], z, st[1], ia,
+                                      s));
+    prof_end(h, pi);
+    return AAO_OK;
+  }
+  // the transform and step 1 in one launch: r read, bhat and x_2 (field 0) written
+  pi = prof_begin(h, AAO_PROF_STEP_FIRST, N * (16.0 * ell + 8.0));
+  AAO_CK(h, aao::launch_dft_first(h->g, h->ell, r, rscale, bhat, X[0], cx, cy, h->dft32, st[1], s));
   prof_end(h, pi);
-  const bool last1 = (p == 2);
-  pi = prof_begin(h, last1 ? AAO_PROF_STEP_LAST : AAO_PROF_STEP_FIRST,
-                  N * (last1 ? (4.0 * ell + 8.0 + 8.0 * ell) : (8.0 * ell + 8.0)));
-  AAO_CK(h, aao::launch_step<float>(h->g, h->dim, h->ell, 0, 0, last1, cx, cy, cz, bhat, nullptr, X[0], z, st[1], ia,
-                                    s));
-  prof_end(h, pi);
-  if (last1) return AAO_OK;
   int cur = 0, prev = -1;  // prev = -1: x_{k-1} = x_1 = bhat/theta (not stored)
   int k = 2;
   const int kind = aao::effective_step_kernel(h);

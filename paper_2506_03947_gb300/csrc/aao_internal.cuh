@@ -147,6 +147,11 @@ bool stream_config_supported(const StreamConfig& c);
 cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConfig& c, const float* cx,
                           const float* cy, const float* bhat, const float* xk, const float* xkm1, float* outA,
                           float* outB, const FuseSteps& fs, cudaStream_t s);
+// Transform and Chebyshev step k = 1 in one launch (2D, n0 % 4 == 0, FP32): writes bhat and
+// x_2 (16-byte aligned bhat, x2, cx, cy).
+cudaError_t launch_dft_first(const GridDesc& g, int ell, const double* r, const double* rscale, float* bhat,
+                             float* x2, const float* cx, const float* cy, const DftArgs<float>& da,
+                             const StepArgs<float>& sa, cudaStream_t s);
 // z = Gamma^{-1} U x_p from the packed FP32 planes of x_p (2 cells per thread; N even, x 8-byte
 // and z 16-byte aligned).
 cudaError_t launch_idft_planes(const GridDesc& g, int ell, const float* x, double* z, const IdftArgs<float>& ia,

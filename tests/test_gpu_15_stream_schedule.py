@@ -1,11 +1,12 @@
 """Schedule of the warp-strip sweep: every p, the two-step final launch, the inverse transform.
 
-With the warp-strip kernel, steps 2 .. p-1 of Eq. 7 run as launches of S steps (step 2 alone
-first when their count is odd, one two-step launch for a remainder of two); the final launch
-writes x_p alone and a separate kernel applies Eq. 5's inverse transform and Gamma^{-1}.  Each
-apply is compared with the oracle's P_NC^{-1} and with the persistent TMA kernel (whose last
-step is fused with the inverse transform), for every residue of p - 2 modulo 4, with the launch
-count of the schedule checked, and for several two-step configurations.
+The α-scaling, the forward transform and step 1 run as one launch (the transform of a one-cell
+ring recomputed per block).  With the warp-strip kernel, steps 2 .. p-1 of Eq. 7 run as launches
+of S steps (step 2 alone first when their count is odd, one two-step launch for a remainder of
+two); the final launch writes x_p alone and a separate kernel applies Eq. 5's inverse transform
+and Gamma^{-1}.  Each apply is compared with the oracle's P_NC^{-1} and with the persistent TMA
+kernel (whose last step is fused with the inverse transform), for every residue of p - 2 modulo
+4, with the launch count of the schedule checked, and for several two-step configurations.
 """
 import numpy as np
 import pytest
@@ -35,14 +36,15 @@ def _apply_counted(s, r):
 
 
 def _expected_launches(p, S):
-    """dft, step 1, [step 2 alone], the S-step launches, [the two-step launch], the inverse transform."""
+    """The transform with step 1 (one launch), [step 2 alone], the S-step launches, [the two-step
+    launch], the inverse transform."""
     R = p - 2
     if R < 2:
         return None
     single = R % 2
     R -= single
     n = R // S if S == 2 else R // 4 + (1 if R % 4 == 2 else 0)
-    return 2 + single + n + 1
+    return 1 + single + n + 1
 
 
 @pytest.mark.parametrize("p", [3, 4, 5, 6, 7, 8, 9, 12, 13, 40])
