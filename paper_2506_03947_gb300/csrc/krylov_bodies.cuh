@@ -277,22 +277,41 @@ __device__ __forceinline__ void mgs_step_body(int blk, int nblk, const double* _
     const uint64_t keep = l2_policy_keep(), stream = l2_policy_stream();
     const int64_t L2 = L / 2;
     double a0 = 0.0, a1 = 0.0;
-    for (int64_t e2 = tid; e2 < L2; e2 += nthr) {
-      double2 v = ld2_pol(w + 2 * e2, keep);
+    // software-pipelined: the loads of the thread's next element pair are issued before the
+    // FP64 arithmetic of the current one (the cache-hinted accesses keep their program order),
+    // so each warp has a pair's loads in flight while its FMAs wait for the FP64 pipe
+    const double2 z2 = make_double2(0.0, 0.0);
+    double2 v = z2, a = z2, b = z2;
+    int64_t e2 = tid;
+    if (e2 < L2) {
+      v = ld2_pol(w + 2 * e2, keep);
+      if (UPD) a = ld2_ro_pol(Vp + 2 * e2, stream);
+      if (DOT) b = ld2_ro_pol(Vn + 2 * e2, stream);
+    }
+    while (e2 < L2) {
+      const int64_t f2 = e2 + nthr;
+      double2 vn = z2, an = z2, bn = z2;
+      if (f2 < L2) {
+        vn = ld2_pol(w + 2 * f2, keep);
+        if (UPD) an = ld2_ro_pol(Vp + 2 * f2, stream);
+        if (DOT) bn = ld2_ro_pol(Vn + 2 * f2, stream);
+      }
       if (UPD) {
-        const double2 a = ld2_ro_pol(Vp + 2 * e2, stream);
         v.x = fma(-coef, a.x, v.x);
         v.y = fma(-coef, a.y, v.y);
         st2_pol(w + 2 * e2, v, keep);
       }
       if (DOT) {
-        const double2 b = ld2_ro_pol(Vn + 2 * e2, stream);
         a0 = fma(b.x, v.x, a0);
         a1 = fma(b.y, v.y, a1);
       } else {
         a0 = fma(v.x, v.x, a0);
         a1 = fma(v.y, v.y, a1);
       }
+      v = vn;
+      a = an;
+      b = bn;
+      e2 = f2;
     }
     acc = a0 + a1;
   } else {
