@@ -15,19 +15,20 @@ real arithmetic with a fixed number K of Krylov iterations each:
 The paper applies the SPD blocks approximately with one V-cycle of an algebraic multigrid
 (HSL_MI20).  This library uses its own multigrid for the same operators, defined here and run
 identically on the GPU:
-  * levels: pairwise aggregation of the structured grid (2 x 2 cells, ceil(n/2) per axis), the
-    coarse operator being the Galerkin product R B P with piecewise-constant P and R = P^T.
-    For B = (1 + c) I + K this keeps the form B_H = (1 + c) W_H + K_H: W_H sums the cells of an
-    aggregate and each coarse face sums the fine face diffusivities crossing it;
+  * levels: pairwise aggregation of the structured grid (2 x 2 cells in 2D, 2 x 2 x 2 in 3D,
+    ceil(n/2) per axis), the coarse operator being the Galerkin product R B P with
+    piecewise-constant P and R = P^T.  For B = (1 + c) I + K this keeps the form
+    B_H = (1 + c) W_H + K_H: W_H sums the cells of an aggregate and each coarse face sums the fine
+    face diffusivities crossing it;
   * smoother: weighted Jacobi, omega = 2/3, NU sweeps before and after the coarse correction
     (a symmetric V-cycle, so it is an SPD preconditioner for CG and MINRES);
-  * coarsest level (both sides <= 4 cells): NU_COARSE Jacobi sweeps from zero.
-Grids are 1D or 2D (n2 = 1).
+  * coarsest level (every side <= 4 cells): NU_COARSE Jacobi sweeps from zero.
+Grids are 1D, 2D (fields of shape (n1, n0)) or 3D (fields of shape (n2, n1, n0)).
 """
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -42,57 +43,92 @@ COARSEST = 4
 
 @dataclass
 class Level:
-    w: np.ndarray    # (n1, n0) cell weights (1 on the finest level)
-    kx: np.ndarray   # (n1, n0 - 1) face diffusivities along x
-    ky: np.ndarray   # (n1 - 1, n0) face diffusivities along y
+    w: np.ndarray    # cell weights, the level's field shape (1 on the finest level)
+    kx: np.ndarray   # face diffusivities along x (last axis): one fewer entry along it
+    ky: np.ndarray   # along y (second-last axis)
+    kz: Optional[np.ndarray] = None   # along z (first axis of a 3D field), None in 1D/2D
 
 
-def hierarchy(kx: np.ndarray, ky: np.ndarray, shape) -> List[Level]:
-    """Aggregation levels for a 1D/2D grid; kx, ky in the (n2, n1, n0-1) / (n2, n1-1, n0) layout."""
+def _faces(L: Level):
+    """(axis, face array) pairs of a level; x is the last axis."""
+    nd = L.w.ndim
+    out = [(nd - 1, L.kx), (nd - 2, L.ky)]
+    if L.kz is not None:
+        out.append((0, L.kz))
+    return out
+
+
+def _agg_index(shape):
+    """Aggregate index of every cell of a field of this shape (2 per axis)."""
+    return tuple(ix // 2 for ix in np.indices(shape))
+
+
+def _coarse_faces(k: np.ndarray, axis: int, cshape) -> np.ndarray:
+    """Coarse faces along `axis`: the fine faces between cells 2I+1 and 2I+2 along the axis
+    cross from aggregate I to I+1; summed over the aggregate's cells along the other axes."""
+    cn = cshape[axis]
+    shp = list(cshape)
+    shp[axis] = max(cn - 1, 0)
+    kc = np.zeros(shp)
+    if cn > 1:
+        sel = np.take(k, np.arange(1, 2 * cn - 2, 2), axis=axis)
+        idx = list(np.indices(sel.shape))
+        for a in range(sel.ndim):
+            if a != axis:
+                idx[a] = idx[a] // 2
+        np.add.at(kc, tuple(idx), sel)
+    return kc
+
+
+def hierarchy(kx: np.ndarray, ky: np.ndarray, shape, kz: Optional[np.ndarray] = None) -> List[Level]:
+    """Aggregation levels; kx, ky, kz in the (n2, n1, n0-1) / (n2, n1-1, n0) / (n2-1, n1, n0)
+    layout.  1D/2D grids (n2 = 1) give fields of shape (n1, n0), 3D grids (n2, n1, n0)."""
     n2, n1, n0 = shape
-    if n2 != 1:
-        raise ValueError("P_SP's multigrid is defined for 1D and 2D grids")
-    lv = [Level(np.ones((n1, n0)), kx[0].astype(float).copy(), ky[0].astype(float).copy())]
-    while lv[-1].w.shape[0] > COARSEST or lv[-1].w.shape[1] > COARSEST:
+    if n2 == 1:
+        lv = [Level(np.ones((n1, n0)), kx[0].astype(float).copy(), ky[0].astype(float).copy())]
+    else:
+        if kz is None:
+            raise ValueError("a 3D grid needs its z faces")
+        lv = [Level(np.ones((n2, n1, n0)), kx.astype(float).copy(), ky.astype(float).copy(),
+                    kz.astype(float).copy())]
+    while max(lv[-1].w.shape) > COARSEST:
         f = lv[-1]
-        m1, m0 = f.w.shape
-        c1, c0 = (m1 + 1) // 2, (m0 + 1) // 2
-        jj, ii = np.meshgrid(np.arange(m1), np.arange(m0), indexing="ij")
-        w = np.zeros((c1, c0))
-        np.add.at(w, (jj // 2, ii // 2), f.w)                       # cells of each aggregate
-        kxc = np.zeros((c1, max(c0 - 1, 0)))
-        if c0 > 1:
-            # fine faces between columns 2ic+1 and 2ic+2 cross from aggregate ic to ic+1
-            np.add.at(kxc, (np.arange(m1)[:, None] // 2, np.arange(c0 - 1)[None, :]), f.kx[:, 1:2 * c0 - 2:2])
-        kyc = np.zeros((max(c1 - 1, 0), c0))
-        if c1 > 1:
-            np.add.at(kyc, (np.arange(c1 - 1)[:, None], np.arange(m0)[None, :] // 2), f.ky[1:2 * c1 - 2:2, :])
-        lv.append(Level(w, kxc, kyc))
+        cshape = tuple((m + 1) // 2 for m in f.w.shape)
+        w = np.zeros(cshape)
+        np.add.at(w, _agg_index(f.w.shape), f.w)                      # cells of each aggregate
+        fc = {a: _coarse_faces(k, a, cshape) for a, k in _faces(f)}
+        nd = len(cshape)
+        lv.append(Level(w, fc[nd - 1], fc[nd - 2], fc.get(0) if f.kz is not None else None))
     return lv
 
 
 def level_apply(L: Level, c: float, x: np.ndarray) -> np.ndarray:
-    """B x = (1 + c) W x + K x on one level (x of shape (n1, n0))."""
+    """B x = (1 + c) W x + K x on one level (x of the level's field shape)."""
     y = (1.0 + c) * L.w * x
-    if L.kx.size:
-        f = L.kx * (x[:, 1:] - x[:, :-1])
-        y[:, :-1] -= f
-        y[:, 1:] += f
-    if L.ky.size:
-        f = L.ky * (x[1:, :] - x[:-1, :])
-        y[:-1, :] -= f
-        y[1:, :] += f
+    for a, k in _faces(L):
+        if k.size:
+            n = x.shape[a]
+            f = k * (np.take(x, np.arange(1, n), axis=a) - np.take(x, np.arange(0, n - 1), axis=a))
+            lo = [slice(None)] * x.ndim
+            hi = [slice(None)] * x.ndim
+            lo[a] = slice(0, n - 1)
+            hi[a] = slice(1, n)
+            y[tuple(lo)] -= f
+            y[tuple(hi)] += f
     return y
 
 
 def level_diag(L: Level, c: float) -> np.ndarray:
     d = (1.0 + c) * L.w.copy()
-    if L.kx.size:
-        d[:, :-1] += L.kx
-        d[:, 1:] += L.kx
-    if L.ky.size:
-        d[:-1, :] += L.ky
-        d[1:, :] += L.ky
+    for a, k in _faces(L):
+        if k.size:
+            n = d.shape[a]
+            lo = [slice(None)] * d.ndim
+            hi = [slice(None)] * d.ndim
+            lo[a] = slice(0, n - 1)
+            hi[a] = slice(1, n)
+            d[tuple(lo)] += k
+            d[tuple(hi)] += k
     return d
 
 
@@ -104,16 +140,15 @@ def jacobi(L: Level, c: float, b: np.ndarray, x: np.ndarray, sweeps: int) -> np.
 
 
 def restrict(b: np.ndarray, coarse_shape) -> np.ndarray:
-    """Sum of b over each 2 x 2 aggregate (R = P^T)."""
+    """Sum of b over each aggregate (R = P^T)."""
     r = np.zeros(coarse_shape)
-    m1, m0 = b.shape
-    np.add.at(r, (np.arange(m1)[:, None] // 2, np.arange(m0)[None, :] // 2), b)
+    np.add.at(r, _agg_index(b.shape), b)
     return r
 
 
 def prolong(xc: np.ndarray, fine_shape) -> np.ndarray:
-    m1, m0 = fine_shape
-    return xc[np.arange(m1)[:, None] // 2, np.arange(m0)[None, :] // 2]
+    """Every fine cell takes its aggregate's value (piecewise-constant P)."""
+    return xc[_agg_index(fine_shape)]
 
 
 def vcycle(levels: List[Level], c: float, b: np.ndarray, q: int = 0) -> np.ndarray:
@@ -210,7 +245,7 @@ def minres(levels: List[Level], lam: complex, fu: np.ndarray, fv: np.ndarray, it
 
 
 def shifted_solve(levels: List[Level], lam: complex, b: np.ndarray, iters: int, real: bool) -> np.ndarray:
-    """Approximate (A - lam I)^{-1} b for one frequency (b complex of shape (n1, n0));
+    """Approximate (A - lam I)^{-1} b for one frequency (b complex of the field shape);
     real: the shift is real (frequencies 0 and ell/2), solved by CG."""
     if real:
         xr = pcg(levels, -lam.real, b.real.copy(), iters)
@@ -224,16 +259,16 @@ def shifted_solve(levels: List[Level], lam: complex, b: np.ndarray, iters: int, 
     return np.conj(x) if conj else x
 
 
-def psp_apply(kx, ky, shape, r: np.ndarray, alpha: float, iters: int) -> np.ndarray:
+def psp_apply(kx, ky, shape, r: np.ndarray, alpha: float, iters: int, kz=None) -> np.ndarray:
     """z = P_SP^{-1} r: Eq. 5 with every shifted solve replaced by iters Krylov steps (Section 4)."""
     ell = r.shape[0]
-    levels = hierarchy(kx, ky, shape)
-    n2, n1, n0 = shape
+    levels = hierarchy(kx, ky, shape, kz)
+    fshape = levels[0].w.shape
     lam = scaled_roots(ell, alpha)
     v = forward_transform(r, alpha)
     y = np.zeros_like(v)
     for j in range(ell):
         real = (j == 0) or (2 * j == ell)
         lj = complex(lam[j].real, 0.0) if real else complex(lam[j])
-        y[j] = shifted_solve(levels, lj, v[j].reshape(n1, n0), iters, real).reshape(-1)
+        y[j] = shifted_solve(levels, lj, v[j].reshape(fshape), iters, real).reshape(-1)
     return inverse_transform(y, alpha)

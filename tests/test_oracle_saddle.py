@@ -128,3 +128,94 @@ def test_psp_tends_to_exact_palpha():
     errs = [np.abs(sd.psp_apply(P.kx, P.ky, P.shape, r, P.alpha, k) - ze).max() / np.abs(ze).max()
             for k in (10, 20, 50)]
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9
+
+
+# ---- 3D grids: 2 x 2 x 2 aggregates -------------------------------------------------------
+
+def _problem3(n, seed=13):
+    return inputs.make_problem("s3", 3, n, 6, 1e-2, 1, 0.5, (3.0, 3.0, 2.0), seed, seed + 1)
+
+
+def test_3d_finest_level_is_the_operator():
+    # level 0 with c = 0 is A = I + K of the finite-volume operator module (Eq. 1's A)
+    P = _problem3((7, 5, 4))
+    lv = sd.hierarchy(P.kx, P.ky, P.shape, P.kz)
+    A = op.fv_dense(P.kx, P.ky, P.kz, P.shape)
+    x = np.random.default_rng(3).standard_normal(P.N)
+    y = sd.level_apply(lv[0], 0.0, x.reshape(P.shape)).ravel()
+    assert np.abs(y - A @ x).max() < 1e-12 * np.abs(A @ x).max()
+    assert [L.w.shape for L in lv] == [(4, 5, 7), (2, 3, 4)]
+
+
+def test_3d_galerkin_coarse_operator():
+    P = _problem3((9, 6, 5))
+    lv = sd.hierarchy(P.kx, P.ky, P.shape, P.kz)
+    c = 0.29
+    assert len(lv) == 3
+    for q in range(len(lv) - 1):
+        f, g = lv[q], lv[q + 1]
+        fs, cs = f.w.shape, g.w.shape
+        nf, nc = int(np.prod(fs)), int(np.prod(cs))
+        Pm = np.zeros((nf, nc))
+        for k in range(fs[0]):
+            for j in range(fs[1]):
+                for i in range(fs[2]):
+                    Pm[i + fs[2] * (j + fs[1] * k), (i // 2) + cs[2] * ((j // 2) + cs[1] * (k // 2))] = 1.0
+        Bf = np.column_stack([sd.level_apply(f, c, e.reshape(fs)).ravel() for e in np.eye(nf)])
+        Bc = np.column_stack([sd.level_apply(g, c, e.reshape(cs)).ravel() for e in np.eye(nc)])
+        assert np.abs(Pm.T @ Bf @ Pm - Bc).max() < 1e-12 * np.abs(Bc).max()
+
+
+def test_3d_vcycle_is_symmetric_positive_definite():
+    P = _problem3((10, 7, 6))
+    lv = sd.hierarchy(P.kx, P.ky, P.shape, P.kz)
+    rng = np.random.default_rng(15)
+    shp = lv[0].w.shape
+    for c in (-0.6, 0.4):
+        a, b = rng.standard_normal(shp), rng.standard_normal(shp)
+        va, vb = sd.vcycle(lv, c, a), sd.vcycle(lv, c, b)
+        assert abs(np.vdot(va, b) - np.vdot(a, vb)) < 1e-12 * np.abs(va).max() * np.abs(b).sum()
+        assert np.vdot(va, a) > 0 and np.vdot(vb, b) > 0
+
+
+def test_3d_krylov_iterates_match_scipy():
+    P = _problem3((9, 8, 6))
+    lv = sd.hierarchy(P.kx, P.ky, P.shape, P.kz)
+    shp = lv[0].w.shape
+    N = P.N
+    rng = np.random.default_rng(16)
+    c = -0.6
+    b = rng.standard_normal(shp)
+    Aop = sla.LinearOperator((N, N), matvec=lambda v: sd.level_apply(lv[0], c, v.reshape(shp)).ravel())
+    Mop = sla.LinearOperator((N, N), matvec=lambda v: sd.vcycle(lv, c, v.reshape(shp)).ravel())
+    for k in (1, 4):
+        ref, _ = sla.cg(Aop, b.ravel(), rtol=0.0, atol=0.0, maxiter=k, M=Mop)
+        assert np.abs(sd.pcg(lv, c, b, k).ravel() - ref).max() < 1e-10 * np.abs(ref).max()
+    lam = complex(np.conj(spc.scaled_roots(6, 1e-2)[1]))
+    c_pd = lam.imag - lam.real
+    fu, fv = rng.standard_normal(shp), rng.standard_normal(shp)
+
+    def S(v):
+        su, sv = sd.saddle_apply(lv, lam, v[:N].reshape(shp), v[N:].reshape(shp))
+        return np.concatenate([su.ravel(), sv.ravel()])
+
+    def M(v):
+        return np.concatenate([sd.vcycle(lv, c_pd, v[:N].reshape(shp)).ravel(),
+                               sd.vcycle(lv, c_pd, v[N:].reshape(shp)).ravel()])
+
+    Sop = sla.LinearOperator((2 * N, 2 * N), matvec=S)
+    Mop2 = sla.LinearOperator((2 * N, 2 * N), matvec=M)
+    for k in (2, 6):
+        ref, _ = sla.minres(Sop, np.concatenate([fu.ravel(), fv.ravel()]), rtol=0.0, maxiter=k, M=Mop2)
+        xu, xv = sd.minres(lv, lam, fu, fv, k)
+        assert np.abs(np.concatenate([xu.ravel(), xv.ravel()]) - ref).max() < 1e-9 * np.abs(ref).max(), k
+
+
+def test_3d_psp_tends_to_exact_palpha():
+    P = _problem3((6, 5, 4))
+    A = op.fv_dense(P.kx, P.ky, P.kz, P.shape)
+    r = np.random.default_rng(17).standard_normal((P.ell, P.N))
+    ze = pc.palpha_exact_apply(A, r, P.alpha)
+    errs = [np.abs(sd.psp_apply(P.kx, P.ky, P.shape, r, P.alpha, k, P.kz) - ze).max() / np.abs(ze).max()
+            for k in (8, 16, 40)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9
