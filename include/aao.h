@@ -299,10 +299,11 @@ int aao_get_tuning(aao_handle h, int32_t out[6]);
  *                          MINRES on the saddle-point system of twice the size with the
  *                          block-diagonal preconditioner P_D (Section 4's theorem); the SPD
  *                          blocks are applied by one V-cycle of this library's aggregation
- *                          multigrid (the paper uses an algebraic multigrid, HSL_MI20).
- *                          p = the handle's inner_its.  FP64 handles, 1D and 2D grids.
- * Returns AAO_EINVAL for an unknown mode, a mixed-precision handle, face diffusivities that
- * vary along an axis (exact mode, relative spread > 1e-12) or a 3D grid (P_SP).  With the
+ *                          multigrid (the paper uses an algebraic multigrid, HSL_MI20):
+ *                          2 x 2 (3D: 2 x 2 x 2) aggregates, Galerkin coarse levels.
+ *                          p = the handle's inner_its.  FP64 handles, 1D, 2D and 3D grids.
+ * Returns AAO_EINVAL for an unknown mode, a mixed-precision handle (P_SP and the exact mode)
+ * or face diffusivities that vary along an axis (exact mode, relative spread > 1e-12).  With the
  * exact mode the statistics count ell A-products per outer iteration (P_alpha^{-1} uses none);
  * with P_SP, ell + ell p (CG: one product per step on two real shifts; MINRES: two per step on
  * the ell/2 - 1 complex shifts that conjugate symmetry leaves).

@@ -1134,8 +1134,7 @@ int aao_set_precond_mode(aao_handle h, int mode) {
   }
   if (mode == AAO_PRECOND_SP) {
     if (h->prec != AAO_FP64) return fail(h, AAO_EINVAL, "P_SP is applied in FP64: create the handle with AAO_FP64");
-    if (h->dim > 2) return fail(h, AAO_EINVAL, "P_SP's multigrid is built for 1D and 2D grids");
-    if (!h->sp) AAO_CK(h, aao::sp_plan_create(&h->sp, h->g, h->dim, h->cx64, h->cy64, h->stream));
+    if (!h->sp) AAO_CK(h, aao::sp_plan_create(&h->sp, h->g, h->dim, h->cx64, h->cy64, h->cz64, h->stream));
     h->pmode = mode;
     reset_graphs(h);
     return AAO_OK;

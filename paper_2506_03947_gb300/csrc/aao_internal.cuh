@@ -179,10 +179,10 @@ cudaError_t launch_idft_planes(int64_t N, int ell, const double* y, double* z, c
 
 // P_SP (saddle.cu): fixed-iteration PCG on the real shifts and block-diagonally preconditioned
 // MINRES on the saddle-point systems of the complex ones, with one aggregation-multigrid
-// V-cycle per preconditioner block (Section 4).  1D/2D, FP64.
+// V-cycle per preconditioner block (Section 4).  1D/2D/3D, FP64.
 struct SpPlan;
 cudaError_t sp_plan_create(SpPlan** out, const GridDesc& g, int dim, const double* cx, const double* cy,
-                           cudaStream_t s);
+                           const double* cz, cudaStream_t s);
 void sp_plan_destroy(SpPlan* p);
 // vhat: packed frequency planes of the time DFT; y: ell planes of work space; z: result.
 cudaError_t sp_precond(SpPlan* p, const GridDesc& g, int ell, int iters, double* vhat, double* y, double* z,

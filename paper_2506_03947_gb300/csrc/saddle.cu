@@ -1,16 +1,16 @@
 // P_SP (Section 4): Eq. 5 with every shifted solve replaced by a fixed number of Krylov steps
-// in real arithmetic, FP64, 1D and 2D grids.
+// in real arithmetic, FP64, 1D, 2D and 3D grids.
 //   * real shifts (frequencies 0 and ell/2): preconditioned CG on B = A - lambda I;
 //   * complex shifts: MINRES on the saddle-point system S = [[Phi, Psi], [Psi, -Phi]]
 //     (Phi = Im(lambda') I > 0, Psi = A - Re(lambda') I, lambda' the shift with positive
 //     imaginary part: (A - lambda) x = b  <=>  (A - conj lambda) conj x = conj b), with the
 //     block-diagonal preconditioner P_D = diag(Phi + Psi, Phi + Psi) (Section 4's theorem).
 // The SPD blocks are applied by one V-cycle of an aggregation multigrid (the paper uses an
-// algebraic multigrid, HSL_MI20, as a black box): 2 x 2 aggregates, Galerkin coarse operators
+// algebraic multigrid, HSL_MI20, as a black box): 2 x 2 (3D: 2 x 2 x 2) aggregates, Galerkin coarse operators
 // with piecewise-constant prolongation (for B = (1 + c) I + K every level is (1 + c) W + K_H,
 // W the aggregate sizes, K_H with summed crossing face diffusivities), weighted Jacobi
 // (omega 2/3, two sweeps before and after the coarse correction), 16 sweeps on the coarsest
-// level (both sides <= 4 cells).  One hierarchy serves every shift.
+// level (every side <= 4 cells).  One hierarchy serves every shift.
 #include <cmath>
 #include <vector>
 
@@ -26,11 +26,22 @@ constexpr int kNuCoarse = 16;
 constexpr int kCoarsest = 4;
 
 struct Lvl {
-  int m0, m1;
+  int m0, m1, m2;
   const double* w;   // cell weights (nullptr on the finest level: all 1)
   const double* kx;  // face to +x of every cell (0 on the last column)
   const double* ky;  // face to +y (0 on the last row); nullptr for 1D
+  const double* kz;  // face to +z (0 on the last plane); nullptr for 1D and 2D
+  __host__ __device__ int64_t n() const { return (int64_t)m0 * m1 * m2; }
 };
+
+// (i, j, k) of cell q of a level
+__device__ __forceinline__ void cell_ijk(const Lvl& L, int64_t q, int& i, int& j, int& k) {
+  const int64_t pl = (int64_t)L.m0 * L.m1;
+  k = (int)(q / pl);
+  const int64_t r = q - (int64_t)k * pl;
+  j = (int)(r / L.m0);
+  i = (int)(r - (int64_t)j * L.m0);
+}
 
 // Up to two planes (the u and v blocks of one saddle system, or one CG vector) per launch,
 // each with its own shift c: B_c x = (1 + c) W x + K x.
@@ -38,32 +49,45 @@ struct Shifts {
   double c[2];
 };
 
-__device__ __forceinline__ double lvl_Bx(const Lvl& L, double c, const double* x, int i, int j, double xc,
+__device__ __forceinline__ double lvl_Bx(const Lvl& L, double c, const double* x, int i, int j, int k, double xc,
                                          double* diag) {
-  const int64_t q = (int64_t)j * L.m0 + i;
+  const int64_t pl = (int64_t)L.m0 * L.m1;
+  const int64_t q = (int64_t)k * pl + (int64_t)j * L.m0 + i;
   const double w = L.w ? L.w[q] : 1.0;
   double y = (1.0 + c) * w * xc;
   double d = (1.0 + c) * w;
   if (i < L.m0 - 1) {
-    const double k = L.kx[q];
-    y += k * (xc - x[q + 1]);
-    d += k;
+    const double f = L.kx[q];
+    y += f * (xc - x[q + 1]);
+    d += f;
   }
   if (i > 0) {
-    const double k = L.kx[q - 1];
-    y += k * (xc - x[q - 1]);
-    d += k;
+    const double f = L.kx[q - 1];
+    y += f * (xc - x[q - 1]);
+    d += f;
   }
   if (L.ky) {
     if (j < L.m1 - 1) {
-      const double k = L.ky[q];
-      y += k * (xc - x[q + L.m0]);
-      d += k;
+      const double f = L.ky[q];
+      y += f * (xc - x[q + L.m0]);
+      d += f;
     }
     if (j > 0) {
-      const double k = L.ky[q - L.m0];
-      y += k * (xc - x[q - L.m0]);
-      d += k;
+      const double f = L.ky[q - L.m0];
+      y += f * (xc - x[q - L.m0]);
+      d += f;
+    }
+  }
+  if (L.kz) {
+    if (k < L.m2 - 1) {
+      const double f = L.kz[q];
+      y += f * (xc - x[q + pl]);
+      d += f;
+    }
+    if (k > 0) {
+      const double f = L.kz[q - pl];
+      y += f * (xc - x[q - pl]);
+      d += f;
     }
   }
   if (diag) *diag = d;
@@ -74,80 +98,100 @@ __device__ __forceinline__ double lvl_Bx(const Lvl& L, double c, const double* x
 __global__ void __launch_bounds__(256)
     k_lvl(Lvl L, Shifts sh, int mode, int first, const double* __restrict__ b, const double* __restrict__ x,
           double* __restrict__ y) {
-  const int64_t n = (int64_t)L.m0 * L.m1;
+  const int64_t n = L.n();
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int p = blockIdx.y;
   const double c = sh.c[p];
   const double* xp = x ? x + p * n : nullptr;
-  const int i = (int)(q % L.m0), j = (int)(q / L.m0);
+  int i, j, k;
+  cell_ijk(L, q, i, j, k);
   if (mode == 2 && first) {
     double d;
-    lvl_Bx(L, c, b + p * n, i, j, 0.0, &d);  // diagonal only (x = 0)
+    lvl_Bx(L, c, b + p * n, i, j, k, 0.0, &d);  // diagonal only (x = 0)
     y[p * n + q] = kOmega * b[p * n + q] / d;
     return;
   }
   double d;
-  const double bx = lvl_Bx(L, c, xp, i, j, xp[q], &d);
+  const double bx = lvl_Bx(L, c, xp, i, j, k, xp[q], &d);
   if (mode == 0) y[p * n + q] = bx;
   else if (mode == 1) y[p * n + q] = b[p * n + q] - bx;
   else y[p * n + q] = xp[q] + kOmega * (b[p * n + q] - bx) / d;
 }
 
-// coarse b (c0 x c1) = sum of the fine residual over each aggregate; planes along blockIdx.y
+// coarse b = sum of the fine residual over each aggregate (2 x 2 x 2 cells, fewer at the far
+// edges and along axes of length 1); planes along blockIdx.y
 __global__ void __launch_bounds__(256)
-    k_restrict(int m0, int m1, int c0, int c1, const double* __restrict__ r, double* __restrict__ bc) {
+    k_restrict(Lvl f, Lvl c, const double* __restrict__ r, double* __restrict__ bc) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)c0 * c1) return;
+  if (q >= c.n()) return;
   const int p = blockIdx.y;
-  const int I = (int)(q % c0), J = (int)(q / c0);
-  const double* rp = r + (int64_t)p * m0 * m1;
+  int I, J, K;
+  cell_ijk(c, q, I, J, K);
+  const double* rp = r + (int64_t)p * f.n();
   double s = 0.0;
-  for (int dj = 0; dj < 2; ++dj)
-    for (int di = 0; di < 2; ++di) {
-      const int i = 2 * I + di, j = 2 * J + dj;
-      if (i < m0 && j < m1) s += rp[(int64_t)j * m0 + i];
-    }
-  bc[(int64_t)p * c0 * c1 + q] = s;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+        if (i < f.m0 && j < f.m1 && k < f.m2) s += rp[((int64_t)k * f.m1 + j) * f.m0 + i];
+      }
+  bc[(int64_t)p * c.n() + q] = s;
 }
 
 // fine x += coarse x of its aggregate
 __global__ void __launch_bounds__(256)
-    k_prolong_add(int m0, int m1, int c0, int c1, const double* __restrict__ xc, double* __restrict__ x) {
+    k_prolong_add(Lvl f, Lvl c, const double* __restrict__ xc, double* __restrict__ x) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)m0 * m1) return;
+  if (q >= f.n()) return;
   const int p = blockIdx.y;
-  const int i = (int)(q % m0), j = (int)(q / m0);
-  x[(int64_t)p * m0 * m1 + q] += xc[(int64_t)p * c0 * c1 + (int64_t)(j / 2) * c0 + i / 2];
+  int i, j, k;
+  cell_ijk(f, q, i, j, k);
+  x[(int64_t)p * f.n() + q] += xc[(int64_t)p * c.n() + ((int64_t)(k / 2) * c.m1 + j / 2) * c.m0 + i / 2];
 }
 
-// coarse weights and faces of the Galerkin product (sums over aggregates / crossing faces)
+// coarse weights and faces of the Galerkin product (sums over aggregates / crossing faces, in
+// the fine cells' order)
 __global__ void __launch_bounds__(256)
-    k_coarsen(Lvl f, int c0, int c1, double* __restrict__ w, double* __restrict__ kx, double* __restrict__ ky) {
+    k_coarsen(Lvl f, Lvl c, double* __restrict__ w, double* __restrict__ kx, double* __restrict__ ky,
+              double* __restrict__ kz) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= (int64_t)c0 * c1) return;
-  const int I = (int)(q % c0), J = (int)(q / c0);
-  double ws = 0.0, sx = 0.0, sy = 0.0;
-  for (int dj = 0; dj < 2; ++dj)
-    for (int di = 0; di < 2; ++di) {
-      const int i = 2 * I + di, j = 2 * J + dj;
-      if (i < f.m0 && j < f.m1) ws += f.w ? f.w[(int64_t)j * f.m0 + i] : 1.0;
-    }
-  if (I < c0 - 1) {
-    for (int dj = 0; dj < 2; ++dj) {
-      const int j = 2 * J + dj;
-      if (j < f.m1) sx += f.kx[(int64_t)j * f.m0 + 2 * I + 1];
-    }
+  if (q >= c.n()) return;
+  int I, J, K;
+  cell_ijk(c, q, I, J, K);
+  auto fidx = [&](int i, int j, int k) { return ((int64_t)k * f.m1 + j) * f.m0 + i; };
+  double ws = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * I + di, j = 2 * J + dj, k = 2 * K + dk;
+        if (i < f.m0 && j < f.m1 && k < f.m2) ws += f.w ? f.w[fidx(i, j, k)] : 1.0;
+      }
+  if (I < c.m0 - 1) {
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = 2 * J + dj, k = 2 * K + dk;
+        if (j < f.m1 && k < f.m2) sx += f.kx[fidx(2 * I + 1, j, k)];
+      }
   }
-  if (f.ky && J < c1 - 1) {
-    for (int di = 0; di < 2; ++di) {
-      const int i = 2 * I + di;
-      if (i < f.m0) sy += f.ky[(int64_t)(2 * J + 1) * f.m0 + i];
-    }
+  if (f.ky && J < c.m1 - 1) {
+    for (int dk = 0; dk < 2; ++dk)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * I + di, k = 2 * K + dk;
+        if (i < f.m0 && k < f.m2) sy += f.ky[fidx(i, 2 * J + 1, k)];
+      }
+  }
+  if (f.kz && K < c.m2 - 1) {
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * I + di, j = 2 * J + dj;
+        if (i < f.m0 && j < f.m1) sz += f.kz[fidx(i, j, 2 * K + 1)];
+      }
   }
   w[q] = ws;
   kx[q] = sx;
   if (ky) ky[q] = sy;
+  if (kz) kz[q] = sz;
 }
 
 // y = a[s] x + b[s] y + c[s] z over planes grouped by sub-problem (plane p belongs to s = p / pps);
@@ -172,12 +216,12 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_saddle(Lvl L, double phi, double re, const double* __restrict__ zu, const double* __restrict__ zv,
              double* __restrict__ su, double* __restrict__ sv) {
-  const int64_t n = (int64_t)L.m0 * L.m1;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const int i = (int)(q % L.m0), j = (int)(q / L.m0);
-  const double pu = lvl_Bx(L, -re, zu, i, j, zu[q], nullptr);
-  const double pv = lvl_Bx(L, -re, zv, i, j, zv[q], nullptr);
+  if (q >= L.n()) return;
+  int i, j, k;
+  cell_ijk(L, q, i, j, k);
+  const double pu = lvl_Bx(L, -re, zu, i, j, k, zu[q], nullptr);
+  const double pv = lvl_Bx(L, -re, zv, i, j, k, zv[q], nullptr);
   su[q] = phi * zu[q] + pv;
   sv[q] = pu - phi * zv[q];
 }
@@ -230,31 +274,37 @@ void sp_plan_destroy(SpPlan* p) {
 }
 
 cudaError_t sp_plan_create(SpPlan** out, const GridDesc& g, int dim, const double* cx, const double* cy,
-                           cudaStream_t s) {
+                           const double* cz, cudaStream_t s) {
   *out = nullptr;
-  if (dim > 2 || g.n2 != 1) return cudaErrorInvalidValue;
+  if (dim < 1 || dim > 3 || (dim < 3 && g.n2 != 1) || (dim == 3 && !cz)) return cudaErrorInvalidValue;
   SpPlan* p = new SpPlan();
   p->N = g.N;
   cudaError_t e = cudaSuccess;
-  p->lv.push_back(Lvl{g.n0, g.n1, nullptr, cx, dim >= 2 ? cy : nullptr});
-  while (e == cudaSuccess && (p->lv.back().m0 > kCoarsest || p->lv.back().m1 > kCoarsest)) {
+  p->lv.push_back(Lvl{g.n0, g.n1, g.n2, nullptr, cx, dim >= 2 ? cy : nullptr, dim == 3 ? cz : nullptr});
+  while (e == cudaSuccess &&
+         (p->lv.back().m0 > kCoarsest || p->lv.back().m1 > kCoarsest || p->lv.back().m2 > kCoarsest)) {
     const Lvl f = p->lv.back();
-    const int c0 = (f.m0 + 1) / 2, c1 = (f.m1 + 1) / 2;
-    const int64_t nc = (int64_t)c0 * c1;
-    double *w = nullptr, *kx = nullptr, *ky = nullptr;
+    Lvl c{(f.m0 + 1) / 2, (f.m1 + 1) / 2, (f.m2 + 1) / 2, nullptr, nullptr, nullptr, nullptr};
+    const int64_t nc = c.n();
+    double *w = nullptr, *kx = nullptr, *ky = nullptr, *kz = nullptr;
     e = cudaMalloc(&w, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&kx, sizeof(double) * nc);
     if (e == cudaSuccess && f.ky) e = cudaMalloc(&ky, sizeof(double) * nc);
-    for (double* d : {w, kx, ky})
+    if (e == cudaSuccess && f.kz) e = cudaMalloc(&kz, sizeof(double) * nc);
+    for (double* d : {w, kx, ky, kz})
       if (d) p->owned.push_back(d);
     if (e != cudaSuccess) break;
-    k_coarsen<<<blocks_for(nc), 256, 0, s>>>(f, c0, c1, w, kx, ky);
+    k_coarsen<<<blocks_for(nc), 256, 0, s>>>(f, c, w, kx, ky, kz);
     count_launch();
     e = cudaGetLastError();
-    p->lv.push_back(Lvl{c0, c1, w, kx, ky});
+    c.w = w;
+    c.kx = kx;
+    c.ky = ky;
+    c.kz = kz;
+    p->lv.push_back(c);
   }
   for (size_t q = 0; q < p->lv.size() && e == cudaSuccess; ++q) {
-    const int64_t n = 2 * (int64_t)p->lv[q].m0 * p->lv[q].m1;
+    const int64_t n = 2 * p->lv[q].n();
     double *a = nullptr, *b = nullptr, *bb = nullptr, *r = nullptr;
     e = cudaMalloc(&a, sizeof(double) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b, sizeof(double) * n);
@@ -288,7 +338,7 @@ cudaError_t vcycle(SpPlan* P, const Shifts& sh, int np, const double* b, double*
   const double* bq = b;
   for (int q = 0; q < nl; ++q) {
     const Lvl& L = P->lv[q];
-    const int64_t n = (int64_t)L.m0 * L.m1;
+    const int64_t n = L.n();
     const dim3 grid(blocks_for(n), np);
     const int sweeps = (q == nl - 1) ? kNuCoarse : kNu;
     double* cur = P->xa[q];
@@ -305,8 +355,7 @@ cudaError_t vcycle(SpPlan* P, const Shifts& sh, int np, const double* b, double*
     k_lvl<<<grid, 256, 0, s>>>(L, sh, 1, 0, bq, P->xa[q], P->rr[q]);
     count_launch();
     const Lvl& C = P->lv[q + 1];
-    k_restrict<<<dim3(blocks_for((int64_t)C.m0 * C.m1), np), 256, 0, s>>>(L.m0, L.m1, C.m0, C.m1, P->rr[q],
-                                                                         P->bb[q + 1]);
+    k_restrict<<<dim3(blocks_for(C.n()), np), 256, 0, s>>>(L, C, P->rr[q], P->bb[q + 1]);
     count_launch();
     bq = P->bb[q + 1];
   }
@@ -314,10 +363,10 @@ cudaError_t vcycle(SpPlan* P, const Shifts& sh, int np, const double* b, double*
   for (int q = nl - 2; q >= 0; --q) {
     const Lvl& L = P->lv[q];
     const Lvl& C = P->lv[q + 1];
-    const int64_t n = (int64_t)L.m0 * L.m1;
+    const int64_t n = L.n();
     const dim3 grid(blocks_for(n), np);
     const double* bl = (q == 0) ? b : P->bb[q];
-    k_prolong_add<<<grid, 256, 0, s>>>(L.m0, L.m1, C.m0, C.m1, P->xa[q + 1], P->xa[q]);
+    k_prolong_add<<<grid, 256, 0, s>>>(L, C, P->xa[q + 1], P->xa[q]);
     count_launch();
     // post-smoothing: ping-pong between xa[q] and xb[q]; the finest level's last sweep writes x
     double* cur = P->xa[q];

@@ -1,6 +1,7 @@
 """P_SP on the GPU (Section 4) against the oracle: the preconditioner apply (fixed-iteration
 CG on the real shifts, block-diagonally preconditioned MINRES on the saddle-point systems,
-aggregation-multigrid V-cycles), FGMRES solves with it, and its limit P_alpha."""
+aggregation-multigrid V-cycles; 1D, 2D and 3D grids, ragged and degenerate sizes), FGMRES solves
+with it, and its limit P_alpha."""
 import numpy as np
 import pytest
 
@@ -27,6 +28,9 @@ CASES = [
     ("2d_20x14_l6", lambda: inputs.make_problem("b", 2, (20, 14), 6, 1e-2, 1, 0.5, (4.0, 4.0), 5, 6), 10),
     ("2d_64x48_l10", lambda: inputs.make_problem("c", 2, (64, 48), 10, 1e-1, 1, 0.7, (8.0, 8.0), 7, 8), 4),
     ("2d_3x5_l4", lambda: inputs.make_problem("d", 2, (3, 5), 4, 0.5, 1, 0.5, (2.0, 2.0), 9, 10), 3),
+    ("3d_20x14x9_l6", lambda: inputs.make_problem("e3", 3, (20, 14, 9), 6, 1e-2, 1, 0.5, (4.0, 4.0, 3.0), 15, 16), 6),
+    ("3d_9x5x33_l8", lambda: inputs.make_problem("f3", 3, (9, 5, 33), 8, 1e-1, 1, 0.7, (3.0, 2.0, 6.0), 17, 18), 4),
+    ("3d_2x3x2_l4", lambda: inputs.make_problem("g3", 3, (2, 3, 2), 4, 0.5, 1, 0.5, (2.0, 2.0, 2.0), 19, 20), 3),
 ]
 
 
@@ -36,7 +40,7 @@ def test_psp_apply_matches_oracle(name, mk, k):
     binding = ensure_lib()
     P = mk()
     r = np.random.default_rng(2).standard_normal((P.ell, P.N))
-    ref = saddle.psp_apply(P.kx, P.ky, P.shape, r, P.alpha, k)
+    ref = saddle.psp_apply(P.kx, P.ky, P.shape, r, P.alpha, k, P.kz)
     s = _solver(P, binding.AAO_FP64, k)
     s.set_precond_mode(binding.AAO_PRECOND_SP)
     rd = to_dev(r)
@@ -83,6 +87,26 @@ def test_psp_tends_to_exact_palpha():
     assert np.abs(zd.cpu().numpy() - ze).max() < 1e-8 * np.abs(ze).max()
 
 
+def test_psp_solve_3d_matches_oracle():
+    torch = torch_cuda()
+    binding = ensure_lib()
+    P = inputs.make_problem("h3", 3, (16, 12, 10), 8, 1e-2, 1, 0.5, (4.0, 4.0, 3.0), 21, 22)
+    k = 6
+    A = make_block_op(P.kx, P.ky, P.kz, P.shape)
+    ref = gmres.fgmres(lambda v: allatonce.aao_apply(A, v),
+                       lambda r: saddle.psp_apply(P.kx, P.ky, P.shape, r, P.alpha, k, P.kz), P.b, 1e-8, 64)
+    s = _solver(P, binding.AAO_FP64, k)
+    s.set_precond_mode(binding.AAO_PRECOND_SP)
+    bd = to_dev(P.b)
+    xd = torch.zeros_like(bd)
+    s.solve(bd, xd, 1e-8, 64)
+    st = s.stats()
+    err = np.linalg.norm(xd.cpu().numpy() - ref.x) / np.linalg.norm(ref.x)
+    log_record({"test": "psp_solve_3d", "its": st["outer_its"], "its_oracle": ref.outer_its, "err": err})
+    assert st["converged"] and st["outer_its"] == ref.outer_its
+    assert err < 1e-7
+
+
 def test_psp_mode_rules():
     binding = ensure_lib()
     P = inputs.make_problem("g", 2, (16, 12), 6, 1e-2, 1, 0.5, (4.0, 4.0), 1, 2)
@@ -90,5 +114,6 @@ def test_psp_mode_rules():
         _solver(P, binding.AAO_MIXED, 5).set_precond_mode(binding.AAO_PRECOND_SP)
     P3 = inputs.make_problem("h", 3, (6, 5, 4), 6, 1e-2, 1, 0.5, (4.0, 4.0, 2.0), 1, 2)
     with pytest.raises(binding.AaoError) as ei:
-        _solver(P3, binding.AAO_FP64, 5).set_precond_mode(binding.AAO_PRECOND_SP)
-    assert "1D and 2D" in str(ei.value)
+        _solver(P3, binding.AAO_MIXED, 5).set_precond_mode(binding.AAO_PRECOND_SP)
+    assert "FP64" in str(ei.value)
+    _solver(P3, binding.AAO_FP64, 5).set_precond_mode(binding.AAO_PRECOND_SP)   # 3D is built
