@@ -366,7 +366,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(P, p, st32["outer_its"])
+        cpu = cpu_baseline_sample(args.workload, P, p, st32["outer_its"])
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -742,14 +742,37 @@ def oracle_rate(durations, its_per_solve):
     return len(durations) / (its_per_solve * sum(durations))
 
 
-def cpu_baseline_sample(P, p, outer_its):
-    """Oracle (numpy FP64, one thread) on a bounded sample: three consecutive outer FGMRES
-    iterations of a real oracle solve of the full workload, converted to solves/s with the
-    outer iteration count the solve needs."""
-    d, _ = oracle_iterations(P, p, 3, 0)
-    return {"value": oracle_rate(d, outer_its), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "the first 3 outer FGMRES iterations of an oracle solve on the full %dx%d grid "
-                      "(%.2f s), over %d outer iterations per solve" % (P.n[0], P.n[1], sum(d), outer_its)}
+def oracle_sample_in_child(workload, p, threads, iters=3):
+    """Durations of the first `iters` outer FGMRES iterations of an oracle solve, timed in a fresh
+    Python process whose BLAS/OpenMP thread pools are set to `threads` before numpy loads (this
+    process's numpy was loaded with the default pools) and which sees no GPU."""
+    code = ("import json, bench; P = bench.make_problem(%r); "
+            "d, _ = bench.oracle_iterations(P, %d, %d, 0); print(json.dumps(d))" % (workload, p, iters))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(threads)
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_sample(workload, P, p, outer_its):
+    """Oracle (numpy FP64) on a bounded sample: three consecutive outer FGMRES iterations of a
+    real oracle solve of the full workload, converted to solves/s with the outer iteration count
+    the solve needs; on one thread, and on all of the host's cores (BLAS pools; the oracle's
+    sparse products and transforms stay single-threaded)."""
+    nproc = os.cpu_count() or 1
+    d1 = oracle_sample_in_child(workload, p, 1)
+    dn = oracle_sample_in_child(workload, p, nproc)
+    desc = "the first 3 outer FGMRES iterations of an oracle solve on the full %dx%d grid (%.2f s), over %d " \
+           "outer iterations per solve"
+    return {"value": oracle_rate(d1, outer_its), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": desc % (P.n[0], P.n[1], sum(d1), outer_its),
+            "all_cores": {"value": oracle_rate(dn, outer_its), "unit": UNIT, "cores": nproc, "kind": "oracle",
+                          "sample": desc % (P.n[0], P.n[1], sum(dn), outer_its) +
+                          "; numpy's BLAS pools on all %d cores of this host" % nproc}}
 
 
 def oracle_outer_its(workload):
