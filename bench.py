@@ -167,6 +167,14 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # nvidia-smi's start-up (its first query) can hold the driver for tens of ms: wait for the
+        # first sample so that it falls before the timed region
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -231,6 +239,8 @@ def run_ours(args):
     L = P.ell * P.N
 
     def timed_solves(solver, steps, warmup, profile=False, sampler=None):
+        if sampler:
+            sampler.start()                     # before the warm-up: its start-up is not timed
         for _ in range(warmup):
             solver.solve(b, x, P.tol, 64)
         barrier()
@@ -238,8 +248,6 @@ def run_ours(args):
             solver.profile_enable(True)
         n0 = binding.aao_kernel_launch_count()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        if sampler:
-            sampler.start()
         t0 = time.perf_counter()
         walls = []
         for k in range(steps):
@@ -392,6 +400,7 @@ def run_ours(args):
         "fused_kernel": binding.KERNEL_NAMES.get(quad_kind), "fused_us_per_launch": round(avg_ms * 1e3, 2),
         "roofline_frac": round(achieved / peak, 4),
         "batch_instance_solves_s": round(batch["value"], 2) if batch else None,
+        "batch_fp64_sequential_solves_s": round(batch["fp64_sequential"]["value"], 2) if batch else None,
         "rhs3d_rhs_solves_s": round(rhs3d["value"], 3) if rhs3d else None,
         "cpu_oracle_solves_s": cpu["value"] if cpu else None}
     if rank == 0:
@@ -429,6 +438,7 @@ def run_batch_leg(args, binding, torch, sptr, peak):
     bprof = bat.profile()
     bat.profile_enable(False)
     fused_gbs = bprof["bytes"] / (bprof["ms"] * 1e-3) / 1e9 if bprof["ms"] > 0 else None
+    xb = [v.clone() for v in xs]              # the batch's solutions
     # sequential reference: the same instances one after another (single-instance path)
     for s, b, x in zip(solvers, bs, xs):
         s.solve(b, x, 1e-8, 200)
@@ -439,6 +449,27 @@ def run_batch_leg(args, binding, torch, sptr, peak):
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     bat.close()
+    # the all-FP64 GPU form of the same instances, one after another (a handle per instance,
+    # created and destroyed outside the timed solves), for the comparison at equal accuracy
+    t64 = 0.0
+    its64, diff64 = [], []
+    for s, P, b, xm in zip(solvers, probs, bs, xb):
+        s64 = binding.Solver(P.dim, P.n, P.kx.ravel(), P.ky.ravel(), None, P.ell, P.alpha, prec=binding.AAO_FP64,
+                             inner_its=P.inner_its, restart=64, stream=sptr)
+        x64 = torch.zeros_like(b)
+        s64.solve(b, x64, 1e-8, 200)
+        torch.cuda.synchronize()
+        x64.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        s64.solve(b, x64, 1e-8, 200)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1) * 1e-3
+        its64.append(s64.stats()["outer_its"])
+        diff64.append(float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)))
+        s64.close()
     cells = sum(P.N * P.ell for P in probs)
     return {"workload": "%d instances, grids {128..512}^2, ell {6..12}, alpha {1e-1,1e-2}, p=20, tol 1e-8"
                         % len(probs),
@@ -446,6 +477,12 @@ def run_batch_leg(args, binding, torch, sptr, peak):
             "value": len(probs) / tb, "unit": "instance solves/s", "ms_per_batch": tb * 1e3,
             "sequential_value": len(probs) / ts, "sequential_ms": ts * 1e3,
             "outer_its_max": max(its), "outer_its_mean": sum(its) / len(its), "all_converged": conv,
+            "fp64_sequential": {"value": len(probs) / t64, "unit": "instance solves/s", "ms": t64 * 1e3,
+                                "outer_its_max": max(its64), "outer_its_mean": sum(its64) / len(its64),
+                                "batch_minus_fp64_its_max": max(a - b for a, b in zip(its, its64)),
+                                "batch_vs_fp64_rel_diff_max": max(diff64),
+                                "timing": "CUDA events around one solve per instance (after one untimed solve), "
+                                          "all-FP64 handles one after another"},
             "fused_sweep": {"kernel": "kb_cheb_stream<S=4,D=3,NW=8> (one persistent warp-strip launch over "
                                       "(member, frequency pair, segment, strip) units from a device queue)",
                             "launches": bprof["launches"], "avg_launch_ms": bprof["ms"] / max(1, bprof["launches"]),
