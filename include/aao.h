@@ -371,8 +371,9 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
  * captured once as a CUDA graph and replayed.  The paper solves one instance
  * at a time; batching is this library's addition for covariance operators
  * applied to many fields at once.
- *   members    count handles created with AAO_MIXED, dim 2, n[0] % 4 == 0, and
- *              the same inner_its (>= 2) and restart; they must outlive the
+ *   members    count handles created with AAO_MIXED, all 2D or all 3D (3D:
+ *              inner_its >= 3), n[0] % 4 == 0, and the same inner_its (>= 2)
+ *              and restart; they must outlive the
  *              batch, and the batch uses their workspace (do not use the
  *              members concurrently with a batched solve).  The batch
  *              orthogonalises by modified Gram-Schmidt when every member
@@ -401,18 +402,28 @@ void aao_batch_destroy(aao_batch hb);
 
 /*
  * Fused sweep of the batch (no counterpart in the paper: launch parameters of
- * the same steps): AAO_STEP_STREAM with S = 4, segment height H (H + 8 a
- * multiple of 6), D in {3, 4} and NW = 8 (the default: H = 64, D = 3, used
- * when inner_its >= 7), or AAO_STEP_TILE (the shared-memory tile kernel, one
- * launch per distinct ell; S, H, D, NW ignored).  Drops the captured graphs.
+ * the same steps; 2D batches):
+ *   AAO_STEP_STREAM  S = 4, segment height H (H + 8 a multiple of 6), D in
+ *                    {3, 4} and NW = 8 (the default: H = 64, D = 3, used when
+ *                    inner_its >= 7).  As in the single solver: the transform
+ *                    and step 1 in one launch per ell, steps 2 .. p-1 as
+ *                    warp-strip launches over every member's units (step 2
+ *                    alone when their count is odd; a two-step final launch,
+ *                    H - 2, for a remainder of two), the final launch writing
+ *                    x_p, then the inverse transform per ell;
+ *   AAO_STEP_TILE    the shared-memory tile kernel, one launch per distinct
+ *                    ell, the last step fused with the inverse transform (S,
+ *                    H, D, NW ignored; the default when inner_its < 7);
+ *   AAO_STEP_AUTO    single steps (every 3D batch runs these).
+ * Drops the captured graphs.
  */
 int aao_batch_set_sweep(aao_batch hb, int kind, int S, int H, int D, int NW);
 /*
  * Event timing of the batch's Chebyshev sweeps (graphs are not used while it
  * is on; turning it on or off clears the totals).  With a fused sweep each
  * fused launch is timed: x_k, x_{k-1} or none, bhat and two face arrays read
- * and two fields written.  With single steps (the default, and every 3D batch)
- * the middle steps k = 2 .. p-2 of each ell group are timed as one span of
+ * and two fields written (one, x_p, by the final launch).  With single steps
+ * (every 3D batch) the middle steps k = 2 .. p-2 of each ell group are timed as one span of
  * p - 3 launches: x_k, x_{k-1} (none at k = 2) and bhat read and x_{k+1}
  * written per member, and the dim face arrays once per member, or once for
  * the whole group when the members share one operator.  4-byte values, over

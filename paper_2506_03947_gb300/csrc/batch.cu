@@ -9,6 +9,7 @@
 // CUDA graph.  The Chebyshev kernels are templated on ell, so their lists are
 // split by ell; the FP64 kernels take ell at run time.
 #include "batch.cuh"
+#include "cheb_ends.cuh"
 #include "cheb_kernels.cuh"
 #include "cheb_quad.cuh"
 #include "krylov_bodies.cuh"
@@ -49,6 +50,24 @@ __device__ __forceinline__ void step_block(const GridDesc& g, int lb, int& bx, i
   bz = lb / (gx * gy);
 }
 
+// The transform and step 1 of every member of one ell in one launch (ends::dft_first_body on
+// the same 128 x 8 tiles as the single steps; 2D): bhat and x_2 into field 0.
+template <int ELL>
+__global__ void __launch_bounds__(256) kb_dft_first(const BInst* __restrict__ I, const int* __restrict__ act,
+                                                     WorkList wl, int j) {
+  extern __shared__ __align__(16) float sb_first[];
+  __shared__ float gs[ELL];
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;  // the whole block: before any barrier
+  const BInst& b = I[inst];
+  const ScLayout L{b.m};
+  int bx, by, bz;
+  step_block(b.g, blockIdx.x - wl.start[li], bx, by, bz);
+  ends::dft_first_body<ELL>(b.g, bx, by, b.V + (int64_t)j * b.L, b.sc + L.vscale(j), b.bhat, b.xa, b.cx32, b.cy32,
+                            *b.da, b.steps[1], sb_first, gs);
+}
+
 // Step k = 1 from x_1 = bhat/theta (x_0 = 0): x_2 into field 0, or (LAST, p = 2) the inverse
 // transform into Z_j.
 template <int ELL, int DIM, bool LAST>
@@ -66,6 +85,25 @@ __global__ void __launch_bounds__(256) kb_step_first(const BInst* __restrict__ I
 
 __device__ __forceinline__ float* field(const BInst& b, int i) {
   return i == 0 ? b.xa : i == 1 ? b.xb : i == 2 ? b.xc : b.xd;
+}
+
+// z = Z_j = Gamma^{-1} U x_p for every member of one ell (ends::idft_pair), x_p in field fld;
+// member-local block lb covers cells [1024 lb, 1024 lb + 1024) (the list gives a member at least
+// N / 1024 blocks: its 128 x 8 tiles).
+template <int ELL>
+__global__ void __launch_bounds__(256) kb_idft(const BInst* __restrict__ I, const int* __restrict__ act, WorkList wl,
+                                                int j, int fld) {
+  const int li = wl_find(wl, blockIdx.x);
+  const int inst = wl.inst[li];
+  if (!act[inst]) return;
+  const BInst& b = I[inst];
+  const int64_t base = (int64_t)(blockIdx.x - wl.start[li]) * 1024;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t c = base + 512 * h + 2 * threadIdx.x;
+    if (c < b.g.N)
+      ends::idft_pair<ELL>(b.g.N, c, field(b, fld), b.Z + (int64_t)j * b.L, *b.ia);
+  }
 }
 
 // Steps k .. k+3 from x_k = field cur and x_{k-1} = field prev (PSRC 2) or bhat/theta (PSRC 1),
@@ -390,6 +428,55 @@ cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, int dim,
 #undef AAO_BH
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t batch_dft_first(const BInst* I, const int* act, int ell, const WorkList& wstep, int j, cudaStream_t s) {
+  if (wstep.cnt == 0) return cudaSuccess;
+  switch (ell) {
+#define AAO_BDF(L)                                                                                         \
+  case L: {                                                                                                \
+    const int smem = (int)(sizeof(float) * ends::dft_first_smem_floats(L));                              \
+    const cudaError_t e = cudaFuncSetAttribute(kb_dft_first<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (e != cudaSuccess) return e;                                                                        \
+    kb_dft_first<L><<<wstep.total, dim3(32, 8, 1), smem, s>>>(I, act, wstep, j);                          \
+    break;                                                                                                 \
+  }
+    AAO_BDF(4)
+    AAO_BDF(6)
+    AAO_BDF(8)
+    AAO_BDF(10)
+    AAO_BDF(12)
+    AAO_BDF(14)
+    AAO_BDF(16)
+#undef AAO_BDF
+    default:
+      return cudaErrorInvalidValue;
+  }
+  AAO_BCHECK();
+  return cudaSuccess;
+}
+
+cudaError_t batch_idft(const BInst* I, const int* act, int ell, const WorkList& wstep, int j, int fld,
+                       cudaStream_t s) {
+  if (wstep.cnt == 0) return cudaSuccess;
+  switch (ell) {
+#define AAO_BID(L) \
+  case L:          \
+    kb_idft<L><<<wstep.total, 256, 0, s>>>(I, act, wstep, j, fld); \
+    break;
+    AAO_BID(4)
+    AAO_BID(6)
+    AAO_BID(8)
+    AAO_BID(10)
+    AAO_BID(12)
+    AAO_BID(14)
+    AAO_BID(16)
+#undef AAO_BID
+    default:
+      return cudaErrorInvalidValue;
+  }
+  AAO_BCHECK();
+  return cudaSuccess;
 }
 
 cudaError_t batch_steps_mid(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,

@@ -78,6 +78,12 @@ cudaError_t batch_steps_mid(const BInst* I, const int* act, int ell, int dim, co
                             const WorkList& wstep, int p, int j, int kf, int* cur, int* prev, cudaStream_t s);
 cudaError_t batch_step_last(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
                             const WorkList& wstep, int p, int j, int cur, int prev, cudaStream_t s);
+// The ends of the warp-strip schedule (2D members of one ell; list wstep: the 128 x 8 tiles of
+// each member): the transform with step 1 (bhat and x_2 into field 0), and the inverse
+// transform of x_p (field fld) into Z_j.
+cudaError_t batch_dft_first(const BInst* I, const int* act, int ell, const WorkList& wstep, int j, cudaStream_t s);
+cudaError_t batch_idft(const BInst* I, const int* act, int ell, const WorkList& wstep, int j, int fld,
+                       cudaStream_t s);
 // Blocks of the single-step kernels (32 x 8 threads, four cells each along x) for one grid.
 int batch_step_blocks(const GridDesc& g);
 // Blocks of the matvec kernel (32 x 8 threads, one cell each) for one grid.
@@ -93,7 +99,8 @@ int batch_stream_units(const GridDesc& g, int ell, int S, int H);
 // One launch of S fused steps k .. k+S-1 over the units of every active member (list units:
 // member inst[i] owns units [start[i], start[i+1])), persistent over a device queue; the fields
 // are the members' rotating buffers (0..3): x_k = cur, x_{k-1} = prev (psrc 2) or bhat/theta
-// (psrc 1), outputs x_{k+S-1} -> o3 and x_{k+S} -> o4.
+// (psrc 1), outputs x_{k+S-1} -> o3 (o3 < 0: not written, the sweep's final launch) and
+// x_{k+S} -> o4.
 cudaError_t launch_batch_stream(const BInst* I, const int* act, const WorkList& units, const StreamConfig& c, int k,
                                 int psrc, int cur, int prev, int o3, int o4, StreamQueue* queue, cudaStream_t s);
 

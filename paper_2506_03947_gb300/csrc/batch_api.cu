@@ -46,6 +46,10 @@ struct aao_batch_ctx {
   aao::SharedSteps shared{false, 0, 0};  // right-hand sides of one operator
   aao::StreamConfig scfg{};
   aao::WorkList wunits{};
+  // the two-step final launch of a sweep whose remaining step count is 2 mod 4 (S = 2, the
+  // sweep's D, NW = 8, segment height H - 2) and its units
+  aao::StreamConfig tail{};
+  aao::WorkList wunits2{};
   aao::StreamQueue* queue = nullptr;
   std::vector<int> hact;  // host copy of the active flags
   // event timing of the Chebyshev sweeps (aao_batch_profile_enable; graphs are not used
@@ -101,16 +105,38 @@ int make_worklist(aao_batch_ctx* B, const std::vector<int>& inst, const std::vec
   return AAO_OK;
 }
 
+// The two-step tail configuration of a four-step sweep configuration, and its unit list.
+int set_tail(aao_batch_ctx* B, const aao::StreamConfig& c) {
+  aao::StreamConfig t = c;
+  t.S = 2;
+  t.H = c.H - 2;  // H + 8 a multiple of 6 <=> (H - 2) + 4 a multiple of 6
+  t.NW = 8;
+  if (!aao::stream_config_supported(t)) return bfail(B, AAO_EINVAL, "no two-step configuration for H=%d", c.H);
+  std::vector<int> all(B->M), nunits(B->M);
+  for (int i = 0; i < B->M; ++i) {
+    all[i] = i;
+    nunits[i] = aao::batch_stream_units(B->hI[i].g, B->hI[i].ell, 2, t.H);
+  }
+  aao::WorkList wl{};
+  const int rc = make_worklist(B, all, nunits, &wl);
+  if (rc) return rc;
+  B->wunits2 = wl;
+  B->tail = t;
+  return AAO_OK;
+}
+
 // Phases of Arnoldi step j for every active instance, in stream order.
 // Algorithmic bytes of one fused launch over the active members: x_k, x_{k-1} (psrc 2), bhat
 // and two face arrays read, two fields written, 4-byte values.
-double fused_bytes(const aao_batch_ctx* B, int psrc) {
+// fin: the sweep's final launch, which writes x_p alone.
+double fused_bytes(const aao_batch_ctx* B, int psrc, bool fin = false) {
+  const double sets = (psrc == 1 ? 2.0 : 3.0) + (fin ? 1.0 : 2.0);
   double t = 0.0;
   for (int i = 0; i < B->M; ++i)
-    if (B->hact.empty() || B->hact[i])
-      t += (double)B->hI[i].g.N * ((psrc == 1 ? 4.0 : 5.0) * 4.0 * B->hI[i].ell + 8.0);
+    if (B->hact.empty() || B->hact[i]) t += (double)B->hI[i].g.N * (sets * 4.0 * B->hI[i].ell + 8.0);
   return t;
 }
+
 
 // Algorithmic bytes of one single-step launch over the active members of the group with this
 // ell: x_k, x_{k-1} (psrc 2) and bhat read, x_{k+1} written, 4-byte values; the dim face arrays
@@ -145,32 +171,50 @@ int prof_begin(aao_batch_ctx* B, double bytes, int launches) {
 
 int batch_precond_stream(aao_batch_ctx* B, int j) {
   cudaStream_t s = B->stream;
-  for (size_t g = 0; g < B->wdft.size(); ++g)
-    AAO_BCK(B, aao::batch_precond_head(B->dI, B->dact, B->wdft[g].first, B->dim, B->shared, B->wdft[g].second,
-                                       B->wstep[g].second, B->p,
-                                       j, s));
-  // fused launches while steps k .. k+S-1 all come before the last step; the four fields rotate
-  // so that a launch never writes a field it reads (the single solver's schedule)
-  const int S = B->scfg.S;
-  int cur = 0, prev = -1, k = 2;
-  while (k + S - 1 <= B->p - 2) {
+  // the transform and step 1 of each ell group in one launch each (bhat and x_2 in field 0)
+  for (size_t g = 0; g < B->wstep.size(); ++g)
+    AAO_BCK(B, aao::batch_dft_first(B->dI, B->dact, B->wstep[g].first, B->wstep[g].second, j, s));
+  // steps 2 .. p-1 as in the single solver: step 2 alone when their count is odd, four-step
+  // launches, a two-step launch for a remainder of two; the final launch writes x_p alone.  The
+  // four fields rotate so that a launch never writes a field it reads.
+  int cur = 0, prev = -1, k = 2, R = B->p - 2;
+  if (R % 2 == 1) {
+    for (size_t g = 0; g < B->wstep.size(); ++g) {
+      int c = 0, pv = -1;  // one single step: the middle-step loop over k = 2 .. (k + 2) - 2
+      AAO_BCK(B, aao::batch_steps_mid(B->dI, B->dact, B->wstep[g].first, B->dim, B->shared, B->wstep[g].second, k + 2,
+                                      j, k, &c, &pv, s));
+      cur = c;
+      prev = pv;
+    }
+    ++k;
+    --R;
+  }
+  while (R > 0) {
+    const int S = R >= 4 ? 4 : 2;
+    const bool fin = (R == S);
+    const aao::StreamConfig& c = (S == 4) ? B->scfg : B->tail;
+    const aao::WorkList& units = (S == 4) ? B->wunits : B->wunits2;
     int o[2], n = 0;
     for (int f = 0; f < 4 && n < 2; ++f)
       if (f != cur && f != prev) o[n++] = f;
     const int psrc = prev < 0 ? 1 : 2;
-    const int ev = prof_begin(B, B->prof ? fused_bytes(B, psrc) : 0.0, 1);
+    const int ev = prof_begin(B, B->prof ? fused_bytes(B, psrc, fin) : 0.0, 1);
     if (ev == -2) return bfail(B, AAO_ECUDA, "profiling events could not be created or recorded");
-    AAO_BCK(B, aao::launch_batch_stream(B->dI, B->dact, B->wunits, B->scfg, k, psrc, cur, prev, o[0], o[1], B->queue,
-                                        s));
+    AAO_BCK(B, aao::launch_batch_stream(B->dI, B->dact, units, c, k, psrc, cur, prev, fin ? -1 : o[0],
+                                        fin ? o[0] : o[1], B->queue, s));
     if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
-    prev = o[0];
-    cur = o[1];
+    if (fin) {
+      cur = o[0];
+    } else {
+      prev = o[0];
+      cur = o[1];
+    }
     k += S;
+    R -= S;
   }
+  // z = Gamma^{-1} U x_p into Z_j, per ell group
   for (size_t g = 0; g < B->wstep.size(); ++g)
-    AAO_BCK(B, aao::batch_precond_tail(B->dI, B->dact, B->wstep[g].first, B->dim, B->shared, B->wstep[g].second,
-                                       B->p, j, k, cur, prev,
-                                       s));
+    AAO_BCK(B, aao::batch_idft(B->dI, B->dact, B->wstep[g].first, B->wstep[g].second, j, cur, s));
   return AAO_OK;
 }
 
@@ -427,6 +471,7 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
     std::vector<int> nunits(count);
     for (int i = 0; i < count; ++i) nunits[i] = aao::batch_stream_units(members[i]->g, members[i]->ell, 4, B->scfg.H);
     if (make_worklist(B, all, nunits, &B->wunits)) return bail(AAO_ECUDA);
+    if (set_tail(B, B->scfg)) return bail(AAO_ECUDA);
   }
   AAO_BCK_CREATE(cudaMalloc(&B->queue, sizeof(aao::StreamQueue)));
   AAO_BCK_CREATE(cudaMemset(B->queue, 0, sizeof(aao::StreamQueue)));
@@ -587,6 +632,8 @@ int aao_batch_set_sweep(aao_batch B, int kind, int S, int H, int D, int NW) {
     aao::WorkList wl{};
     const int rc = make_worklist(B, all, nunits, &wl);
     if (rc) return rc;
+    const int rt = set_tail(B, c);
+    if (rt) return rt;
     B->wunits = wl;
     B->scfg = c;
     B->sweep = kind;

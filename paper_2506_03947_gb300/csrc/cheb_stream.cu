@@ -34,6 +34,7 @@
 
 #include "aao_internal.cuh"
 #include "batch.cuh"
+#include "cheb_ends.cuh"
 
 namespace aao {
 
@@ -467,39 +468,14 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
 
 namespace {
 
-// z_t = gamma_t^{-1} sum_m (Re x_p(m) ci[t][m] - Im x_p(m) si[t][m]) (Eq. 5's Gamma^{-1} U) for
-// two consecutive cells per thread: the packed frequency planes of x_p in FP32 (plane 0 =
-// f_0, plane 1 = f_{ell/2}, planes 2m, 2m+1 = Re, Im f_m), z in FP64 (exact conversions of the
-// FP32 values, block-major like r).  Same summation order as the last-step kernel: f_0, then
-// f_{ell/2}, then m = 1 .. ell/2 - 1.
+// Inverse transform of x_p, two cells per thread (ends::idft_pair, cheb_ends.cuh).
 template <int ELL>
 __global__ void __launch_bounds__(256, 4) k_idft_planes(int64_t N2, int64_t N, const float* __restrict__ x,
                                                         double* __restrict__ z,
                                                         const __grid_constant__ IdftArgs<float> ia) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N2) return;
-  const int64_t c = 2 * q;
-  // all ELL planes of the two cells first (ELL 8-byte loads in flight), then one time block at
-  // a time
-  float2 v[ELL];
-#pragma unroll
-  for (int pl = 0; pl < ELL; ++pl) v[pl] = __ldcs(reinterpret_cast<const float2*>(x + (int64_t)pl * N + c));
-#pragma unroll
-  for (int t = 0; t < ELL; ++t) {
-    float a0 = 0.f, a1 = 0.f;
-    const float c0 = ia.ci[t][0], c1 = ia.ci[t][ELL / 2];
-    a0 += v[0].x * c0, a1 += v[0].y * c0;
-    a0 += v[1].x * c1, a1 += v[1].y * c1;
-#pragma unroll
-    for (int m = 1; m < ELL / 2; ++m) {
-      const float cr = ia.ci[t][m], si = ia.si[t][m];
-      const float2 r = v[2 * m], im = v[2 * m + 1];
-      a0 += r.x * cr - im.x * si;
-      a1 += r.y * cr - im.y * si;
-    }
-    const float gmul = ia.igamma_T[t];
-    *reinterpret_cast<double2*>(z + (int64_t)t * N + c) = make_double2(f2d_exact(a0 * gmul), f2d_exact(a1 * gmul));
-  }
+  ends::idft_pair<ELL>(N, 2 * q, x, z, ia);
 }
 
 }  // namespace
@@ -594,7 +570,7 @@ __global__ void __launch_bounds__(NW * 32, 1) kb_cheb_stream(const __grid_consta
       gg.bhat = b.bhat;
       gg.xk = bfield(b, ba.cur);
       gg.xkm1 = (PSRC == 2) ? bfield(b, ba.prev) : nullptr;
-      gg.outA = bfield(b, ba.o3);
+      gg.outA = ba.o3 < 0 ? nullptr : bfield(b, ba.o3);
       gg.outB = bfield(b, ba.o4);
       *geo = gg;
     }
@@ -685,6 +661,8 @@ cudaError_t launch_batch_stream(const BInst* I, const int* act, const WorkList& 
   if (c.S == SS && c.D == DD && c.NW == NN) return launch_batch_stream_cfg<SS, DD, NN>(ba, psrc, s);
   AAO_BSTREAM_CFG(4, 3, 8)
   AAO_BSTREAM_CFG(4, 4, 8)
+  AAO_BSTREAM_CFG(2, 3, 8)
+  AAO_BSTREAM_CFG(2, 4, 8)
 #undef AAO_BSTREAM_CFG
   return cudaErrorInvalidValue;
 }
