@@ -168,7 +168,7 @@ class ClockSampler:
         except Exception:
             self.proc = None
             return
-        # nvidia-smi's start-up (its first query) can hold the driver for tens of ms: wait for the
+        # nvidia-smi's start-up (its first query) can stall CUDA calls for tens of ms: wait for the
         # first sample so that it falls before the timed region
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
