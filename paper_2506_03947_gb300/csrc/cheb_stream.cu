@@ -4,8 +4,10 @@
 // frequency,
 //   x_{q+1} = x_q + a_q (x_q - x_{q-1}) + g_q (bhat - A x_q + lambda x_q),
 // with the residual formed as bhat + sum_f kappa_f x_nbr(f) - (d - lambda) x
-// (d = 1 + sum of the four face coefficients), in the same operation order as the shared-memory
-// tile kernel (bitwise equal results), with the two cells of a lane in packed FP32x2 operations.
+// (d = 1 + sum of the four face coefficients): the north and south terms first, packed over
+// the lane's two cells in FP32x2 operations, then the east and west terms per cell in scalar
+// FMAs (their operands straddle the lane's pair; packed, they needed register moves that cost
+// more than the scalar FMAs).  The rest of the step is packed.
 //
 // Organisation:
 //  * A unit of work is (plane pair, y segment, x strip).  A strip is 64 staged columns (lane l
@@ -81,6 +83,7 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return _
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // Per-level scalars of a pass, hoisted out of the step loop as duplicated pairs.  Real pass:
 // (l, a, g) of the two real frequencies; complex pass: (lr, li, ar, ai, gr, gi) of one frequency.
@@ -262,11 +265,12 @@ struct StreamUnit {
     for (int pl = 0; pl < 2; ++pl) {
       const float left = __shfl_up_sync(0xffffffffu, cur[pl].y, 1);
       const float right = __shfl_down_sync(0xffffffffu, cur[pl].x, 1);
-      float2 acc = f2fma(cf.e, make_float2(cur[pl].y, right), hh[pl]);
-      acc = f2fma(make_float2(cf.w0, cf.e.x), make_float2(left, cur[pl].x), acc);
-      acc = f2fma(cf.n, L[j][RN][pl], acc);
-      acc = f2fma(kS, L[j][RSo][pl], acc);
-      nb[pl] = acc;
+      // north and south on both cells packed (their operands are aligned pairs); east and west
+      // per cell in scalar FMAs (their operands straddle the lane's pair), written straight into
+      // the halves of the result
+      const float2 ns = f2fma(kS, L[j][RSo][pl], f2fma(cf.n, L[j][RN][pl], hh[pl]));
+      nb[pl].x = fmaf(cf.w0, left, fmaf(cf.e.x, cur[pl].y, ns.x));
+      nb[pl].y = fmaf(cf.e.x, cur[pl].x, fmaf(cf.e.y, right, ns.y));
     }
     float2 nw[2];
     const float2* q = pc.c[j];
@@ -275,10 +279,10 @@ struct StreamUnit {
       // the products with -li, -ai, -gi are formed as li (-xi), ai (-di), gi (-ri) (same values)
       const float2 xr = cur[0], xi = cur[1];
       const float2 ndl = f2add(cf.nd, q[0]);                 // -(d - lr)
-      const float2 rr = f2fma(q[1], f2mul(xi, m1), f2fma(ndl, xr, nb[0]));
+      const float2 rr = f2fma(q[1], neg2(xi), f2fma(ndl, xr, nb[0]));
       const float2 ri = f2fma(q[1], xr, f2fma(ndl, xi, nb[1]));
       const float2 dr = f2fma(pv[0], m1, xr), di = f2fma(pv[1], m1, xi), ndi = f2fma(xi, m1, pv[1]);
-      nw[0] = f2fma(q[5], f2mul(ri, m1), f2fma(q[4], rr, f2fma(q[3], ndi, f2fma(q[2], dr, xr))));
+      nw[0] = f2fma(q[5], neg2(ri), f2fma(q[4], rr, f2fma(q[3], ndi, f2fma(q[2], dr, xr))));
       nw[1] = f2fma(q[5], rr, f2fma(q[4], ri, f2fma(q[3], dr, f2fma(q[2], di, xi))));
     } else {
       const float2 x0 = cur[0], x1 = cur[1];
