@@ -149,6 +149,10 @@ struct StreamUnit {
   int offc;
   int y0;      // first interior row of the segment (stream row S)
   bool colok, interior_lane;
+  int ybase;   // grid row of stream row 0 (y0 - S)
+  int nrow;    // n1 when this lane's columns are inside the grid, else 0: stream row u is read
+               // iff (unsigned)(ybase + u) < nrow
+  int hout;    // rows of the segment this lane writes (0 for halo lanes and lanes outside)
   PassCoef<S> pc;
   float it[2];            // 1/theta (x_1 = bhat/theta): real (it0, it1), complex (re, im)
   float2 L[S][3][2];      // level windows: L[j][r % 3][plane] = level j of stream row r
@@ -166,8 +170,8 @@ struct StreamUnit {
   // copies of stream row u into ring slot SL of both rings
   template <int SL>
   __device__ __forceinline__ void issue(int u) {
-    const int y = y0 - S + u;
-    const bool ok = colok && y >= 0 && y < a.g.n1;
+    const int y = ybase + u;
+    const bool ok = (unsigned)y < (unsigned)nrow;
     const int64_t row = ok ? (int64_t)y * a.g.n0 : 0;
     const unsigned nb = ok ? 8u : 0u;
     const int64_t of = offf + row, oc = offc + row;
@@ -208,7 +212,7 @@ struct StreamUnit {
     levels<I>(std::make_integer_sequence<int, S>{});
     // outputs: level S and level S-1 of row t - S
     const int oy = t - 2 * S;
-    if (oy >= 0 && oy < a.H && interior_lane && colok && y0 + oy < a.g.n1) {
+    if ((unsigned)oy < (unsigned)hout) {
       constexpr int RS = ((PH - S) % 3 + 3) % 3;
       const int64_t o = offf + (int64_t)(y0 + oy) * a.g.n0;
       *reinterpret_cast<float2*>(a.outB + o) = last[0];
@@ -339,6 +343,9 @@ __device__ __forceinline__ void stream_unit(const StreamGeo& a, const StepArgs<f
   su.y0 = un.y0;
   su.colok = un.colok;
   su.interior_lane = lane >= S / 2 && lane < 32 - S / 2;
+  su.ybase = un.y0 - S;
+  su.nrow = un.colok ? a.g.n1 : 0;
+  su.hout = (su.interior_lane && un.colok) ? min(a.H, a.g.n1 - un.y0) : 0;
   su.offc = un.colok ? un.gx : 0;  // keep every source address inside its array
   su.offf = (int64_t)un.p0 * a.g.N + su.offc;
   if (CPLX) {
