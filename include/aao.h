@@ -220,7 +220,7 @@ int aao_set_step_kernel(aao_handle h, int kind);
  * Configuration of the warp-strip kernel (AAO_STEP_STREAM): S fused Chebyshev
  * steps per launch (the halo width; 2 or 4), H interior rows per segment
  * (1 <= H <= 4096, H + 2S a multiple of 6), D rows prefetched ahead (3 or 4)
- * and NW warps per CTA (S = 4: 6 or 8; S = 2: 8, 12 or 16).  No counterpart
+ * and NW warps per CTA (S = 4: 6, 8 or 12; S = 2: 8, 12 or 16).  No counterpart
  * in the paper: these are launch parameters of this library's kernel (Eq. 7's
  * steps are unchanged).  AAO_EINVAL for an unsupported combination.
  * aao_get_stream_config writes (S, H, D, NW) to out[0..3].

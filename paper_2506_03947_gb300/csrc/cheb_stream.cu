@@ -449,7 +449,7 @@ bool stream_config_supported(const StreamConfig& c) {
   if ((c.S != 2 && c.S != 4) || c.H < 1 || c.H > 4096 || (c.H + 2 * c.S) % kUnroll != 0) return false;
   if (c.D != 3 && c.D != 4) return false;
   if (c.S == 2) return c.NW == 8 || c.NW == 12 || c.NW == 16;
-  return c.NW == 6 || c.NW == 8;
+  return c.NW == 6 || c.NW == 8 || c.NW == 12;
 }
 
 cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConfig& c, const float* cx,
@@ -465,6 +465,8 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
   AAO_STREAM_CFG(4, 3, 8)
   AAO_STREAM_CFG(4, 4, 6)
   AAO_STREAM_CFG(4, 4, 8)
+  AAO_STREAM_CFG(4, 3, 12)
+  AAO_STREAM_CFG(4, 4, 12)
   AAO_STREAM_CFG(2, 3, 8)
   AAO_STREAM_CFG(2, 3, 12)
   AAO_STREAM_CFG(2, 4, 8)

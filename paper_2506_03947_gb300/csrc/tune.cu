@@ -374,9 +374,9 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
   for (int S : {2, 4}) {
     if (h->p - 2 < S) continue;  // no fused launch would run
     const int nws_s2[] = {8, 12, 16};
-    const int nws_s4[] = {6, 8};
+    const int nws_s4[] = {6, 8, 12};
     const int* nws = (S == 2) ? nws_s2 : nws_s4;
-    const int nnw = (S == 2) ? 3 : 2;
+    const int nnw = 3;
     for (int i = 0; i < nnw; ++i) {
       const int NW = nws[i];
       const int nstrip = (h->g.n0 + (64 - 2 * S) - 1) / (64 - 2 * S);
