@@ -741,6 +741,30 @@ def run_ncu_batch(args):
                       "outer_its_max": max(its), "outer_its_mean": sum(its) / len(its)}))
 
 
+def run_ncu_multi(args):
+    """One multi-right-hand-side solve (aao_solve_multi) of the 3D workload's operator at 96^3 with
+    eight right-hand sides, for an ncu launch list of its kernels (about 80 GB on the device)."""
+    import torch
+
+    from paper_2506_03947_gb300 import binding
+    from paper_2506_03947_gb300 import build as pkg_build
+    from paper_2506_03947_gb300 import inputs
+    pkg_build.build()
+    P = inputs.config_3d(n=96)
+    sptr = torch.cuda.current_stream().cuda_stream
+    kx, ky, kz = (torch.from_numpy(a.ravel()).cuda() for a in (P.kx, P.ky, P.kz))
+    s = binding.Solver(3, P.n, kx, ky, kz, P.ell, P.alpha, prec=binding.AAO_MIXED, inner_its=P.inner_its,
+                       restart=64, stream=sptr)
+    bs = [torch.from_numpy(P.b[i]).cuda() for i in range(P.b.shape[0])]
+    xs = [torch.zeros_like(b) for b in bs]
+    n0 = binding.aao_kernel_launch_count()
+    s.solve_multi(bs, xs, P.tol, 64)
+    torch.cuda.synchronize()
+    its = [s.multi_stats(i)["outer_its"] for i in range(len(bs))]
+    print(json.dumps({"ncu_multi": len(bs), "grid": list(P.n), "launches": binding.aao_kernel_launch_count() - n0,
+                      "outer_its": its}))
+
+
 def oracle_iterations(P, p, steps, warmup):
     """Time the oracle (numpy FP64) iteration by iteration on the full workload.
 
@@ -895,12 +919,17 @@ def main():
                     help="with --ncu-case: also one solve with a 16-vector Krylov space (about 3 GB)")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="run only one batched solve of the 64-instance workload without graphs (ncu launch list)")
+    ap.add_argument("--ncu-multi", action="store_true",
+                    help="run only one eight-right-hand-side solve of the 3D operator at 96^3 (ncu launch list)")
     args = ap.parse_args()
     if args.ncu_case:
         run_ncu_case(args)
         return
     if args.ncu_batch:
         run_ncu_batch(args)
+        return
+    if args.ncu_multi:
+        run_ncu_multi(args)
         return
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -32,7 +32,10 @@
  * host data through buffers it owns, with the copies on the handle's stream.
  * The caller owns every pointer it passes and keeps device buffers alive
  * until the call returns (all calls synchronise the handle's stream before
- * returning, except where noted).  The library owns all workspace.
+ * returning, except where noted).  The library owns all workspace.  Block
+ * vectors must be 8-byte aligned (AAO_EINVAL otherwise); an output written
+ * two doubles at a time (z of aao_precond_apply) that is device memory but
+ * not 16-byte aligned is staged like host memory and copied on the device.
  *
  * Threads and streams: one handle is used by one host thread at a time; all
  * device work of a handle is ordered on the stream given at creation.
@@ -517,7 +520,9 @@ int64_t aao_kernel_launch_count(void);
  *                  both are rejected.
  *   prec, inner_its                  as aao_options.
  *   mu_max         > 1: upper spectral bound to use; 0: the Gershgorin bound.
- *   r, z           ell*N doubles each, block-major, distinct.
+ *   r, z           ell*N doubles each, block-major, distinct; r 8-byte and z
+ *                  16-byte aligned (AAO_EINVAL otherwise: z is written two
+ *                  doubles at a time and there is no staging buffer).
  *   stream         cudaStream_t for the work (NULL = default stream).
  *   err, err_len   optional buffer for a one-line message on failure.
  * The call synchronises the stream before returning.  On its first call on

@@ -974,9 +974,14 @@ int aao_get_bounds(aao_handle h, double* mu_min, double* mu_max) {
   return AAO_OK;
 }
 
+// A double array must be 8-byte aligned: the kernels read and write it element by element at
+// least.  (Outputs written two doubles at a time are staged when not 16-byte aligned.)
+static bool misaligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7) != 0; }
+
 int aao_matvec(aao_handle h, const double* x, double* y) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   if (!x || !y || x == y) return fail(h, AAO_EINVAL, "aao_matvec: x and y must be distinct non-NULL pointers");
+  if (misaligned8(x) || misaligned8(y)) return fail(h, AAO_EINVAL, "aao_matvec: x and y must be 8-byte aligned");
   h->err.clear();
   if (is_other_device_ptr(x) || is_other_device_ptr(y))
     return fail(h, AAO_EINVAL, "aao_matvec: x and y must be host memory or memory of the current device");
@@ -1000,10 +1005,15 @@ int aao_matvec(aao_handle h, const double* x, double* y) {
 int aao_precond_apply(aao_handle h, const double* r, double* z) {
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   if (!r || !z || r == z) return fail(h, AAO_EINVAL, "aao_precond_apply: r and z must be distinct non-NULL pointers");
+  if (misaligned8(r) || misaligned8(z))
+    return fail(h, AAO_EINVAL, "aao_precond_apply: r and z must be 8-byte aligned");
   h->err.clear();
   if (is_other_device_ptr(r) || is_other_device_ptr(z))
     return fail(h, AAO_EINVAL, "aao_precond_apply: r and z must be host memory or memory of the current device");
-  const bool hr = !is_device_ptr(r), hz = !is_device_ptr(z);
+  // z is written two doubles at a time by the inverse transforms: a device z that is not
+  // 16-byte aligned is staged like host memory and copied on the device afterwards
+  const bool zdev = is_device_ptr(z);
+  const bool hr = !is_device_ptr(r), hz = !zdev || (reinterpret_cast<uintptr_t>(z) & 15) != 0;
   int rc = (hr || hz) ? ensure_stage(h) : AAO_OK;
   if (rc) return rc;
   const double* dr = r;
@@ -1016,7 +1026,9 @@ int aao_precond_apply(aao_handle h, const double* r, double* z) {
   rc = precond(h, dr, nullptr, dz);
   if (rc == AAO_OK) rc = check_tma(h);
   if (rc) return rc;
-  if (hz) AAO_CK(h, cudaMemcpyAsync(z, dz, sizeof(double) * h->L, cudaMemcpyDeviceToHost, h->stream));
+  if (hz)
+    AAO_CK(h, cudaMemcpyAsync(z, dz, sizeof(double) * h->L, zdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              h->stream));
   AAO_CK(h, cudaStreamSynchronize(h->stream));
   return AAO_OK;
 }
@@ -1026,6 +1038,7 @@ static int solve_entry(aao_handle h, const double* b, double* x, double tol, int
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   h->err.clear();
   if (!b || !x || b == x) return fail(h, AAO_EINVAL, "b and x must be distinct non-NULL pointers");
+  if (misaligned8(b) || misaligned8(x)) return fail(h, AAO_EINVAL, "b and x must be 8-byte aligned");
   if (!fixed && !(tol > 0.0 && tol < 1.0)) return fail(h, AAO_EINVAL, "tol must be in (0, 1)");
   if (max_outer < 1) return fail(h, AAO_EINVAL, "max_outer must be >= 1");
   if (fixed && fixed > h->m) return fail(h, AAO_EINVAL, "fixed step count %d exceeds restart %d", fixed, h->m);
@@ -1248,6 +1261,7 @@ int aao_solve_ci(aao_handle h, const double* b, double* x, double tol, int max_o
   if (!h) return fail(nullptr, AAO_EINVAL, "NULL handle");
   h->err.clear();
   if (!b || !x || b == x) return fail(h, AAO_EINVAL, "b and x must be distinct non-NULL pointers");
+  if (misaligned8(b) || misaligned8(x)) return fail(h, AAO_EINVAL, "b and x must be 8-byte aligned");
   if (!fixed_its && !(tol > 0.0 && tol < 1.0)) return fail(h, AAO_EINVAL, "tol must be in (0, 1)");
   if (max_outer < 1 && !fixed_its) return fail(h, AAO_EINVAL, "max_outer must be >= 1");
   if (fixed_its < 0) return fail(h, AAO_EINVAL, "fixed_its must be >= 0");

@@ -498,6 +498,8 @@ int aao_batch_solve(aao_batch B, const double* const* b, double* const* x, doubl
   for (int i = 0; i < M; ++i) {
     if (!is_device_ptr(b[i]) || !is_device_ptr(x[i]) || b[i] == x[i])
       return bfail(B, AAO_EINVAL, "instance %d: b and x must be distinct device pointers", i);
+    if (((reinterpret_cast<uintptr_t>(b[i]) | reinterpret_cast<uintptr_t>(x[i])) & 7) != 0)
+      return bfail(B, AAO_EINVAL, "instance %d: b and x must be 8-byte aligned", i);
     B->hI[i].b = b[i];
     B->hI[i].x = x[i];
   }

@@ -192,6 +192,9 @@ extern "C" int aao_precond_apply_noalloc(int dim, const int64_t n[3], const doub
       return say(err, err_len, AAO_EINVAL, "face array %d must be a device pointer on the current device", d);
   if (!on_device(r) || !on_device(z) || r == z)
     return say(err, err_len, AAO_EINVAL, "r and z must be distinct device pointers on the current device");
+  // r is read element by element; z is written two doubles at a time by the inverse transform
+  if ((reinterpret_cast<uintptr_t>(r) & 7) != 0 || (reinterpret_cast<uintptr_t>(z) & 15) != 0)
+    return say(err, err_len, AAO_EINVAL, "r must be 8-byte and z 16-byte aligned");
 
   const int64_t L = (int64_t)ell * N;
   const size_t Ts = (prec == AAO_MIXED) ? sizeof(float) : sizeof(double);

@@ -97,6 +97,36 @@ def test_precond_host_pointers_match_device_pointers():
     np.testing.assert_array_equal(zd.cpu().numpy(), z_host)
 
 
+def test_precond_unaligned_device_buffers():
+    # r read element by element may sit at any 8-byte boundary; a device z that is not 16-byte
+    # aligned (the inverse transform stores two doubles at a time) is staged and copied on the
+    # device, so both give the bits of the aligned apply
+    torch = torch_cuda()
+    binding = ensure_lib()
+    for prec, p in ((1, 9), (1, 2), (0, 5)):
+        P = inputs.config_2d(n=40)
+        s = make_solver(P, prec, p)
+        L = P.ell * P.N
+        rd = to_dev(_rand_block(P, 4))
+        zd = torch.empty_like(rd)
+        s.precond_apply(rd, zd)
+        rbuf = torch.zeros(L + 1, dtype=torch.float64, device="cuda")
+        zbuf = torch.full((L + 1,), float("nan"), dtype=torch.float64, device="cuda")
+        r1, z1 = rbuf[1:], zbuf[1:]
+        r1.copy_(rd.reshape(-1))
+        assert z1.data_ptr() % 16 == 8 and r1.data_ptr() % 16 == 8
+        s.precond_apply(r1, z1)
+        assert torch.equal(z1, zd.reshape(-1)), prec
+        assert torch.isnan(zbuf[0])                       # nothing written before z
+        # a pointer that is not 8-byte aligned is refused before any device work
+        lib = binding.load_library()
+        rc = lib.aao_precond_apply(s.h, rd.data_ptr() + 4, zd.data_ptr())
+        assert rc == binding.AAO_EINVAL
+        assert b"8-byte" in lib.aao_last_error(s.h)
+        rc = lib.aao_matvec(s.h, rd.data_ptr(), zd.data_ptr() + 4)
+        assert rc == binding.AAO_EINVAL
+
+
 def test_precond_is_deterministic():
     torch = torch_cuda()
     P = inputs.config_2d(n=48)

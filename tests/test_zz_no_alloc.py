@@ -105,3 +105,29 @@ def test_noalloc_refuses_memory_of_another_device():
                                           torch.cuda.current_stream().cuda_stream)
     assert ei.value.status == binding.AAO_EINVAL
     assert "current device" in str(ei.value)
+
+
+def test_noalloc_refuses_unaligned_buffers():
+    # z is written two doubles at a time and r read one at a time: a z off a 16-byte boundary
+    # or an r off an 8-byte one is refused before any launch (this entry point stages nothing)
+    torch = torch_cuda()
+    binding = ensure_lib()
+    Q = inputs.config_2d(n=32, ell=10, alpha=1e-2)
+    kx, ky, kz = _faces_dev(Q)
+    L = Q.ell * Q.N
+    buf = torch.zeros(L + 1, dtype=torch.float64, device="cuda")
+    r = torch.zeros(L, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(binding.AaoError) as ei:
+        binding.aao_precond_apply_noalloc(Q.dim, Q.n, kx, ky, kz, Q.ell, Q.alpha, 1, 5, 0.0, r, buf[1:], stream)
+    assert ei.value.status == binding.AAO_EINVAL and "16-byte" in str(ei.value)
+    # r at an 8-byte offset is accepted and gives the bits of the aligned call
+    z0 = torch.empty(L, dtype=torch.float64, device="cuda")
+    z1 = torch.empty(L, dtype=torch.float64, device="cuda")
+    r.copy_(torch.from_numpy(np.random.default_rng(5).standard_normal(L)).cuda())
+    buf[1:].copy_(r)
+    binding.aao_precond_apply_noalloc(Q.dim, Q.n, kx, ky, kz, Q.ell, Q.alpha, 1, 5, 0.0, r, z0, stream)
+    binding.aao_precond_apply_noalloc(Q.dim, Q.n, kx, ky, kz, Q.ell, Q.alpha, 1, 5, 0.0, buf[1:], z1, stream)
+    torch.cuda.synchronize()
+    assert torch.equal(z0, z1)
+
