@@ -567,14 +567,14 @@ def run_rhs3d_leg(args, binding, torch, sptr, peak):
                       "all_converged": all(r < P.tol for r in res_multi),
                       "timing": "CUDA events around one aao_solve_multi of the 8 right-hand sides (views allocated by "
                                 "an untimed call before)",
-                      "sweep": {"kernel": "kb_step_shared<10,3,1,2,false> (one Chebyshev step of every right-hand "
+                      "sweep": {"kernel": "kb_step_shared<10,3,1,2> (one Chebyshev step of every right-hand "
                                           "side per launch; each tile's stencil loaded once)",
                                 "launches": mprof["launches"],
                                 "avg_launch_ms": mprof["ms"] / max(1, mprof["launches"]),
                                 "bytes_per_launch": mprof["bytes"] / max(1, mprof["launches"]),
                                 "achieved_gbs": mgbs, "peak_gbs": peak,
                                 "frac": (mgbs / peak if mgbs else None),
-                                "timing": "CUDA events around the middle steps 2 .. p-2 of each Arnoldi step in one "
+                                "timing": "CUDA events around the steps 2 .. p-1 of each Arnoldi step in one "
                                           "extra solve without graphs"}},
             "one_after_another": {"value": len(bs) / (ms * 1e-3), "ms_per_rhs": ms / len(bs)},
             "outer_its": its, "resid_explicit_max": max(res), "all_converged": all(r < P.tol for r in res),

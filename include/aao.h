@@ -111,9 +111,11 @@ typedef struct {
 #define AAO_PROF_STEP_FIRST 1 /* Chebyshev step k = 1 (x_1 = bhat/theta); on the 2D mixed
                                  path one launch with the forward transform               */
 #define AAO_PROF_STEP_SECOND 2 /* Chebyshev step k = 2                                     */
-#define AAO_PROF_STEP_MID 3   /* Chebyshev steps 3 <= k <= p-2 (the fused sweep)           */
-#define AAO_PROF_STEP_LAST 4  /* last Chebyshev step fused with the inverse transform
-                                 (after a warp-strip sweep: the inverse transform of x_p)  */
+#define AAO_PROF_STEP_MID 3   /* single Chebyshev steps 3 <= k <= p-1 (k = p-1 when it
+                                 writes x_p for a separate inverse transform)             */
+#define AAO_PROF_STEP_LAST 4  /* the inverse transform of x_p (mixed precision with an
+                                 even cell count), else the last Chebyshev step fused with
+                                 the inverse transform                                    */
 #define AAO_PROF_MATVEC 5     /* script-A matvec and explicit residual                      */
 #define AAO_PROF_ORTH 6       /* Gram-Schmidt multi-dots, updates and their reductions     */
 #define AAO_PROF_STEP_PAIR 7  /* two fused Chebyshev steps (2D mixed path)                 */
@@ -426,8 +428,8 @@ int aao_batch_set_sweep(aao_batch hb, int kind, int S, int H, int D, int NW);
  * is on; turning it on or off clears the totals).  With a fused sweep each
  * fused launch is timed: x_k, x_{k-1} or none, bhat and two face arrays read
  * and two fields written (one, x_p, by the final launch).  With single steps
- * (every 3D batch) the middle steps k = 2 .. p-2 of each ell group are timed as one span of
- * p - 3 launches: x_k, x_{k-1} (none at k = 2) and bhat read and x_{k+1}
+ * (every 3D batch) the steps k = 2 .. p-1 of each ell group are timed as one span of
+ * p - 2 launches: x_k, x_{k-1} (none at k = 2) and bhat read and x_{k+1}
  * written per member, and the dim face arrays once per member, or once for
  * the whole group when the members share one operator.  4-byte values, over
  * the members active in each launch.  aao_batch_get_profile synchronises the

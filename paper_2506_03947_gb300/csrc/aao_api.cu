@@ -17,7 +17,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace aao {
@@ -170,24 +172,43 @@ int precond_impl(aao_ctx* h, const double* r, const double* rscale, double* z, c
     if (psrc == 1) return AAO_PROF_STEP_SECOND;
     return AAO_PROF_STEP_MID;
   };
-  // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in xa (or z if p == 2)
-  pi = prof_begin(h, step_class(0, 0, p == 2), step_bytes(0, 0, p == 2));
-  AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 0, 0, p == 2, cx, cy, cz, bhat, nullptr, xa, z, st[1], ia, s));
+  // In FP32 with an even cell count the last step runs as a middle step (x_p into the buffer of
+  // x_{p-2}) and the inverse transform is a launch of its own (k_idft_planes): the fused last
+  // step holds the ell time blocks of z in registers beside the stencil and runs far below the
+  // bandwidth of the two launches that replace it.
+  const bool split = std::is_same<T, float>::value && h->N % 2 == 0 && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
+  const int fused_last = split ? p : p - 1;  // the step that writes z itself (none when split)
+  // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in xa (or z)
+  pi = prof_begin(h, step_class(0, 0, fused_last == 1), step_bytes(0, 0, fused_last == 1));
+  AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 0, 0, fused_last == 1, cx, cy, cz, bhat, nullptr, xa, z, st[1],
+                                ia, s));
   prof_end(h, pi);
+  T* xp = xa;  // x_p when split
   if (p >= 3) {
-    // k = 2: x_2 from xa, x_1 = bhat/theta -> x_3 in xb
-    pi = prof_begin(h, step_class(1, 1, p == 3), step_bytes(1, 1, p == 3));
-    AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 1, 1, p == 3, cx, cy, cz, bhat, xa, xb, z, st[2], ia, s));
+    // k = 2: x_2 from xa, x_1 = bhat/theta -> x_3 in xb (or z)
+    pi = prof_begin(h, step_class(1, 1, fused_last == 2), step_bytes(1, 1, fused_last == 2));
+    AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 1, 1, fused_last == 2, cx, cy, cz, bhat, xa, xb, z, st[2], ia,
+                                  s));
     prof_end(h, pi);
+    xp = xb;
   }
   for (int k = 3; k <= p - 1; ++k) {
-    // x_k in `cur`, x_{k-1} in `prev`; x_{k+1} overwrites x_{k-1}
+    // x_k in `cur`, x_{k-1} in `prev`; x_{k+1} overwrites x_{k-1} (or goes to z)
     T* cur = (k % 2 == 1) ? xb : xa;
     T* prev = (k % 2 == 1) ? xa : xb;
-    const bool last = (k == p - 1);
+    const bool last = (k == fused_last);
     pi = prof_begin(h, step_class(1, 2, last), step_bytes(1, 2, last));
     AAO_CK(h, aao::launch_step<T>(h->g, h->dim, h->ell, 1, 2, last, cx, cy, cz, bhat, cur, prev, z, st[k], ia, s));
     prof_end(h, pi);
+    xp = prev;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (split) {
+      // z = Gamma^{-1} U x_p
+      pi = prof_begin(h, AAO_PROF_STEP_LAST, N * (4.0 * ell + 8.0 * ell));
+      AAO_CK(h, aao::launch_idft_planes(h->g, h->ell, xp, z, ia, s));
+      prof_end(h, pi);
+    }
   }
   return AAO_OK;
 }

@@ -68,9 +68,8 @@ __global__ void __launch_bounds__(256) kb_dft_first(const BInst* __restrict__ I,
                             *b.da, b.steps[1], sb_first, gs);
 }
 
-// Step k = 1 from x_1 = bhat/theta (x_0 = 0): x_2 into field 0, or (LAST, p = 2) the inverse
-// transform into Z_j.
-template <int ELL, int DIM, bool LAST>
+// Step k = 1 from x_1 = bhat/theta (x_0 = 0): x_2 into field 0.
+template <int ELL, int DIM>
 __global__ void __launch_bounds__(256) kb_step_first(const BInst* __restrict__ I, const int* __restrict__ act,
                                                       WorkList wl, int j) {
   const int li = wl_find(wl, blockIdx.x);
@@ -79,8 +78,8 @@ __global__ void __launch_bounds__(256) kb_step_first(const BInst* __restrict__ I
   const BInst& b = I[inst];
   int bx, by, bz;
   step_block(b.g, blockIdx.x - wl.start[li], bx, by, bz);
-  cheb_step_v4_body<ELL, DIM, 0, 0, LAST>(b.g, bx, by, bz, b.cx32, b.cy32, b.cz32, b.bhat, nullptr, b.xa,
-                                          b.Z + (int64_t)j * b.L, b.steps[1], *b.ia);
+  cheb_step_v4_body<ELL, DIM, 0, 0, false>(b.g, bx, by, bz, b.cx32, b.cy32, b.cz32, b.bhat, nullptr, b.xa,
+                                           nullptr, b.steps[1], *b.ia);
 }
 
 __device__ __forceinline__ float* field(const BInst& b, int i) {
@@ -125,8 +124,8 @@ __global__ void __launch_bounds__(kQuadTileNT, 2) kb_quad(const BInst* __restric
 }
 
 // One step k from x_k = field cur; x_{k-1} = field io (PSRC 2, overwritten by x_{k+1}) or
-// bhat/theta (PSRC 1, x_{k+1} into field io); LAST: inverse transform into Z_j instead.
-template <int ELL, int DIM, int PSRC, bool LAST>
+// bhat/theta (PSRC 1, x_{k+1} into field io).
+template <int ELL, int DIM, int PSRC>
 __global__ void __launch_bounds__(256) kb_step_f(const BInst* __restrict__ I, const int* __restrict__ act,
                                                   WorkList wl, int k, int j, int cur, int io) {
   const int li = wl_find(wl, blockIdx.x);
@@ -135,14 +134,14 @@ __global__ void __launch_bounds__(256) kb_step_f(const BInst* __restrict__ I, co
   const BInst& b = I[inst];
   int bx, by, bz;
   step_block(b.g, blockIdx.x - wl.start[li], bx, by, bz);
-  cheb_step_v4_body<ELL, DIM, 1, PSRC, LAST>(b.g, bx, by, bz, b.cx32, b.cy32, b.cz32, b.bhat, field(b, cur),
-                                             field(b, io), b.Z + (int64_t)j * b.L, b.steps[k], *b.ia);
+  cheb_step_v4_body<ELL, DIM, 1, PSRC, false>(b.g, bx, by, bz, b.cx32, b.cy32, b.cz32, b.bhat, field(b, cur),
+                                              field(b, io), nullptr, b.steps[k], *b.ia);
 }
 
 // Members that share one grid and its face coefficients (right-hand sides of one operator):
 // one block per tile of that grid; the tile's stencil is loaded once and applied to every
-// active member's fields.  KSRC 0: step k = 1 from x_1 = bhat/theta into field 0 (or Z_j).
-template <int ELL, int DIM, int KSRC, int PSRC, bool LAST>
+// active member's fields.  KSRC 0: step k = 1 from x_1 = bhat/theta into field 0.
+template <int ELL, int DIM, int KSRC, int PSRC>
 __global__ void __launch_bounds__(256) kb_step_shared(const BInst* __restrict__ I, const int* __restrict__ act, int M,
                                                        int k, int j, int cur, int io) {
   const BInst& b0 = I[0];
@@ -156,8 +155,8 @@ __global__ void __launch_bounds__(256) kb_step_shared(const BInst* __restrict__ 
     const BInst& b = I[r];
     const float* xk = (KSRC == 0) ? nullptr : field(b, cur);
     float* xio = (KSRC == 0) ? b.xa : field(b, io);
-    cheb_step_v4_apply<ELL, DIM, KSRC, PSRC, LAST>(b.g, st, c, b.bhat, xk, xio, b.Z + (int64_t)j * b.L,
-                                                   b.steps[KSRC == 0 ? 1 : k], *b.ia);
+    cheb_step_v4_apply<ELL, DIM, KSRC, PSRC, false>(b.g, st, c, b.bhat, xk, xio, nullptr, b.steps[KSRC == 0 ? 1 : k],
+                                                    *b.ia);
   }
 }
 
@@ -305,13 +304,8 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
   kb_dft<ELL><<<wdft.total, 256, 0, s>>>(I, act, wdft, j);
   AAO_BCHECK();
   const dim3 blk(32, 8, 1);
-  // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in field 0 (or Z_j if p == 2)
-  if (p == 2) {
-    kb_step_first<ELL, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
-    AAO_BCHECK();
-    return cudaSuccess;
-  }
-  kb_step_first<ELL, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
+  // k = 1: x_1 = bhat/theta, x_0 = 0 -> x_2 in field 0
+  kb_step_first<ELL, 2><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);
   AAO_BCHECK();
   // Four-step launches while steps k .. k+3 all come before the last step; the four fields
   // rotate so that a launch never writes a field it reads (same schedule as the single solver).
@@ -337,19 +331,17 @@ cudaError_t batch_precond_ell(const BInst* I, const int* act, const WorkList& wd
     cur = o[1];
     k += 4;
   }
-  // single steps up to p - 2, x_{k+1} over x_{k-1}
-  for (; k <= p - 2; ++k) {
+  // single steps up to p - 1, x_{k+1} over x_{k-1}; then z = Gamma^{-1} U x_p into Z_j
+  for (; k <= p - 1; ++k) {
     int dst = prev;
     if (dst < 0) dst = (cur == 0) ? 1 : 0;
-    if (prev < 0) kb_step_f<ELL, 2, 1, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
-    else kb_step_f<ELL, 2, 2, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    if (prev < 0) kb_step_f<ELL, 2, 1><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+    else kb_step_f<ELL, 2, 2><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
     AAO_BCHECK();
     prev = cur;
     cur = dst;
   }
-  // the last step k = p - 1, fused with the inverse transform into Z_j
-  if (prev < 0) kb_step_f<ELL, 2, 1, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
-  else kb_step_f<ELL, 2, 2, true><<<wstep.total, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
+  kb_idft<ELL><<<wstep.total, 256, 0, s>>>(I, act, wstep, j, cur);
   AAO_BCHECK();
   return cudaSuccess;
 }
@@ -362,8 +354,8 @@ cudaError_t batch_precond_head_ell(const BInst* I, const int* act, const SharedS
   kb_dft<ELL><<<wdft.total, 256, 0, s>>>(I, act, wdft, j);
   AAO_BCHECK();
   const dim3 blk(32, 8, 1);
-  if (sh.on) kb_step_shared<ELL, DIM, 0, 0, false><<<sh.ntiles, blk, 0, s>>>(I, act, sh.M, 1, j, 0, 0);
-  else kb_step_first<ELL, DIM, false><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);  // x_2 into field 0
+  if (sh.on) kb_step_shared<ELL, DIM, 0, 0><<<sh.ntiles, blk, 0, s>>>(I, act, sh.M, 1, j, 0, 0);
+  else kb_step_first<ELL, DIM><<<wstep.total, blk, 0, s>>>(I, act, wstep, j);  // x_2 into field 0
   AAO_BCHECK();
   return cudaSuccess;
 }
@@ -379,11 +371,11 @@ cudaError_t batch_steps_mid_ell(const BInst* I, const int* act, const SharedStep
     int dst = prev;
     if (dst < 0) dst = (cur == 0) ? 1 : 0;
     if (sh.on) {
-      if (prev < 0) kb_step_shared<ELL, DIM, 1, 1, false><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, dst);
-      else kb_step_shared<ELL, DIM, 1, 2, false><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, dst);
+      if (prev < 0) kb_step_shared<ELL, DIM, 1, 1><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, dst);
+      else kb_step_shared<ELL, DIM, 1, 2><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, dst);
     } else {
-      if (prev < 0) kb_step_f<ELL, DIM, 1, false><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
-      else kb_step_f<ELL, DIM, 2, false><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+      if (prev < 0) kb_step_f<ELL, DIM, 1><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
+      else kb_step_f<ELL, DIM, 2><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, dst);
     }
     AAO_BCHECK();
     prev = cur;
@@ -391,24 +383,6 @@ cudaError_t batch_steps_mid_ell(const BInst* I, const int* act, const SharedStep
   }
   *curp = cur;
   *prevp = prev;
-  return cudaSuccess;
-}
-
-template <int ELL, int DIM>
-cudaError_t batch_step_last_ell(const BInst* I, const int* act, const SharedSteps& sh, const WorkList& wstep, int p,
-                                int j, int cur, int prev, cudaStream_t s) {
-  if (!sh.on && wstep.cnt == 0) return cudaSuccess;
-  const dim3 blk(32, 8, 1);
-  const unsigned nb = sh.on ? (unsigned)sh.ntiles : (unsigned)wstep.total;
-  const int k = p - 1;
-  if (sh.on) {
-    if (prev < 0) kb_step_shared<ELL, DIM, 1, 1, true><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, cur);
-    else kb_step_shared<ELL, DIM, 1, 2, true><<<nb, blk, 0, s>>>(I, act, sh.M, k, j, cur, prev);
-  } else {
-    if (prev < 0) kb_step_f<ELL, DIM, 1, true><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, cur);
-    else kb_step_f<ELL, DIM, 2, true><<<nb, blk, 0, s>>>(I, act, wstep, k, j, cur, prev);
-  }
-  AAO_BCHECK();
   return cudaSuccess;
 }
 
@@ -495,31 +469,6 @@ cudaError_t batch_steps_mid(const BInst* I, const int* act, int ell, int dim, co
 #undef AAO_BM
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t batch_step_last(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
-                            const WorkList& wstep, int p, int j, int cur, int prev, cudaStream_t s) {
-  switch (ell * 10 + dim) {
-#define AAO_BL(L)                                                                            \
-  case L * 10 + 2: return batch_step_last_ell<L, 2>(I, act, sh, wstep, p, j, cur, prev, s); \
-  case L * 10 + 3: return batch_step_last_ell<L, 3>(I, act, sh, wstep, p, j, cur, prev, s);
-    AAO_BL(4)
-    AAO_BL(6)
-    AAO_BL(8)
-    AAO_BL(10)
-    AAO_BL(12)
-    AAO_BL(14)
-    AAO_BL(16)
-#undef AAO_BL
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
-                               const WorkList& wstep, int p, int j, int kf, int cur, int prev, cudaStream_t s) {
-  cudaError_t e = batch_steps_mid(I, act, ell, dim, sh, wstep, p, j, kf, &cur, &prev, s);
-  if (e != cudaSuccess) return e;
-  return batch_step_last(I, act, ell, dim, sh, wstep, p, j, cur, prev, s);
 }
 
 cudaError_t batch_precond(const BInst* I, const int* act, int ell, const WorkList& wdft, const WorkList& wstep,

@@ -53,15 +53,13 @@ cudaError_t batch_small(const BInst* I, const int* act, const WorkList& wone, in
 cudaError_t batch_norm2_b(const BInst* I, const int* act, const WorkList& wred, cudaStream_t s);
 cudaError_t batch_xupdate(const BInst* I, const int* act, const WorkList& wred, const int* kvec, cudaStream_t s);
 
-// P_NC^{-1} of Arnoldi step j in three parts, so that the fused sweeps of all members (any
-// ell) run as single launches: batch_precond_head (transform and step 1, per ell), the
-// caller's warp-strip launches (launch_batch_stream) for steps 2 .. kf-1, and
-// batch_precond_tail (single steps kf .. p-2 and the last step with the inverse transform,
-// per ell), with x_k in field cur and x_{k-1} in field prev (-1: bhat/theta) at kf.
+// The single-step sweep of P_NC^{-1} for Arnoldi step j, per ell: batch_precond_head (the
+// transform and step 1: bhat, and x_2 into field 0), batch_steps_mid (steps), and batch_idft
+// (the inverse transform of x_p, below).
 // dim: 2 or 3 (every member).  shared: every member has the same grid and face coefficients
 // (right-hand sides of one operator); the step kernels then take one block per tile of that
 // grid, load the tile's stencil once and apply it to every active member (M members,
-// ntiles = the tile count of the grid), and wstep is not used.
+// ntiles = the tile count of the grid), and wstep serves only the inverse transform.
 struct SharedSteps {
   bool on;
   int M;
@@ -69,18 +67,14 @@ struct SharedSteps {
 };
 cudaError_t batch_precond_head(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
                                const WorkList& wdft, const WorkList& wstep, int p, int j, cudaStream_t s);
-cudaError_t batch_precond_tail(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
-                               const WorkList& wstep, int p, int j, int kf, int cur, int prev, cudaStream_t s);
-// The middle single steps k = kf .. p-2 alone (no last step): cur and prev are updated to the
-// fields holding x_{p-1} and x_{p-2} (prev -1: bhat/theta).  batch_step_last then runs the last
-// step with the inverse transform.  Together they are batch_precond_tail.
+// Single steps k = kf .. p-2 (pass p + 1 to run through step p - 1, whose output is x_p), with
+// x_k in field *cur and x_{k-1} in field *prev (-1: bhat/theta) at kf; each writes x_{k+1} over
+// x_{k-1}.  On return *cur and *prev name the fields of the newest two iterates.
 cudaError_t batch_steps_mid(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
                             const WorkList& wstep, int p, int j, int kf, int* cur, int* prev, cudaStream_t s);
-cudaError_t batch_step_last(const BInst* I, const int* act, int ell, int dim, const SharedSteps& sh,
-                            const WorkList& wstep, int p, int j, int cur, int prev, cudaStream_t s);
-// The ends of the warp-strip schedule (2D members of one ell; list wstep: the 128 x 8 tiles of
-// each member): the transform with step 1 (bhat and x_2 into field 0), and the inverse
-// transform of x_p (field fld) into Z_j.
+// The ends of the sweep (members of one ell; list wstep: the 128 x 8 (x 1) tiles of each
+// member): the transform with step 1 (2D members: bhat and x_2 into field 0), and the inverse
+// transform of x_p (field fld) into Z_j (2D and 3D members, 1024 cells per block).
 cudaError_t batch_dft_first(const BInst* I, const int* act, int ell, const WorkList& wstep, int j, cudaStream_t s);
 cudaError_t batch_idft(const BInst* I, const int* act, int ell, const WorkList& wstep, int j, int fld,
                        cudaStream_t s);

@@ -245,17 +245,19 @@ int batch_step_launches(aao_batch_ctx* B, int j) {
     for (size_t g = 0; g < B->wstep.size(); ++g) {
       const int ell = B->wstep[g].first;
       int cur = 0, prev = -1;
-      // profiled: the middle steps 2 .. p-2 of the group as one timed span (p-3 launches)
+      // steps 2 .. p-1 as middle steps (the last one writes x_p), profiled as one timed span of
+      // p-2 launches; then z = Gamma^{-1} U x_p by the inverse-transform launch of the group.  A
+      // last step with the inverse transform fused (its z time blocks held in registers beside
+      // the stencil) runs far below the bandwidth of these two launches.
       double bytes = 0.0;
       if (B->prof)
-        for (int k = 2; k <= B->p - 2; ++k) bytes += single_bytes(B, ell, k == 2 ? 1 : 2);
-      const int ev = B->p > 3 ? prof_begin(B, bytes, B->p - 3) : -1;
+        for (int k = 2; k <= B->p - 1; ++k) bytes += single_bytes(B, ell, k == 2 ? 1 : 2);
+      const int ev = prof_begin(B, bytes, B->p - 2);
       if (ev == -2) return bfail(B, AAO_ECUDA, "profiling events could not be created or recorded");
-      AAO_BCK(B, aao::batch_steps_mid(B->dI, B->dact, ell, B->dim, B->shared, B->wstep[g].second, B->p, j, 2, &cur,
+      AAO_BCK(B, aao::batch_steps_mid(B->dI, B->dact, ell, B->dim, B->shared, B->wstep[g].second, B->p + 1, j, 2, &cur,
                                       &prev, s));
       if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
-      AAO_BCK(B, aao::batch_step_last(B->dI, B->dact, ell, B->dim, B->shared, B->wstep[g].second, B->p, j, cur, prev,
-                                      s));
+      AAO_BCK(B, aao::batch_idft(B->dI, B->dact, ell, B->wstep[g].second, j, cur, s));
     }
   } else {
     for (size_t g = 0; g < B->wdft.size(); ++g)

@@ -79,8 +79,9 @@ def test_multi_rhs_argument_checks():
 
 
 def test_multi_rhs_profile_counts_middle_steps():
-    """Event timing of the middle Chebyshev steps (k = 2 .. p-2, one span of p - 3 launches per
-    Arnoldi step); the profiled solve runs without graphs and gives the same bits."""
+    """Event timing of the single Chebyshev steps k = 2 .. p-1 (one span of p - 2 launches per
+    Arnoldi step; the last of them writes x_p for the inverse-transform launch); the profiled
+    solve runs without graphs and gives the same bits."""
     torch = torch_cuda()
     P = inputs.make_problem("m3p", 3, (40, 32, 24), 10, 1e-2, 7, 0.7, (8.0, 8.0, 4.0), 91, [92, 93, 94])
     p = 7
@@ -98,11 +99,11 @@ def test_multi_rhs_profile_counts_middle_steps():
     its = [s.multi_stats(i)["outer_its"] for i in range(nr)]
     for a, b in zip(xs, xp):
         assert torch.equal(a, b)
-    spans, rem = divmod(prof["launches"], p - 3)
+    spans, rem = divmod(prof["launches"], p - 2)
     assert rem == 0 and max(its) <= spans <= sum(its)
     N, ell = P.N, P.ell
-    one = sum((3.0 if k == 2 else 4.0) * 4.0 * ell * N + 12.0 * N for k in range(2, p - 1))
-    full = sum((3.0 if k == 2 else 4.0) * 4.0 * ell * N * nr + 12.0 * N for k in range(2, p - 1))
+    one = sum((3.0 if k == 2 else 4.0) * 4.0 * ell * N + 12.0 * N for k in range(2, p))
+    full = sum((3.0 if k == 2 else 4.0) * 4.0 * ell * N * nr + 12.0 * N for k in range(2, p))
     assert spans * one <= prof["bytes"] <= spans * full + 1.0
     assert prof["ms"] > 0.0
     log_record({"test": "multi_rhs_profile", "spans": spans, "its": its, "ms": prof["ms"],
