@@ -224,10 +224,16 @@ int aao_set_step_kernel(aao_handle h, int kind);
 /*
  * Configuration of the warp-strip kernel (AAO_STEP_STREAM): S fused Chebyshev
  * steps per launch (the halo width; 2 or 4), H interior rows per segment
- * (1 <= H <= 4096, H + 2S a multiple of 6), D rows prefetched ahead (3 or 4)
- * and NW warps per CTA (S = 4: 6, 8 or 12; S = 2: 8, 12 or 16).  No counterpart
- * in the paper: these are launch parameters of this library's kernel (Eq. 7's
- * steps are unchanged).  AAO_EINVAL for an unsupported combination.
+ * (1 <= H <= 4096), D rows prefetched ahead (3 or 4) and NW warps per CTA.
+ * H + 2S a multiple of 6: the S levels of a row step advance in lockstep (S = 4:
+ * NW 6, 8 or 12; S = 2: NW 8, 12 or 16).  S = 4 and H + 9 a multiple of 6: the
+ * skewed schedule, where levels 3 and 4 trail level 2 by one more row so that a
+ * row step holds two independent chains of levels (NW 8; one more row step per
+ * segment; the same arithmetic, bit for bit).  The default without a tune cache
+ * is S = 4 on the skewed schedule, D = 4, NW = 8 and the segment height that
+ * fills one round of the device's warps.  No counterpart in the paper: these
+ * are launch parameters of this library's kernel (Eq. 7's steps are
+ * unchanged).  AAO_EINVAL for an unsupported combination.
  * aao_get_stream_config writes (S, H, D, NW) to out[0..3].
  *
  * With the warp-strip kernel the sweep runs steps 2 .. p-1 (step 1 and, when

@@ -116,8 +116,8 @@ inline int effective_step_kernel(const aao_ctx* h) {
 StreamConfig default_stream_config(const GridDesc& g, int ell);
 StreamConfig default_tail_config(const GridDesc& g, int ell);
 // Configuration (S, D, NW) with the smallest segment height that puts all units of one launch
-// into `waves` rounds over the device's warps.
-StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW, int waves);
+// into `waves` rounds over the device's warps (skew 1: a height for the skewed schedule).
+StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW, int waves, int skew);
 // Apply the tune cache's entry for h, if a cache is configured and holds one (tune.cu).
 void apply_tune_cache(aao_ctx* h);
 // Release the views of aao_solve_multi (multi.cu).

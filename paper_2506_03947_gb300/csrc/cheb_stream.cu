@@ -136,10 +136,23 @@ struct StreamArgs {
   FuseSteps fs;
 };
 
-template <int S, int D, int PSRC, bool CPLX>
+// Row lag of level j behind the newest input row: level j of stream row t - lag(j) is computed
+// at step t.  Lockstep (SK 0): lag(j) = j, so within a step each level waits for the one below.
+// Skewed (SK 1, S = 4): lags 0, 1, 2, 4, 5, so levels 3 and 4 read rows of level 2 computed one
+// step earlier, and a step holds two independent chains, (row load, level 1, level 2) and
+// (level 3, level 4), at the cost of one more streamed step per unit.
+template <int SK>
+__device__ __host__ constexpr int level_lag(int j) {
+  return SK ? (j <= 2 ? j : j + 1) : j;
+}
+
+template <int S, int D, int PSRC, bool CPLX, int SK>
 struct StreamUnit {
   static constexpr int NA = StreamGeom<PSRC>::NA;
+  static constexpr int LS = level_lag<SK>(S);  // lag of the output level
   static_assert(D + 2 <= kRing && S + 2 <= kRing, "ring or window too shallow");
+  static_assert(SK == 0 || S == 4, "the skewed schedule is defined for S = 4");
+  static_assert(LS + 1 <= kRing, "face window too shallow");
 
   const StreamGeo& a;
   unsigned ringA, ringB;  // this warp's rings (shared addresses) plus the lane's 8-byte slot
@@ -158,6 +171,7 @@ struct StreamUnit {
   float2 L[S][3][2];      // level windows: L[j][r % 3][plane] = level j of stream row r
   float2 Hw[kRing][2];    // bhat of stream row r in Hw[r % 6][plane]
   RowCoef Cw[kRing];      // face coefficients of stream row r in Cw[r % 6]
+  float2 nS6;             // north faces of stream row t - 6 (SK 1: the south faces of level 4's row)
   float2 last[2];         // level S of the step's output row
 
   __device__ __forceinline__ unsigned slotA(int row_slot, int arr) const {
@@ -187,7 +201,7 @@ struct StreamUnit {
     cp8(slotB(SL, kB_N), a.cy + oc, nb);
   }
 
-  // step t = 6 b + I of the stream
+  // step t = 6 b + I of the stream (T: streamed input rows)
   template <int I>
   __device__ __forceinline__ void step(int t, int T) {
     constexpr int PH = I % 3;
@@ -195,7 +209,9 @@ struct StreamUnit {
     constexpr int SLm = (I + kRing - 1) % kRing;  // ... of row t - 1
     if (t + D < T) issue<(I + D) % kRing>(t + D);
     cp_commit();
-    cp_wait<D>();  // row t has landed (this lane's copies)
+    cp_wait<D>();  // row t has landed (this lane's copies); past the last row, stale rows feed
+                   // only halo rows that no output depends on
+    if (SK) nS6 = Cw[SL].n;  // row t - 6, about to be replaced by row t
     {
       L[0][PH][0] = lds2(slotA(SL, 0));
       L[0][PH][1] = lds2(slotA(SL, 1));
@@ -209,11 +225,20 @@ struct StreamUnit {
       const float2 t3 = f2add(f2add(c.e, make_float2(c.w0, c.e.x)), f2add(c.n, Cw[SLm].n));
       c.nd = f2fma(t3, dup(-1.f), dup(-1.f));  // -(1 + t3), exactly -RN(1 + t3)
     }
-    levels<I>(std::make_integer_sequence<int, S>{});
-    // outputs: level S and level S-1 of row t - S
-    const int oy = t - 2 * S;
+    if (SK) {
+      // levels 3 and 4 first (they read level 2's rows of earlier steps, and level 1's row
+      // t - 4, which level 1 replaces this step), then levels 1 and 2
+      level<I, 2>();
+      level<I, 3>();
+      level<I, 0>();
+      level<I, 1>();
+    } else {
+      levels<I>(std::make_integer_sequence<int, S>{});
+    }
+    // outputs: level S and level S-1 of stream row t - LS (segment row t - LS - S)
+    const int oy = t - LS - S;
     if ((unsigned)oy < (unsigned)hout) {
-      constexpr int RS = ((PH - S) % 3 + 3) % 3;
+      constexpr int RS = ((PH - LS) % 3 + 3) % 3;
       const int64_t o = offf + (int64_t)(y0 + oy) * a.g.n0;
       *reinterpret_cast<float2*>(a.outB + o) = last[0];
       *reinterpret_cast<float2*>(a.outB + o + a.g.N) = last[1];
@@ -229,17 +254,18 @@ struct StreamUnit {
     (level<I, J>(), ...);
   }
 
-  // level j+1 of stream row rho = t - 1 - j
+  // level j+1 of stream row rho = t - lag(j+1)
   template <int I, int j>
   __device__ __forceinline__ void level() {
-    constexpr int PH = I % 3;
-    constexpr int RS = ((PH - 1 - j) % 3 + 3) % 3;  // rho % 3
+    constexpr int LG = level_lag<SK>(j + 1);
+    constexpr int RS = ((I - LG) % 3 + 3) % 3;  // rho % 3
     constexpr int RN = (RS + 1) % 3, RSo = (RS + 2) % 3;
-    constexpr int W = ((I - 1 - j) % kRing + kRing) % kRing;   // rho % 6
-    constexpr int Wm = ((I - 2 - j) % kRing + kRing) % kRing;  // (rho - 1) % 6
-    constexpr int SAm = ((I - 1) % kRing + kRing) % kRing;     // ring A slot of row t - 1
+    constexpr int W = ((I - LG) % kRing + kRing) % kRing;       // rho % 6
+    constexpr int Wm = ((I - LG - 1) % kRing + kRing) % kRing;  // (rho - 1) % 6
+    constexpr int SAm = ((I - 1) % kRing + kRing) % kRing;      // ring A slot of row t - 1
+    static_assert(j > 0 || LG == 1, "level 1 reads x_{k-1} of row t - 1");
     const RowCoef& cf = Cw[W];
-    const float2 kS = Cw[Wm].n;
+    const float2 kS = (LG + 1 == kRing) ? nS6 : Cw[Wm].n;  // row t - 6 has left the window
     const float2* hh = Hw[W];
     const float2 m1 = dup(-1.f);
     float2 pv[2];
@@ -305,7 +331,8 @@ struct StreamUnit {
   }
 
   __device__ __forceinline__ void run() {
-    const int T = a.H + 2 * S;  // streamed rows, a multiple of 6
+    const int T = a.H + 2 * S;       // streamed input rows
+    const int TS = T + LS - S;       // steps, a multiple of 6
     issue<0>(0);
     cp_commit();
     issue<1>(1);
@@ -322,7 +349,8 @@ struct StreamUnit {
       for (int s2 = 0; s2 < 3; ++s2) L[j][s2][0] = L[j][s2][1] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kRing; ++r) Cw[r].n = make_float2(0.f, 0.f);
-    for (int t = 0; t < T; t += kUnroll) {
+    nS6 = make_float2(0.f, 0.f);
+    for (int t = 0; t < TS; t += kUnroll) {
       step<0>(t, T);
       step<1>(t + 1, T);
       step<2>(t + 2, T);
@@ -334,10 +362,10 @@ struct StreamUnit {
   }
 };
 
-template <int S, int D, int PSRC, bool CPLX>
+template <int S, int D, int PSRC, bool CPLX, int SK>
 __device__ __forceinline__ void stream_unit(const StreamGeo& a, const StepArgs<float>* steps, const Unit& un,
                                             int lane, unsigned ringA, unsigned ringB) {
-  StreamUnit<S, D, PSRC, CPLX> su{a};
+  StreamUnit<S, D, PSRC, CPLX, SK> su{a};
   su.ringA = ringA + (unsigned)(lane * 8);
   su.ringB = ringB + (unsigned)(lane * 8);
   su.y0 = un.y0;
@@ -359,7 +387,7 @@ __device__ __forceinline__ void stream_unit(const StreamGeo& a, const StepArgs<f
 
 // Registers: 8 warps of up to 200 per thread (two per SM sub-partition of 16 K registers); the
 // two-step variant with 12 warps stays within 168.
-template <int S, int D, int NW, int PSRC>
+template <int S, int D, int NW, int PSRC, int SK>
 __global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constant__ StreamArgs args) {
   const StreamGeo& a = args.geo;
   using G = StreamGeom<PSRC>;
@@ -392,13 +420,13 @@ __global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constan
     un.gx = strip * IW - S + 2 * lane;
     un.colok = un.gx >= 0 && un.gx < a.g.n0;
     if (pass == 0)
-      stream_unit<S, D, PSRC, false>(a, args.fs.s, un, lane, ringA, ringB);
+      stream_unit<S, D, PSRC, false, SK>(a, args.fs.s, un, lane, ringA, ringB);
     else
-      stream_unit<S, D, PSRC, true>(a, args.fs.s, un, lane, ringA, ringB);
+      stream_unit<S, D, PSRC, true, SK>(a, args.fs.s, un, lane, ringA, ringB);
   }
 }
 
-template <int S, int D, int NW>
+template <int S, int D, int NW, int SK>
 cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const float* cx, const float* cy,
                               const float* bhat, const float* xk, const float* xkm1, float* outA, float* outB,
                               const FuseSteps& fs, cudaStream_t s) {
@@ -427,13 +455,13 @@ cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const
   a.geo.outB = outB;
   a.fs = fs;
   if (psrc == 1) {
-    auto k = k_cheb_stream<S, D, NW, 1>;
+    auto k = k_cheb_stream<S, D, NW, 1, SK>;
     const size_t smem = (size_t)NW * 32 * StreamGeom<1>::lane_bytes;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NW * 32, smem, s>>>(a);
   } else {
-    auto k = k_cheb_stream<S, D, NW, 2>;
+    auto k = k_cheb_stream<S, D, NW, 2, SK>;
     const size_t smem = (size_t)NW * 32 * StreamGeom<2>::lane_bytes;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -445,10 +473,17 @@ cudaError_t launch_stream_cfg(const GridDesc& g, int ell, int psrc, int H, const
 
 }  // namespace
 
+// S = 4 launches stream H + 8 rows when that is a multiple of 6 (levels in lockstep), else the
+// skewed schedule when H + 9 is (one more step per unit; see level_lag).
+static int stream_skew(const StreamConfig& c) { return (c.S == 4 && (c.H + 2 * c.S) % kUnroll != 0) ? 1 : 0; }
+
 bool stream_config_supported(const StreamConfig& c) {
-  if ((c.S != 2 && c.S != 4) || c.H < 1 || c.H > 4096 || (c.H + 2 * c.S) % kUnroll != 0) return false;
+  if ((c.S != 2 && c.S != 4) || c.H < 1 || c.H > 4096) return false;
+  const int sk = stream_skew(c);
+  if ((c.H + 2 * c.S + (sk ? 1 : 0)) % kUnroll != 0) return false;
   if (c.D != 3 && c.D != 4) return false;
   if (c.S == 2) return c.NW == 8 || c.NW == 12 || c.NW == 16;
+  if (sk) return c.NW == 8;  // 196-205 registers: no room for 12 warps
   return c.NW == 6 || c.NW == 8 || c.NW == 12;
 }
 
@@ -458,21 +493,24 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
   if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2) || ell < 4 || ell > kMaxEll || (ell % 2) ||
       !stream_config_supported(c))
     return cudaErrorInvalidValue;
-#define AAO_STREAM_CFG(SS, DD, NN)                                                                             \
-  if (c.S == SS && c.D == DD && c.NW == NN)                                                                    \
-    return launch_stream_cfg<SS, DD, NN>(g, ell, psrc, c.H, cx, cy, bhat, xk, xkm1, outA, outB, fs, s);
-  AAO_STREAM_CFG(4, 3, 6)
-  AAO_STREAM_CFG(4, 3, 8)
-  AAO_STREAM_CFG(4, 4, 6)
-  AAO_STREAM_CFG(4, 4, 8)
-  AAO_STREAM_CFG(4, 3, 12)
-  AAO_STREAM_CFG(4, 4, 12)
-  AAO_STREAM_CFG(2, 3, 8)
-  AAO_STREAM_CFG(2, 3, 12)
-  AAO_STREAM_CFG(2, 4, 8)
-  AAO_STREAM_CFG(2, 4, 12)
-  AAO_STREAM_CFG(2, 3, 16)
-  AAO_STREAM_CFG(2, 4, 16)
+  const int sk = stream_skew(c);
+#define AAO_STREAM_CFG(SS, DD, NN, KK)                                                                         \
+  if (c.S == SS && c.D == DD && c.NW == NN && sk == KK)                                                        \
+    return launch_stream_cfg<SS, DD, NN, KK>(g, ell, psrc, c.H, cx, cy, bhat, xk, xkm1, outA, outB, fs, s);
+  AAO_STREAM_CFG(4, 3, 6, 0)
+  AAO_STREAM_CFG(4, 3, 8, 0)
+  AAO_STREAM_CFG(4, 4, 6, 0)
+  AAO_STREAM_CFG(4, 4, 8, 0)
+  AAO_STREAM_CFG(4, 3, 12, 0)
+  AAO_STREAM_CFG(4, 4, 12, 0)
+  AAO_STREAM_CFG(4, 3, 8, 1)
+  AAO_STREAM_CFG(4, 4, 8, 1)
+  AAO_STREAM_CFG(2, 3, 8, 0)
+  AAO_STREAM_CFG(2, 3, 12, 0)
+  AAO_STREAM_CFG(2, 4, 8, 0)
+  AAO_STREAM_CFG(2, 4, 12, 0)
+  AAO_STREAM_CFG(2, 3, 16, 0)
+  AAO_STREAM_CFG(2, 4, 16, 0)
 #undef AAO_STREAM_CFG
   return cudaErrorInvalidValue;
 }
@@ -604,9 +642,9 @@ __global__ void __launch_bounds__(NW * 32, 1) kb_cheb_stream(const __grid_consta
     un.colok = un.gx >= 0 && un.gx < a.g.n0;
     const StepArgs<float>* steps = b.steps + ba.k;
     if (pass == 0)
-      stream_unit<S, D, PSRC, false>(a, steps, un, lane, ringA, ringB);
+      stream_unit<S, D, PSRC, false, 0>(a, steps, un, lane, ringA, ringB);
     else
-      stream_unit<S, D, PSRC, true>(a, steps, un, lane, ringA, ringB);
+      stream_unit<S, D, PSRC, true, 0>(a, steps, un, lane, ringA, ringB);
   }
   // every warp ends here once, after its ticket past the end: the last one resets the queue
   // for the next launch
@@ -654,7 +692,8 @@ int batch_stream_units(const GridDesc& g, int ell, int S, int H) {
 
 cudaError_t launch_batch_stream(const BInst* I, const int* act, const WorkList& units, const StreamConfig& c, int k,
                                 int psrc, int cur, int prev, int o3, int o4, StreamQueue* queue, cudaStream_t s) {
-  if (!stream_config_supported(c) || (psrc != 1 && psrc != 2) || !queue) return cudaErrorInvalidValue;
+  if (!stream_config_supported(c) || stream_skew(c) || (psrc != 1 && psrc != 2) || !queue)
+    return cudaErrorInvalidValue;  // the batched launch runs the lockstep schedule
   if (units.total == 0) return cudaSuccess;
   StreamBatchArgs ba;
   ba.I = I;

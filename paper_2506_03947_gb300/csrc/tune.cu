@@ -235,10 +235,11 @@ std::string cache_path() {
   return env ? std::string(env) : std::string();
 }
 
-// A valid segment height for halo depth S (H + 2S a multiple of 6), at least h.
-int round_h(int h, int S) {
+// A valid segment height for halo depth S, at least h: H + 2S a multiple of 6 (levels in
+// lockstep), or with skew H + 2S + 1 (the skewed schedule of S = 4, one more step per unit).
+int round_h(int h, int S, int skew = 0) {
   h = std::max(h, 8);
-  while ((h + 2 * S) % 6) ++h;
+  while ((h + 2 * S + skew) % 6) ++h;
   return h;
 }
 
@@ -249,7 +250,7 @@ namespace aao {
 // Configuration (S, D, NW) with the smallest segment height that puts all units of one launch
 // into `waves` rounds over the device's warps (units = ell/2 passes x segments x strips of
 // 64 - 2S interior columns), at most one segment per strip.
-StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW, int waves) {
+StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW, int waves, int skew) {
   StreamConfig c;
   c.S = S;
   c.D = D;
@@ -264,18 +265,18 @@ StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW
   const int nstrip = (g.n0 + iw - 1) / iw;
   const int per_seg = (ell / 2) * nstrip;
   const int segs = std::max(1, waves * nsm * NW / std::max(1, per_seg));
-  c.H = round_h((g.n1 + segs - 1) / segs, S);
-  if (c.H > round_h(g.n1, S)) c.H = round_h(g.n1, S);
+  c.H = round_h((g.n1 + segs - 1) / segs, S, skew);
+  if (c.H > round_h(g.n1, S, skew)) c.H = round_h(g.n1, S, skew);
   return c;
 }
 
-// The warp-strip configuration used without a cache entry: S = 4, D = 3, 8 warps per CTA, one
-// round of units.
-StreamConfig default_stream_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 4, 3, 8, 1); }
+// The warp-strip configuration used without a cache entry: S = 4 on the skewed schedule, D = 4,
+// 8 warps per CTA, one round of units.
+StreamConfig default_stream_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 4, 4, 8, 1, 1); }
 
 // The two-step final launch: S = 2, D = 3, 16 warps per CTA (the two-step kernel stays within
 // 128 registers), one round of units.
-StreamConfig default_tail_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 2, 3, 16, 1); }
+StreamConfig default_tail_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 2, 3, 16, 1, 0); }
 
 // Apply the cache entry for this handle, if a cache is configured and holds one.
 void apply_tune_cache(aao_ctx* h) {
@@ -355,6 +356,7 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
 
   // candidates: the tile and TMA kernels, and warp-strip configurations whose segment heights
   // fill one, two or three rounds of units over the device's warps, plus one segment per strip
+  // (S = 4 with 6, 8 or 12 warps in lockstep, and with 8 warps on the skewed schedule)
   std::vector<aao_tune_entry> cand;
   auto add = [&](int kind, int S, int H, int D, int NW) {
     aao_tune_entry c{};
@@ -376,15 +378,16 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
     const int nws_s2[] = {8, 12, 16};
     const int nws_s4[] = {6, 8, 12};
     const int* nws = (S == 2) ? nws_s2 : nws_s4;
-    const int nnw = 3;
+    const int nnw = (S == 2) ? 3 : 4;
     for (int i = 0; i < nnw; ++i) {
-      const int NW = nws[i];
+      const int NW = i < 3 ? nws[i] : 8;
+      const int skew = i < 3 ? 0 : 1;
       const int nstrip = (h->g.n0 + (64 - 2 * S) - 1) / (64 - 2 * S);
-      const int hmax = aao::round_h(h->g.n1, S);
+      const int hmax = aao::round_h(h->g.n1, S, skew);
       std::vector<int> hs = {hmax};
       for (int w = 1; w <= 3; ++w) {
         const int segs = w * nsm * NW / std::max(1, npass * nstrip);
-        if (segs >= 1) hs.push_back(std::min(hmax, aao::round_h((h->g.n1 + segs - 1) / segs, S)));
+        if (segs >= 1) hs.push_back(std::min(hmax, aao::round_h((h->g.n1 + segs - 1) / segs, S, skew)));
       }
       for (int H : hs)
         for (int D : {3, 4}) {
@@ -453,7 +456,7 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
     for (int NW : {8, 12, 16})
       for (int D : {3, 4})
         for (int w = 1; w <= 3; ++w) {
-          const aao::StreamConfig c = aao::wave_stream_config(h->g, h->ell, 2, D, NW, w);
+          const aao::StreamConfig c = aao::wave_stream_config(h->g, h->ell, 2, D, NW, w, 0);
           bool dup = false;
           for (size_t i = i0; i < cand.size(); ++i)
             dup = dup || (cand[i].H == c.H && cand[i].D == D && cand[i].NW == NW);

@@ -80,7 +80,8 @@ def test_persistent_kernel_whole_field_matches_oracle(name, mk, p):
 
 
 STREAM_CASES = [
-    ("bench1024_p40_default", lambda: inputs.config_2d_large(inner_its=40), 40, (4, 88, 4, 8)),
+    ("bench1024_p40_lockstep", lambda: inputs.config_2d_large(inner_its=40), 40, (4, 88, 4, 8)),
+    ("bench1024_p40_skewed", lambda: inputs.config_2d_large(inner_its=40), 40, (4, 87, 4, 8)),
     ("bench1024_p12_H16", lambda: inputs.config_2d_large(inner_its=12), 12, (4, 16, 3, 6)),
     ("g1204x500_l16_p21_H28", lambda: inputs.make_problem("g1204x500", 2, (1204, 500), 16, 1e-2, 21, 0.8,
                                                           (16.0, 16.0), 53, 54), 21, (4, 28, 4, 6)),
