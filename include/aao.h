@@ -123,8 +123,9 @@ typedef struct {
 #define AAO_NPROF 9
 
 /* Accumulated device time of each kernel class, from CUDA events recorded on
- * the handle's stream around every launch while profiling is on, with the
- * algorithmic bytes each launch must move (reads + writes of its operands,
+ * the handle's stream around every launch while profiling is on (around the
+ * warp-strip launches of one apply together, which run back to back), with
+ * the algorithmic bytes each launch must move (reads + writes of its operands,
  * every value once). */
 typedef struct {
   int64_t launches[AAO_NPROF];
@@ -414,8 +415,9 @@ void aao_batch_destroy(aao_batch hb);
 /*
  * Fused sweep of the batch (no counterpart in the paper: launch parameters of
  * the same steps; 2D batches):
- *   AAO_STEP_STREAM  S = 4, segment height H (H + 8 a multiple of 6), D in
- *                    {3, 4} and NW = 8 (the default: H = 64, D = 3, used when
+ *   AAO_STEP_STREAM  S = 4, segment height H (H + 8 a multiple of 6: the
+ *                    lockstep schedule; the skewed one is the single solver's
+ *                    only), D in {3, 4} and NW = 8 (the default: H = 64, D = 3, used when
  *                    inner_its >= 7).  As in the single solver: the transform
  *                    and step 1 in one launch per ell, steps 2 .. p-1 as
  *                    warp-strip launches over every member's units (step 2
@@ -423,9 +425,11 @@ void aao_batch_destroy(aao_batch hb);
  *                    H - 2, for a remainder of two), the final launch writing
  *                    x_p, then the inverse transform per ell;
  *   AAO_STEP_TILE    the shared-memory tile kernel, one launch per distinct
- *                    ell, the last step fused with the inverse transform (S,
- *                    H, D, NW ignored; the default when inner_its < 7);
- *   AAO_STEP_AUTO    single steps (every 3D batch runs these).
+ *                    ell, single steps through step p-1 and the inverse
+ *                    transform per ell (S, H, D, NW ignored; the default when
+ *                    inner_its < 7);
+ *   AAO_STEP_AUTO    single steps through step p-1 and the inverse transform
+ *                    (every 3D batch runs these).
  * Drops the captured graphs.
  */
 int aao_batch_set_sweep(aao_batch hb, int kind, int S, int H, int D, int NW);

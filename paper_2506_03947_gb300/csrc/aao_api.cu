@@ -263,6 +263,9 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
       ++k;
       --R;
     }
+    // The warp-strip launches run back to back: one event span over all of them, whose
+    // average is the per-launch time (events between them would add gaps of their own).
+    const int span = prof_begin(h, AAO_PROF_STEP_QUAD, 0.0, 0);
     while (R > 0) {
       const bool four = h->scfg.S == 4 && R >= 4;
       const aao::StreamConfig& c = (four || h->scfg.S == 2) ? h->scfg : h->tail;
@@ -274,11 +277,13 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
       aao::FuseSteps fs;
       for (int q = 0; q < S; ++q) fs.s[q] = st[k + q];
       const double sets = (prev < 0 ? 2.0 : 3.0) + (fin ? 1.0 : 2.0);
-      pi = prof_begin(h, AAO_PROF_STEP_QUAD, N * (sets * 4.0 * ell + 8.0));
+      if (span >= 0) {
+        h->pending[span].bytes += N * (sets * 4.0 * ell + 8.0);
+        h->pending[span].launches += 1;
+      }
       AAO_CK(h, aao::launch_stream(h->g, h->ell, prev < 0 ? 1 : 2, c, cx, cy, bhat, X[cur],
                                    prev < 0 ? nullptr : X[prev], fin ? nullptr : X[o[0]], fin ? X[o[0]] : X[o[1]],
                                    fs, s));
-      prof_end(h, pi);
       if (fin) {
         cur = o[0];
       } else {
@@ -288,6 +293,7 @@ int precond_pairs(aao_ctx* h, const double* r, const double* rscale, double* z) 
       k += S;
       R -= S;
     }
+    prof_end(h, span);
     // z = Gamma^{-1} U x_p
     pi = prof_begin(h, AAO_PROF_STEP_LAST, N * (4.0 * ell + 8.0 * ell));
     AAO_CK(h, aao::launch_idft_planes(h->g, h->ell, X[cur], z, ia, s));

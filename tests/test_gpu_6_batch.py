@@ -202,4 +202,7 @@ def test_batch_profile_reports_fused_sweeps():
     cells = sum(P.N * ((4 + 5 + 4) * 4.0 * P.ell + 3 * 8) for P in probs)
     assert 0 < prof["bytes"] <= its * cells * 1.01
     with pytest.raises(binding.AaoError):
-        batch.set_sweep(binding.AAO_STEP_STREAM, 4, 63, 3, 8)       # H + 8 not a multiple of 6
+        batch.set_sweep(binding.AAO_STEP_STREAM, 4, 62, 3, 8)       # H + 8 not a multiple of 6
+    with pytest.raises(binding.AaoError) as ei:
+        batch.set_sweep(binding.AAO_STEP_STREAM, 4, 63, 3, 8)       # the skewed schedule: single solver only
+    assert "lockstep" in str(ei.value)

@@ -77,7 +77,7 @@ def test_step_kernels_match_oracle_and_each_other(n0, n1, ell, p):
 STREAM_CONFIGS = [(4, 64, 4, 8), (4, 16, 3, 6), (4, 28, 4, 6), (4, 40, 3, 8), (4, 100, 4, 8), (4, 52, 3, 6),
                   (4, 46, 3, 12), (4, 88, 4, 12),
                   # H + 9 a multiple of 6: the skewed level schedule
-                  (4, 87, 3, 8), (4, 15, 4, 8), (4, 33, 3, 8)]
+                  (4, 87, 3, 8), (4, 15, 4, 8), (4, 33, 3, 8), (4, 3, 3, 8)]
 
 
 @pytest.mark.parametrize("cfg", STREAM_CONFIGS, ids=["S%d_H%d_D%d_NW%d" % c for c in STREAM_CONFIGS])
