@@ -311,8 +311,8 @@ struct StreamUnit {
       const float2 ndl = f2add(cf.nd, q[0]);                 // -(d - lr)
       const float2 rr = f2fma(q[1], neg2(xi), f2fma(ndl, xr, nb[0]));
       const float2 ri = f2fma(q[1], xr, f2fma(ndl, xi, nb[1]));
-      const float2 dr = f2fma(pv[0], m1, xr), di = f2fma(pv[1], m1, xi), ndi = f2fma(xi, m1, pv[1]);
-      nw[0] = f2fma(q[5], neg2(ri), f2fma(q[4], rr, f2fma(q[3], ndi, f2fma(q[2], dr, xr))));
+      const float2 dr = f2fma(pv[0], m1, xr), di = f2fma(pv[1], m1, xi);  // x - x_prev
+      nw[0] = f2fma(q[5], neg2(ri), f2fma(q[4], rr, f2fma(q[3], neg2(di), f2fma(q[2], dr, xr))));
       nw[1] = f2fma(q[5], rr, f2fma(q[4], ri, f2fma(q[3], dr, f2fma(q[2], di, xi))));
     } else {
       const float2 x0 = cur[0], x1 = cur[1];
