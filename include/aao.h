@@ -225,13 +225,14 @@ int aao_set_step_kernel(aao_handle h, int kind);
 /*
  * Configuration of the warp-strip kernel (AAO_STEP_STREAM): S fused Chebyshev
  * steps per launch (the halo width; 2 or 4), H interior rows per segment
- * (1 <= H <= 4096), D rows prefetched ahead (3 or 4) and NW warps per CTA.
+ * (1 <= H <= 4096), D rows prefetched ahead (3 or 4; 5 with S = 4 and NW = 8) and
+ * NW warps per CTA.
  * H + 2S a multiple of 6: the S levels of a row step advance in lockstep (S = 4:
  * NW 6, 8 or 12; S = 2: NW 8, 12 or 16).  S = 4 and H + 9 a multiple of 6: the
  * skewed schedule, where levels 3 and 4 trail level 2 by one more row so that a
  * row step holds two independent chains of levels (NW 8; one more row step per
  * segment; the same arithmetic, bit for bit).  The default without a tune cache
- * is S = 4 on the skewed schedule, D = 4, NW = 8 and the segment height that
+ * is S = 4 on the skewed schedule, D = 5, NW = 8 and the segment height that
  * fills one round of the device's warps.  No counterpart in the paper: these
  * are launch parameters of this library's kernel (Eq. 7's steps are
  * unchanged).  AAO_EINVAL for an unsupported combination.
@@ -256,7 +257,7 @@ int aao_get_stream_tail(aao_handle h, int32_t out[3]);
  * unchanged; only which kernel runs them, and with which launch parameters, is chosen).
  * Candidates: AAO_STEP_TILE, AAO_STEP_TMA, and AAO_STEP_STREAM with halo depth S in {2, 4},
  * segment heights that fill one to three rounds of the device's warps (and one segment per
- * strip), D in {3, 4} and each supported NW.  Each candidate runs reps + 1 preconditioner
+ * strip), each supported D (3 to 5) and NW.  Each candidate runs reps + 1 preconditioner
  * applies on the handle's own staging buffers (the first untimed) and is timed by CUDA events
  * on the handle's stream; the fastest becomes what AAO_STEP_AUTO selects on h.  When the
  * winner is the warp-strip kernel with S = 4 and the sweep ends in a two-step launch, the

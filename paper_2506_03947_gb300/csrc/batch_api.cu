@@ -624,10 +624,10 @@ int aao_batch_set_sweep(aao_batch B, int kind, int S, int H, int D, int NW) {
     c.H = H;
     c.D = D;
     c.NW = NW;
-    if (!aao::stream_config_supported(c) || S != 4 || NW != 8 || (H + 8) % 6 != 0)
+    if (!aao::stream_config_supported(c) || S != 4 || NW != 8 || D > 4 || (H + 8) % 6 != 0)
       return bfail(B, AAO_EINVAL,
-                   "the batched warp-strip launch runs S = 4, NW = 8 and the lockstep schedule, H + 8 a multiple "
-                   "of 6 (got S=%d H=%d D=%d NW=%d)",
+                   "the batched warp-strip launch runs S = 4, D 3 or 4, NW = 8 and the lockstep schedule, H + 8 "
+                   "a multiple of 6 (got S=%d H=%d D=%d NW=%d)",
                    S, H, D, NW);
     if (B->p - 2 < S + 1) return bfail(B, AAO_EINVAL, "inner_its %d leaves no fused launch", B->p);
     std::vector<int> all(B->M), nunits(B->M);

@@ -47,6 +47,9 @@ constexpr int kSW = 64;  // staged columns of a strip
 __device__ __forceinline__ void cp8(unsigned dst, const void* src, unsigned src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp16(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -150,21 +153,30 @@ template <int S, int D, int PSRC, bool CPLX, int SK>
 struct StreamUnit {
   static constexpr int NA = StreamGeom<PSRC>::NA;
   static constexpr int LS = level_lag<SK>(S);  // lag of the output level
-  static_assert(D + 2 <= kRing && S + 2 <= kRing, "ring or window too shallow");
+  static_assert(D + 1 <= kRing && S + 2 <= kRing, "ring or window too shallow");
   static_assert(SK == 0 || S == 4, "the skewed schedule is defined for S = 4");
   static_assert(LS + 1 <= kRing, "face window too shallow");
 
   const StreamGeo& a;
   unsigned ringA, ringB;  // this warp's rings (shared addresses) plus the lane's 8-byte slot
-  // element offsets of this lane's first cell: in the fields (plane p0) and in a face array
-  // (column 0 when the lane's cells are outside the grid: such copies read nothing)
+  unsigned cpA, cpB;      // ... plus the lane's copy slot (S = 4: 16 bytes, lanes 16-31 in the
+                          // second array of a pair; S = 2: the lane's own 8 bytes)
+  // Copies, S = 4 (the strip starts at a multiple of four columns): lane l moves 16 bytes
+  // (columns 4 (l mod 16) .. 4 (l mod 16) + 3 of the strip) of the pair's first plane (l < 16)
+  // or second plane (l >= 16), and of cx (l < 16) or cy, and then reads its own two cells,
+  // copied by another lane (visible to it after the warp barrier).  S = 2 (strips start two
+  // columns off a multiple of four): each lane copies its own two cells, 8 bytes per array.
+  // Element offsets of the lane's copy chunk: in the fields (its plane) and in its face array
+  // (column 0 when the chunk is outside the grid: such copies read nothing)
   int64_t offf;
   int offc;
+  const float* fsrc;  // cx or cy
+  int64_t offo;       // element offset of the lane's own first cell in plane p0 (outputs)
   int y0;      // first interior row of the segment (stream row S)
   bool colok, interior_lane;
   int ybase;   // grid row of stream row 0 (y0 - S)
-  int nrow;    // n1 when this lane's columns are inside the grid, else 0: stream row u is read
-               // iff (unsigned)(ybase + u) < nrow
+  int nrow;    // n1 when the lane's copy chunk is inside the grid, else 0: stream row u is
+               // copied iff (unsigned)(ybase + u) < nrow
   int hout;    // rows of the segment this lane writes (0 for halo lanes and lanes outside)
   PassCoef<S> pc;
   float it[2];            // 1/theta (x_1 = bhat/theta): real (it0, it1), complex (re, im)
@@ -173,6 +185,8 @@ struct StreamUnit {
   RowCoef Cw[kRing];      // face coefficients of stream row r in Cw[r % 6]
   float2 nS6;             // north faces of stream row t - 6 (SK 1: the south faces of level 4's row)
   float2 last[2];         // level S of the step's output row
+  float2 pvk[2];          // x_{k-1} of row t - 1 (PSRC 2), read before this step's copies may
+                          // reuse its ring slot (D = 5)
 
   __device__ __forceinline__ unsigned slotA(int row_slot, int arr) const {
     return ringA + (unsigned)((row_slot * NA + arr) * 256);
@@ -181,24 +195,33 @@ struct StreamUnit {
     return ringB + (unsigned)((row_slot * kNB + arr) * 256);
   }
 
-  // copies of stream row u into ring slot SL of both rings
+  // copies of stream row u into ring slot SL of both rings (the two arrays of each pair of
+  // slots are adjacent, so one 16-byte copy per lane fills both)
   template <int SL>
   __device__ __forceinline__ void issue(int u) {
     const int y = ybase + u;
     const bool ok = (unsigned)y < (unsigned)nrow;
     const int64_t row = ok ? (int64_t)y * a.g.n0 : 0;
-    const unsigned nb = ok ? 8u : 0u;
     const int64_t of = offf + row, oc = offc + row;
-    cp8(slotA(SL, 0), a.xk + of, nb);
-    cp8(slotA(SL, 1), a.xk + a.g.N + of, nb);
-    if (PSRC == 2) {
-      cp8(slotA(SL, 2), a.xkm1 + of, nb);
-      cp8(slotA(SL, 3), a.xkm1 + a.g.N + of, nb);
+    if constexpr (S == 4) {
+      const unsigned nb = ok ? 16u : 0u;
+      cp16(cpA + (unsigned)((SL * NA + 0) * 256), a.xk + of, nb);
+      if (PSRC == 2) cp16(cpA + (unsigned)((SL * NA + 2) * 256), a.xkm1 + of, nb);
+      cp16(cpB + (unsigned)((SL * kNB + kB_H0) * 256), a.bhat + of, nb);
+      cp16(cpB + (unsigned)((SL * kNB + kB_E) * 256), fsrc + oc, nb);
+    } else {
+      const unsigned nb = ok ? 8u : 0u;
+      cp8(cpA + (unsigned)((SL * NA + 0) * 256), a.xk + of, nb);
+      cp8(cpA + (unsigned)((SL * NA + 1) * 256), a.xk + a.g.N + of, nb);
+      if (PSRC == 2) {
+        cp8(cpA + (unsigned)((SL * NA + 2) * 256), a.xkm1 + of, nb);
+        cp8(cpA + (unsigned)((SL * NA + 3) * 256), a.xkm1 + a.g.N + of, nb);
+      }
+      cp8(cpB + (unsigned)((SL * kNB + kB_H0) * 256), a.bhat + of, nb);
+      cp8(cpB + (unsigned)((SL * kNB + kB_H1) * 256), a.bhat + a.g.N + of, nb);
+      cp8(cpB + (unsigned)((SL * kNB + kB_E) * 256), a.cx + oc, nb);
+      cp8(cpB + (unsigned)((SL * kNB + kB_N) * 256), a.cy + oc, nb);
     }
-    cp8(slotB(SL, kB_H0), a.bhat + of, nb);
-    cp8(slotB(SL, kB_H1), a.bhat + a.g.N + of, nb);
-    cp8(slotB(SL, kB_E), a.cx + oc, nb);
-    cp8(slotB(SL, kB_N), a.cy + oc, nb);
   }
 
   // step t = 6 b + I of the stream (T: streamed input rows)
@@ -207,10 +230,16 @@ struct StreamUnit {
     constexpr int PH = I % 3;
     constexpr int SL = I;                        // ring slot and window row of stream row t
     constexpr int SLm = (I + kRing - 1) % kRing;  // ... of row t - 1
+    cp_wait<D - 1>();  // row t has landed (this lane's copies); past the last row, stale rows
+                       // feed only halo rows that no output depends on
+    if (PSRC == 2) {
+      pvk[0] = lds2(slotA(SLm, 2));
+      pvk[1] = lds2(slotA(SLm, 3));
+    }
+    __syncwarp();      // row t of every lane has landed; and every lane is done reading the ring
+                       // slot (row t + D - 6 <= t - 1) the next copies overwrite
     if (t + D < T) issue<(I + D) % kRing>(t + D);
     cp_commit();
-    cp_wait<D>();  // row t has landed (this lane's copies); past the last row, stale rows feed
-                   // only halo rows that no output depends on
     if (SK) nS6 = Cw[SL].n;  // row t - 6, about to be replaced by row t
     {
       L[0][PH][0] = lds2(slotA(SL, 0));
@@ -239,7 +268,7 @@ struct StreamUnit {
     const int oy = t - LS - S;
     if ((unsigned)oy < (unsigned)hout) {
       constexpr int RS = ((PH - LS) % 3 + 3) % 3;
-      const int64_t o = offf + (int64_t)(y0 + oy) * a.g.n0;
+      const int64_t o = offo + (int64_t)(y0 + oy) * a.g.n0;
       *reinterpret_cast<float2*>(a.outB + o) = last[0];
       *reinterpret_cast<float2*>(a.outB + o + a.g.N) = last[1];
       if (a.outA) {  // null on the sweep's final launch, which keeps x_p alone
@@ -262,7 +291,6 @@ struct StreamUnit {
     constexpr int RN = (RS + 1) % 3, RSo = (RS + 2) % 3;
     constexpr int W = ((I - LG) % kRing + kRing) % kRing;       // rho % 6
     constexpr int Wm = ((I - LG - 1) % kRing + kRing) % kRing;  // (rho - 1) % 6
-    constexpr int SAm = ((I - 1) % kRing + kRing) % kRing;      // ring A slot of row t - 1
     static_assert(j > 0 || LG == 1, "level 1 reads x_{k-1} of row t - 1");
     const RowCoef& cf = Cw[W];
     const float2 kS = (LG + 1 == kRing) ? nS6 : Cw[Wm].n;  // row t - 6 has left the window
@@ -271,8 +299,8 @@ struct StreamUnit {
     float2 pv[2];
     if (j == 0) {
       if (PSRC == 2) {
-        pv[0] = lds2(slotA(SAm, 2));
-        pv[1] = lds2(slotA(SAm, 3));
+        pv[0] = pvk[0];
+        pv[1] = pvk[1];
       } else {
         // x_{k-1} = x_1 = bhat / theta
         const float h00 = hh[0].x, h01 = hh[0].y, h10 = hh[1].x, h11 = hh[1].y;
@@ -343,6 +371,10 @@ struct StreamUnit {
       issue<3>(3);
       cp_commit();
     }
+    if (D >= 5) {
+      issue<4>(4);
+      cp_commit();
+    }
 #pragma unroll
     for (int j = 0; j < S; ++j)
 #pragma unroll
@@ -359,6 +391,7 @@ struct StreamUnit {
       step<5>(t + 5, T);
     }
     cp_wait<0>();  // (empty groups only by now) the rings are free for the next unit
+    __syncwarp();
   }
 };
 
@@ -372,10 +405,28 @@ __device__ __forceinline__ void stream_unit(const StreamGeo& a, const StepArgs<f
   su.colok = un.colok;
   su.interior_lane = lane >= S / 2 && lane < 32 - S / 2;
   su.ybase = un.y0 - S;
-  su.nrow = un.colok ? a.g.n1 : 0;
   su.hout = (su.interior_lane && un.colok) ? min(a.H, a.g.n1 - un.y0) : 0;
-  su.offc = un.colok ? un.gx : 0;  // keep every source address inside its array
-  su.offf = (int64_t)un.p0 * a.g.N + su.offc;
+  su.offo = (int64_t)un.p0 * a.g.N + (un.colok ? un.gx : 0);
+  if constexpr (S == 4) {
+    // the lane's copy chunk: columns gc .. gc + 3 (gc and n0 are multiples of 4: the chunk is
+    // wholly inside the grid or wholly outside), plane p0 + (lane >= 16)
+    const int hi = lane >> 4;
+    const int gc = un.gx - 2 * lane + 4 * (lane & 15);
+    const bool cok = gc >= 0 && gc < a.g.n0;
+    su.cpA = ringA + (unsigned)(lane * 16);
+    su.cpB = ringB + (unsigned)(lane * 16);
+    su.nrow = cok ? a.g.n1 : 0;
+    su.offc = cok ? gc : 0;  // keep every source address inside its array
+    su.offf = (int64_t)(un.p0 + hi) * a.g.N + su.offc;
+    su.fsrc = hi ? a.cy : a.cx;
+  } else {
+    su.cpA = su.ringA;
+    su.cpB = su.ringB;
+    su.nrow = un.colok ? a.g.n1 : 0;
+    su.offc = un.colok ? un.gx : 0;
+    su.offf = (int64_t)un.p0 * a.g.N + su.offc;
+    su.fsrc = a.cx;
+  }
   if (CPLX) {
     su.it[0] = steps[0].it_re[un.m0], su.it[1] = steps[0].it_im[un.m0];
   } else {
@@ -481,7 +532,7 @@ bool stream_config_supported(const StreamConfig& c) {
   if ((c.S != 2 && c.S != 4) || c.H < 1 || c.H > 4096) return false;
   const int sk = stream_skew(c);
   if ((c.H + 2 * c.S + (sk ? 1 : 0)) % kUnroll != 0) return false;
-  if (c.D != 3 && c.D != 4) return false;
+  if (c.D < 3 || c.D > 5 || (c.D == 5 && (c.S != 4 || c.NW != 8))) return false;
   if (c.S == 2) return c.NW == 8 || c.NW == 12 || c.NW == 16;
   if (sk) return c.NW == 8;  // 196-205 registers: no room for 12 warps
   return c.NW == 6 || c.NW == 8 || c.NW == 12;
@@ -492,6 +543,10 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
                           float* outB, const FuseSteps& fs, cudaStream_t s) {
   if (g.n2 != 1 || g.n0 % 4 != 0 || (psrc != 1 && psrc != 2) || ell < 4 || ell > kMaxEll || (ell % 2) ||
       !stream_config_supported(c))
+    return cudaErrorInvalidValue;
+  // the four-step kernel copies 16-byte chunks of every input array
+  if (((reinterpret_cast<uintptr_t>(cx) | reinterpret_cast<uintptr_t>(cy) | reinterpret_cast<uintptr_t>(bhat) |
+        reinterpret_cast<uintptr_t>(xk) | reinterpret_cast<uintptr_t>(xkm1)) & 15) != 0)
     return cudaErrorInvalidValue;
   const int sk = stream_skew(c);
 #define AAO_STREAM_CFG(SS, DD, NN, KK)                                                                         \
@@ -505,6 +560,8 @@ cudaError_t launch_stream(const GridDesc& g, int ell, int psrc, const StreamConf
   AAO_STREAM_CFG(4, 4, 12, 0)
   AAO_STREAM_CFG(4, 3, 8, 1)
   AAO_STREAM_CFG(4, 4, 8, 1)
+  AAO_STREAM_CFG(4, 5, 8, 1)
+  AAO_STREAM_CFG(4, 5, 8, 0)
   AAO_STREAM_CFG(2, 3, 8, 0)
   AAO_STREAM_CFG(2, 3, 12, 0)
   AAO_STREAM_CFG(2, 4, 8, 0)

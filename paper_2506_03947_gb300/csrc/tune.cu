@@ -270,9 +270,9 @@ StreamConfig wave_stream_config(const GridDesc& g, int ell, int S, int D, int NW
   return c;
 }
 
-// The warp-strip configuration used without a cache entry: S = 4 on the skewed schedule, D = 4,
+// The warp-strip configuration used without a cache entry: S = 4 on the skewed schedule, D = 5,
 // 8 warps per CTA, one round of units.
-StreamConfig default_stream_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 4, 4, 8, 1, 1); }
+StreamConfig default_stream_config(const GridDesc& g, int ell) { return wave_stream_config(g, ell, 4, 5, 8, 1, 1); }
 
 // The two-step final launch: S = 2, D = 3, 16 warps per CTA (the two-step kernel stays within
 // 128 registers), one round of units.
@@ -390,7 +390,7 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
         if (segs >= 1) hs.push_back(std::min(hmax, aao::round_h((h->g.n1 + segs - 1) / segs, S, skew)));
       }
       for (int H : hs)
-        for (int D : {3, 4}) {
+        for (int D : {3, 4, 5}) {  // 5: S = 4 at 8 warps only (stream_config_supported)
           aao::StreamConfig c;
           c.S = S;
           c.H = H;

@@ -77,7 +77,9 @@ def test_step_kernels_match_oracle_and_each_other(n0, n1, ell, p):
 STREAM_CONFIGS = [(4, 64, 4, 8), (4, 16, 3, 6), (4, 28, 4, 6), (4, 40, 3, 8), (4, 100, 4, 8), (4, 52, 3, 6),
                   (4, 46, 3, 12), (4, 88, 4, 12),
                   # H + 9 a multiple of 6: the skewed level schedule
-                  (4, 87, 3, 8), (4, 15, 4, 8), (4, 33, 3, 8), (4, 3, 3, 8)]
+                  (4, 87, 3, 8), (4, 15, 4, 8), (4, 33, 3, 8), (4, 3, 3, 8),
+                  # five rows in flight (the ring slot of row t - 1 is refilled once its x_{k-1} is read)
+                  (4, 87, 5, 8), (4, 88, 5, 8), (4, 15, 5, 8), (4, 3, 5, 8)]
 
 
 @pytest.mark.parametrize("cfg", STREAM_CONFIGS, ids=["S%d_H%d_D%d_NW%d" % c for c in STREAM_CONFIGS])
@@ -106,8 +108,8 @@ def test_stream_config_rules():
     P = _problem(64, 64, 8, 9)
     s = make_solver(P, 1, 9)
     # H + 8 and H + 9 both off a multiple of 6; the skewed schedule (H + 9) at 6 or 12 warps
-    for bad in ((4, 62, 4, 8), (4, 24, 4, 8), (2, 64, 4, 8), (4, 64, 5, 8), (4, 64, 4, 9), (4, 0, 3, 8),
-                (4, 63, 4, 12), (4, 63, 3, 6)):
+    for bad in ((4, 62, 4, 8), (4, 24, 4, 8), (2, 64, 4, 8), (4, 64, 6, 8), (4, 64, 4, 9), (4, 0, 3, 8),
+                (4, 63, 4, 12), (4, 63, 3, 6), (4, 64, 5, 12), (2, 62, 5, 8)):
         with pytest.raises(binding.AaoError):
             s.set_stream_config(*bad)
     s64 = make_solver(P, 0, 9)
