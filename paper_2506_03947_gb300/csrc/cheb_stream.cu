@@ -18,19 +18,25 @@
 //    same step from level j's rows t-j, t-1-j, t-2-j.  Each level's three newest rows live in
 //    registers (the step loop is unrolled by three, so the rotation is a renaming); level S of
 //    row t-S, and level S-1 of the same row, are the outputs.
-//  * Inputs stream through per-lane shared-memory rings filled by cp.async (8 bytes per lane
-//    per plane, zero-filled outside the grid, which gives the Neumann boundary: faces and
-//    values outside are zero).  Rows are issued D steps ahead; a lane only ever reads the
-//    ring slots it filled itself, so cp.async.wait_group is the only synchronisation.  Ring A
-//    holds x_k and x_{k-1}, ring B bhat and the two face arrays, 6 rows each.  When a row
-//    lands, its bhat and face coefficients (with the diagonal) move into register windows of
-//    6 rows, where all S levels read them; shared memory is read once per value.  The step
-//    loop is unrolled by 6, so every ring slot and window row is a compile-time constant.
+//  * Inputs stream through per-warp shared-memory rings filled by cp.async, zero-filled
+//    outside the grid (the Neumann boundary: faces and values outside are zero).  With S = 4
+//    a lane copies 16 bytes, four columns of one plane of a pair (lanes 0-15 the first, 16-31
+//    the second; cx and cy likewise), so a row of a pair of arrays is one copy instruction;
+//    with S = 2 (strips two columns off a multiple of four) each lane copies its own 8 bytes
+//    per array.  Rows are issued D steps ahead; at each step a lane waits for its own copies of
+//    the row (cp.async.wait_group) and a warp barrier (__syncwarp) publishes every lane's, and
+//    also orders the ring slot's last reads (x_{k-1} of row t-1, read before the barrier)
+//    before its refill, so D = 5 rows fit a 6-row ring.  Ring A holds x_k and x_{k-1}, ring B
+//    bhat and the two face arrays, 6 rows each.  When a row lands, its bhat and face
+//    coefficients (with the diagonal) move into register windows of 6 rows, where all S levels
+//    read them; shared memory is read once per value.  The step loop is unrolled by 6, so
+//    every ring slot and window row is a compile-time constant.
 //  * Per cell and S steps the launch moves (5 ell + 2) * 4 bytes algorithmically (reads x_k,
 //    x_{k-1}, bhat, two face arrays; writes two fields); the redundant halo reads are
 //    64/(64-2S) across x and (H+2S)/H across y, and mostly hit L2 (neighbouring units run
 //    side by side).
-// cp.async waits are hardware waits on the thread's own copies: nothing here spins.
+// cp.async waits are hardware waits on the thread's own copies and the warp barrier involves
+// only the warp's own lanes: nothing here spins, and warps never wait on one another.
 #include <type_traits>
 #include <utility>
 
