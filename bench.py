@@ -483,7 +483,7 @@ def run_batch_leg(args, binding, torch, sptr, peak):
                                 "batch_vs_fp64_rel_diff_max": max(diff64),
                                 "timing": "CUDA events around one solve per instance (after one untimed solve), "
                                           "all-FP64 handles one after another"},
-            "fused_sweep": {"kernel": "kb_cheb_stream<S=4,D=5,NW=8> and the final kb_cheb_stream<S=2,D=4,NW=8> "
+            "fused_sweep": {"kernel": "kb_cheb_stream<S=4,D=3,NW=8> and the final kb_cheb_stream<S=2,D=3,NW=8> "
                                       "(persistent warp-strip launches over (member, frequency pair, segment, "
                                       "strip) units from a device queue)",
                             "launches": bprof["launches"], "avg_launch_ms": bprof["ms"] / max(1, bprof["launches"]),

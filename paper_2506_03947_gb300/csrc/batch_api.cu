@@ -110,7 +110,6 @@ int set_tail(aao_batch_ctx* B, const aao::StreamConfig& c) {
   aao::StreamConfig t = c;
   t.S = 2;
   t.H = c.H - 2;  // H + 8 a multiple of 6 <=> (H - 2) + 4 a multiple of 6
-  t.D = c.D > 4 ? 4 : c.D;  // the two-step launch keeps at most four rows in flight
   t.NW = 8;
   if (!aao::stream_config_supported(t)) return bfail(B, AAO_EINVAL, "no two-step configuration for H=%d", c.H);
   std::vector<int> all(B->M), nunits(B->M);
@@ -451,7 +450,7 @@ int aao_batch_create(aao_batch* out, int count, const aao_handle* members, int u
   // warp-strip units of every member (any ell) for the fused sweeps: segments of 64 rows
   B->scfg.S = 4;
   B->scfg.H = 64;
-  B->scfg.D = 5;
+  B->scfg.D = 3;
   B->scfg.NW = 8;
   B->dim = members[0]->dim;
   if (B->p < 7) B->sweep = AAO_STEP_TILE;  // no step of the fused form would fit
@@ -625,9 +624,9 @@ int aao_batch_set_sweep(aao_batch B, int kind, int S, int H, int D, int NW) {
     c.H = H;
     c.D = D;
     c.NW = NW;
-    if (!aao::stream_config_supported(c) || S != 4 || NW != 8 || (H + 8) % 6 != 0)
+    if (!aao::stream_config_supported(c) || S != 4 || NW != 8 || D > 4 || (H + 8) % 6 != 0)
       return bfail(B, AAO_EINVAL,
-                   "the batched warp-strip launch runs S = 4, D 3 to 5, NW = 8 and the lockstep schedule, H + 8 "
+                   "the batched warp-strip launch runs S = 4, D 3 or 4, NW = 8 and the lockstep schedule, H + 8 "
                    "a multiple of 6 (got S=%d H=%d D=%d NW=%d)",
                    S, H, D, NW);
     if (B->p - 2 < S + 1) return bfail(B, AAO_EINVAL, "inner_its %d leaves no fused launch", B->p);

@@ -776,7 +776,6 @@ cudaError_t launch_batch_stream(const BInst* I, const int* act, const WorkList& 
   if (c.S == SS && c.D == DD && c.NW == NN) return launch_batch_stream_cfg<SS, DD, NN>(ba, psrc, s);
   AAO_BSTREAM_CFG(4, 3, 8)
   AAO_BSTREAM_CFG(4, 4, 8)
-  AAO_BSTREAM_CFG(4, 5, 8)
   AAO_BSTREAM_CFG(2, 3, 8)
   AAO_BSTREAM_CFG(2, 4, 8)
 #undef AAO_BSTREAM_CFG

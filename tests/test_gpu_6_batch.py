@@ -207,4 +207,4 @@ def test_batch_profile_reports_fused_sweeps():
         batch.set_sweep(binding.AAO_STEP_STREAM, 4, 63, 3, 8)       # the skewed schedule: single solver only
     assert "lockstep" in str(ei.value)
     with pytest.raises(binding.AaoError):
-        batch.set_sweep(binding.AAO_STEP_STREAM, 4, 64, 6, 8)       # at most five rows in flight
+        batch.set_sweep(binding.AAO_STEP_STREAM, 4, 64, 5, 8)       # five rows in flight: single solver only
