@@ -285,8 +285,8 @@ int aao_autotune(aao_handle h, int reps, aao_tune_entry* results, int max_result
  * every later aao_create in the process (NULL: none; without a call, the environment
  * variable AAO_TUNE_CACHE is used); aao_create applies the entry matching the device name,
  * dim, n, ell and precision (one with the same inner_its preferred) to AAO_STEP_AUTO, and
- * without one uses the warp-strip kernel with S = 4, D = 3, NW = 8 and the segment height
- * that fills one round of the device's warps.
+ * without one uses the default of aao_set_stream_config (S = 4 on the skewed schedule,
+ * D = 5, NW = 8, the segment height that fills one round of the device's warps).
  * aao_tune_lookup performs that lookup on the host alone (no device needed): returns 1 and
  * fills out = (kind, S, H, D, NW) when an entry matches, 0 when none does, and -AAO_EINVAL
  * when the file cannot be read or parsed.  device NULL matches any device.
