@@ -14,10 +14,11 @@
 //    owns columns 2l, 2l+1), of which the middle 64 - 2S are interior; a segment is H interior
 //    rows, streamed from S rows above it to S rows below it.  Units are spread over all warps of
 //    a persistent grid (one CTA per SM); warps never wait on one another.
-//  * Level 0 (x_k) of stream row t arrives at step t; level j+1 of row t-1-j is computed at the
-//    same step from level j's rows t-j, t-1-j, t-2-j.  Each level's three newest rows live in
-//    registers (the step loop is unrolled by three, so the rotation is a renaming); level S of
-//    row t-S, and level S-1 of the same row, are the outputs.
+//  * Level 0 (x_k) of stream row t arrives at step t; level j+1 of row t - lag(j+1) is computed
+//    at the same step from level j's three rows around it: lag(j) = j in the lockstep schedule,
+//    0, 1, 2, 4, 5 in the skewed one (S = 4, level_lag).  Each level's three newest rows live in
+//    registers (the step loop is unrolled by 6, a multiple of three, so the rotation is a
+//    renaming); level S of row t - lag(S), and level S-1 of the same row, are the outputs.
 //  * Inputs stream through per-warp shared-memory rings filled by cp.async, zero-filled
 //    outside the grid (the Neumann boundary: faces and values outside are zero).  With S = 4
 //    a lane copies 16 bytes, four columns of one plane of a pair (lanes 0-15 the first, 16-31
@@ -442,8 +443,8 @@ __device__ __forceinline__ void stream_unit(const StreamGeo& a, const StepArgs<f
   su.run();
 }
 
-// Registers: 8 warps of up to 200 per thread (two per SM sub-partition of 16 K registers); the
-// two-step variant with 12 warps stays within 168.
+// Registers: the four-step kernels at 8 warps use 180-215 per thread (two warps per SM
+// sub-partition of 16 K registers); the two-step kernel stays within 128 at 16 warps.
 template <int S, int D, int NW, int PSRC, int SK>
 __global__ void __launch_bounds__(NW * 32, 1) k_cheb_stream(const __grid_constant__ StreamArgs args) {
   const StreamGeo& a = args.geo;
@@ -540,7 +541,7 @@ bool stream_config_supported(const StreamConfig& c) {
   if ((c.H + 2 * c.S + (sk ? 1 : 0)) % kUnroll != 0) return false;
   if (c.D < 3 || c.D > 5 || (c.D == 5 && (c.S != 4 || c.NW != 8))) return false;
   if (c.S == 2) return c.NW == 8 || c.NW == 12 || c.NW == 16;
-  if (sk) return c.NW == 8;  // 196-205 registers: no room for 12 warps
+  if (sk) return c.NW == 8;  // 205-215 registers: no room for 12 warps
   return c.NW == 6 || c.NW == 8 || c.NW == 12;
 }
 
