@@ -490,7 +490,7 @@ def run_batch_leg(args, binding, torch, sptr, peak):
                             "bytes_per_launch": bprof["bytes"] / max(1, bprof["launches"]),
                             "achieved_gbs": fused_gbs, "peak_gbs": peak,
                             "frac": (fused_gbs / peak if fused_gbs else None),
-                            "timing": "CUDA events around each fused launch in one extra solve without graphs"},
+                            "timing": "CUDA events around the back-to-back fused launches of each Arnoldi step in one extra solve without graphs"},
             "timing": "host wall clock around synchronised batch solves (3 reps after 2 warm-ups)"}
 
 

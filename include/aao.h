@@ -436,9 +436,10 @@ void aao_batch_destroy(aao_batch hb);
 int aao_batch_set_sweep(aao_batch hb, int kind, int S, int H, int D, int NW);
 /*
  * Event timing of the batch's Chebyshev sweeps (graphs are not used while it
- * is on; turning it on or off clears the totals).  With a fused sweep each
- * fused launch is timed: x_k, x_{k-1} or none, bhat and two face arrays read
- * and two fields written (one, x_p, by the final launch).  With single steps
+ * is on; turning it on or off clears the totals).  With a fused sweep the
+ * fused launches of each Arnoldi step, which run back to back, are timed as one
+ * span: x_k, x_{k-1} or none, bhat and two face arrays read and two fields
+ * written per launch (one, x_p, by the final launch).  With single steps
  * (every 3D batch) the steps k = 2 .. p-1 of each ell group are timed as one span of
  * p - 2 launches: x_k, x_{k-1} (none at k = 2) and bhat read and x_{k+1}
  * written per member, and the dim face arrays once per member, or once for

@@ -189,6 +189,10 @@ int batch_precond_stream(aao_batch_ctx* B, int j) {
     ++k;
     --R;
   }
+  // the fused launches run back to back: one event span over all of them (events between them
+  // would add gaps of their own)
+  const int ev = prof_begin(B, 0.0, 0);
+  if (ev == -2) return bfail(B, AAO_ECUDA, "profiling events could not be created or recorded");
   while (R > 0) {
     const int S = R >= 4 ? 4 : 2;
     const bool fin = (R == S);
@@ -198,11 +202,12 @@ int batch_precond_stream(aao_batch_ctx* B, int j) {
     for (int f = 0; f < 4 && n < 2; ++f)
       if (f != cur && f != prev) o[n++] = f;
     const int psrc = prev < 0 ? 1 : 2;
-    const int ev = prof_begin(B, B->prof ? fused_bytes(B, psrc, fin) : 0.0, 1);
-    if (ev == -2) return bfail(B, AAO_ECUDA, "profiling events could not be created or recorded");
+    if (ev >= 0) {
+      B->pend_bytes[ev] += fused_bytes(B, psrc, fin);
+      B->pend_launches[ev] += 1;
+    }
     AAO_BCK(B, aao::launch_batch_stream(B->dI, B->dact, units, c, k, psrc, cur, prev, fin ? -1 : o[0],
                                         fin ? o[0] : o[1], B->queue, s));
-    if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
     if (fin) {
       cur = o[0];
     } else {
@@ -212,6 +217,7 @@ int batch_precond_stream(aao_batch_ctx* B, int j) {
     k += S;
     R -= S;
   }
+  if (ev >= 0) AAO_BCK(B, cudaEventRecord(B->events[2 * ev + 1], s));
   // z = Gamma^{-1} U x_p into Z_j, per ell group
   for (size_t g = 0; g < B->wstep.size(); ++g)
     AAO_BCK(B, aao::batch_idft(B->dI, B->dact, B->wstep[g].first, B->wstep[g].second, j, cur, s));
